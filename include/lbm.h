@@ -1,0 +1,204 @@
+/*
+ * lbm.h -- C ABI of the GB300 boiling time-step library (liblbm_gb300.so).
+ *
+ * One run = one 2-D domain of NX periodic columns: NS solid heater rows
+ * (row 0 = heater bottom) under NF fluid rows.  Each time step advances
+ *   - the flow: D2Q9 multiple-relaxation-time lattice Boltzmann collision with
+ *     the pseudopotential force of a Peng-Robinson fluid and Li's improved
+ *     forcing, fused with streaming and halfway bounce-back
+ *     (arXiv:1911.10747 Sec. 2.1, Eq. 1-15);
+ *   - the heat: the temperature equation of Eq. 24 (advection, conduction
+ *     with the solid/fluid conductivity jump, phase-change source) by one RK4
+ *     step (Eq. 25-26) with the isotropic differences of Eq. 27-28;
+ *   - the diagnostics: heater-bottom flux (Eq. 36/39), heater-top local flux,
+ *     vapour fraction and mass.
+ *
+ * Conventions for every entry point:
+ *   - Return value: LBM_OK (0) or an lbm_status error code; the message of
+ *     the last error on a handle is returned by lbm_last_error.
+ *   - All structs passed in are copied; the caller keeps ownership.
+ *   - The handle owns every device allocation it makes; lbm_destroy frees
+ *     them.  Pointers passed as "host" buffers must stay valid for the call
+ *     only (calls that read back synchronise the handle's stream first).
+ *   - Work is queued on the handle's CUDA stream (lbm_opts_t.stream, or a
+ *     stream the library creates).  Numerical faults found by the kernels
+ *     (negative pseudopotential radicand, non-finite density or temperature)
+ *     are latched in a device word and reported as LBM_E_NUMERIC by the next
+ *     call that synchronises (lbm_sync and every read-back).
+ *   - A handle is not thread-safe; distinct handles are independent.
+ *
+ * Layouts (row-major, x fastest): populations f[9][NF][NX] in the order of
+ * Eq. 2; temperature T[NS+NF][NX]; rho, ux, uy [NF][NX].  Values crossing the
+ * ABI are always float64, whatever the internal storage precision.
+ */
+#ifndef LBM_GB300_H
+#define LBM_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LBM_ABI_VERSION 1
+
+enum lbm_status {
+    LBM_OK = 0,
+    LBM_E_INVAL = 1,   /* invalid argument or configuration */
+    LBM_E_NOMEM = 2,   /* device or host allocation failed */
+    LBM_E_CUDA = 3,    /* a CUDA runtime call failed (message has the CUDA error) */
+    LBM_E_NUMERIC = 4, /* the kernels latched a numerical fault */
+    LBM_E_TIMEOUT = 5, /* reserved: a bounded device wait gave up */
+    LBM_E_STATE = 6    /* call not valid in the handle's current state */
+};
+
+enum lbm_top_mode { LBM_TOP_WALL = 0, LBM_TOP_OUTFLOW = 1 };
+enum lbm_bc_mode { LBM_BC_SPOTS = 0, LBM_BC_NOISE = 1, LBM_BC_SINE = 2 };
+enum lbm_precision { LBM_FP64 = 0, LBM_FP32 = 1, LBM_FP16 = 2 };
+enum lbm_flags { LBM_PERIODIC_Y = 1, LBM_ISOTHERMAL = 2, LBM_FROZEN_FLOW = 4 };
+enum lbm_field_mask {
+    LBM_FIELD_RHO = 1, LBM_FIELD_UX = 2, LBM_FIELD_UY = 4, LBM_FIELD_T = 8, LBM_FIELD_F = 16
+};
+
+typedef struct lbm_run *lbm_handle;
+
+/* Fluid domain and flow model (Sec. 2.1, 3.1). */
+typedef struct {
+    int32_t nx;          /* periodic columns, >= 1 */
+    int32_t ny_fluid;    /* fluid rows NF, >= 2 */
+    int32_t liquid_rows; /* initial liquid layer (rows 0..liquid_rows-1 at rho_L) */
+    int32_t top_mode;    /* lbm_top_mode: no-slip wall (Sec. 3.1) or zero-gradient outflow */
+    int32_t flags;       /* lbm_flags test modes: periodic in y (needs ny_solid = 0),
+                            temperature frozen, flow frozen (u = 0) */
+    int32_t pad0;
+    double g;            /* gravity magnitude, F_g = (rho - rho_mean)(0, -g), Eq. 15 */
+    double nu_L, nu_V;   /* kinematic viscosities; tau = 3 nu + 1/2 (Eq. 4), Eq. 5 blend */
+    double c_v;          /* specific heat C_V */
+    double cv_chi;       /* lambda = rho * cv_chi in the fluid (Sec. 3.1) */
+    double s[9];         /* MRT rates s0..s8 (Eq. 3); s7, s8 are replaced by 1/tau(rho) */
+    double varpi;        /* weight of the |F_m|^2 term of Eq. 9 */
+    double sign_eps;     /* sign of that term in entry 2 of Eq. 9 (-1 in the cited scheme) */
+    double init_noise;   /* relative amplitude of the seeded initial density noise */
+    double rho_mean;     /* buoyancy reference density; <= 0: the initial fluid mean */
+    uint64_t seed;       /* seed of the counter-based draws (initial noise, noisy bottom) */
+} lbm_domain_t;
+
+/* Solid heater for conjugate heat transfer (Fig. 1b, Sec. 3.1).  Heater rows
+ * conduct only: dT/dt = div(lambda_s grad T) / rho_c_s. */
+typedef struct {
+    int32_t ny_solid;    /* NS heater rows; >= 3 unless the domain is periodic in y */
+    int32_t pad0;
+    double lambda_s;     /* heater conductivity */
+    double rho_c_s;      /* heater volumetric heat capacity rho_S c_S */
+} lbm_heater_t;
+
+/* Peng-Robinson equation of state (Eq. 13) and pseudopotential (Eq. 12). */
+typedef struct {
+    double a, b, R, omega;  /* Tc = 0.0778 a / (0.45724 b R) */
+    double G;               /* interaction strength (Eq. 11-12), negative */
+    double T_sat_over_Tc;   /* saturation temperature: initial and top temperature */
+    double rho_L, rho_V;    /* coexistence densities: initial phases, Eq. 5 blend,
+                               vapour-fraction threshold (rho_L + rho_V) / 2 */
+} lbm_eos_t;
+
+/* Bottom temperature and heater-surface wettability (Sec. 3.2, 4.1). */
+typedef struct {
+    int32_t mode;           /* lbm_bc_mode: constant T_b (with spots), T_b (1 + A(2U-1))
+                               per column and step, or the sine of Sec. 3.2 */
+    int32_t n_spots;        /* nucleate spots, <= 8 */
+    double T_b_over_Tc;     /* bottom temperature */
+    double noise_amp;       /* A of the noisy bottom */
+    double sine_amp_over_Tc, sine_wavelength;  /* T_b + amp Tc sin(2 pi (x - l/4) / l) */
+    int64_t sine_t0, sine_t1;                  /* ... applied for t0 < step < t1 */
+    int32_t spot_x[8];      /* spot centre columns */
+    int32_t spot_half_width;/* a spot covers columns within this periodic distance */
+    int32_t pad0;
+    double c_w_base;        /* c_w = G_w psi(rho_w) of Eq. 14 along the heater surface */
+    double c_w_spot[8];     /* c_w over each spot */
+    double c_w_top;         /* c_w of the top wall */
+} lbm_bc_t;
+
+/* Library options. */
+typedef struct {
+    int32_t precision;      /* lbm_precision: FP64 (oracle parity), FP32 shifted
+                               populations, FP16 population storage (probe) */
+    int32_t use_graphs;     /* 1: lbm_step replays a captured two-step CUDA graph */
+    void *stream;           /* cudaStream_t to queue work on; NULL: library-owned stream */
+    double rho_shift;       /* reference density of the shifted populations; <= 0: rho_mean */
+    int32_t series_capacity;/* per-step diagnostics ring length (0: 4096) */
+    int32_t device;         /* CUDA device ordinal */
+} lbm_opts_t;
+
+/* Create a run, allocate its device state and initialise it (Sec. 3.1):
+ * liquid below, vapour above, at rest, T = T_sat everywhere.  Fails with
+ * LBM_E_INVAL on an inconsistent configuration (message says which field). */
+int lbm_create(const lbm_domain_t *domain, const lbm_heater_t *heater, const lbm_eos_t *eos,
+               const lbm_bc_t *bc, const lbm_opts_t *opts, lbm_handle *out);
+
+/* Free every resource of the run.  Accepts NULL. */
+int lbm_destroy(lbm_handle h);
+
+/* Queue n >= 0 time steps (asynchronous). */
+int lbm_step(lbm_handle h, int64_t n);
+
+/* Wait for queued work and report latched numerical faults. */
+int lbm_sync(lbm_handle h);
+
+/* Steps completed (including queued ones). */
+int64_t lbm_step_count(lbm_handle h);
+
+/* Copy fields out as float64.  For each bit set in mask, in the order RHO,
+ * UX, UY, T, F, the next pointer of dst receives the field (rho/ux/uy:
+ * NF*NX values, the moments of the last step; T: (NS+NF)*NX; F: 9*NF*NX,
+ * post-stream populations).  dst_is_device: 1 if the pointers are device
+ * memory on the run's device, 0 for host memory.  Synchronises. */
+int lbm_fields(lbm_handle h, unsigned mask, double *const *dst, int dst_is_device);
+
+/* Replace the state: post-stream populations f (9*NF*NX) and temperature T
+ * ((NS+NF)*NX), float64, host or device; either may be NULL to keep it.
+ * Sets the step counter to `step` (the counter keys the noisy bottom). */
+int lbm_set_state(lbm_handle h, const double *f, const double *T, int64_t step,
+                  int src_is_device);
+
+/* Heat flux of the last step: mean over x of -lambda_s dT/dy at the heater
+ * bottom (Eq. 36 with rows 0-2, Eq. 39 without its scale factor) and, if
+ * q_top_local is not NULL, the NX local fluxes -lambda_face dT/dy across the
+ * heater/fluid interface.  Synchronises. */
+int lbm_wall_heat_flux(lbm_handle h, double *q_bottom_mean, double *q_top_local);
+
+/* Fraction of fluid sites with rho < (rho_L + rho_V) / 2 after the last step. */
+int lbm_vapour_fraction(lbm_handle h, double *out);
+
+/* Total fluid mass sum(rho) of the last step (float64 accumulation). */
+int lbm_mass(lbm_handle h, double *out);
+
+/* Per-step diagnostics ring: for steps first .. first+count-1 (each still in
+ * the ring), 4 values each: q_bottom_mean, q_top_mean, vapour fraction, mass.
+ * Synchronises.  LBM_E_INVAL if a step is not in the ring. */
+int lbm_series(lbm_handle h, int64_t first, int64_t count, double *out);
+
+/* Per-kernel timing with CUDA events on the run's stream: enable (1) or
+ * disable (0).  While enabled, lbm_step launches kernel by kernel (no graph)
+ * and accumulates the event time of each kernel. */
+int lbm_set_timing(lbm_handle h, int enable);
+
+/* Average milliseconds per launch of the flow kernel, the heat kernel and
+ * the diagnostics kernel since timing was enabled, and the launches
+ * averaged.  Synchronises. */
+int lbm_kernel_times(lbm_handle h, double *avg_ms /* [3] */, int64_t *launches);
+
+/* Kernels queued per time step (for launch accounting). */
+int lbm_kernels_per_step(lbm_handle h);
+
+/* Message of the last error on h (or of the last failed lbm_create when h is
+ * NULL).  Valid until the next call on the same handle. */
+const char *lbm_last_error(lbm_handle h);
+
+/* Static name of a status code. */
+const char *lbm_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBM_GB300_H */

@@ -1,0 +1,82 @@
+// Internal interface between the host runtime (lbm_runtime.cu) and the
+// per-precision kernel translation units (lbm_fp64.cu, lbm_fp32.cu).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lbmgb {
+
+enum { FLAG_PERIODIC_Y = 1, FLAG_ISOTHERMAL = 2, FLAG_FROZEN_FLOW = 4 };
+enum { TOP_WALL = 0, TOP_OUTFLOW = 1 };
+enum { BCM_SPOTS = 0, BCM_NOISE = 1, BCM_SINE = 2 };
+enum { ERRW_PSI = 1, ERRW_NONFINITE_RHO = 2, ERRW_NONFINITE_T = 4 };
+enum { TAG_INIT_NOISE = 1, TAG_BOTTOM_NOISE = 2 };
+enum { SERIES_WIDTH = 4 };
+
+// Everything a kernel needs about the run, precomputed on the host in FP64.
+struct DevParams {
+    int nx, nf, ns, nt;           // columns, fluid rows, heater rows, nt = ns + nf
+    int flags, top_mode, bc_mode;
+    int liquid_rows;
+    double a, b, R, G, kappa, Tc; // Peng-Robinson constants
+    double T_sat, T_b;
+    double rho_L, rho_V, rho_mean, rho_shift;
+    double drho_LV, dtau_LV;      // rho_L - rho_V, tau_L - tau_V (Eq. 5)
+    double g, c_v, cv_chi, lambda_s, rho_c_s;
+    double tau_L, tau_V;
+    double s[9];                  // MRT rates; s7, s8 unused (per-site)
+    double hs[9];                 // 1 - s_k / 2
+    double tau_e_m, tau_s_m;      // 1/s1 - 1/2, 1/s2 - 1/2
+    double varpi12;               // 12 varpi
+    double sign_eps;
+    double c_w_top;
+    double bc_noise, sine_amp, sine_wl;
+    long long sine_t0, sine_t1;
+    double init_noise;
+    double vap_threshold;         // (rho_L + rho_V) / 2
+    unsigned long long seed;
+};
+
+// Device buffers of one run touched by a step (types erased; the kernel
+// translation unit casts them to its storage types).
+struct StepBuffers {
+    const void *f_in;
+    void *f_out;
+    const void *T_in;
+    void *T_out;
+    void *rho, *ux, *uy;     // moments of this step (real type of the path)
+    const double *cw;        // [nx] heater-surface wettability coefficients
+    double *part;            // [2 * lbm blocks] per-block mass and vapour count
+    unsigned *err;           // latched fault bits
+    long long *step;         // device step counter
+    double *series;          // [cap][SERIES_WIDTH]
+    int series_cap;
+    double *q_top;           // [nx] local interface flux of the last step
+    double *last;            // [SERIES_WIDTH] diagnostics of the last step
+    double *scratch;         // reduction scratch for init (>= 1024 doubles)
+};
+
+struct KernelSet {
+    const char *name;
+    size_t f_elem, T_elem, m_elem;      // storage bytes per population, T, moment
+    cudaError_t (*lbm)(const DevParams &, const StepBuffers &, cudaStream_t);
+    cudaError_t (*fd)(const DevParams &, const StepBuffers &, cudaStream_t);
+    cudaError_t (*diag)(const DevParams &, const StepBuffers &, cudaStream_t);
+    // Initial state (Sec. 3.1).  phase 0: initial densities into rho and
+    // their sum into scratch[0]; phase 1 (after the host has fixed rho_mean
+    // and rho_shift): populations into f_out, T_sat into T_out.
+    cudaError_t (*init)(const DevParams &, const StepBuffers &, int phase, cudaStream_t);
+    // float64 post-stream f / T (device) -> storage (f_out / T_out).
+    cudaError_t (*import_state)(const DevParams &, const double *f, const double *T,
+                                const StepBuffers &, cudaStream_t);
+    // storage -> float64 device arrays (any pointer may be NULL).
+    cudaError_t (*export_fields)(const DevParams &, const StepBuffers &, double *rho, double *ux,
+                                 double *uy, double *T, double *f, cudaStream_t);
+    int (*blocks)(const DevParams &);   // number of flow-kernel blocks (partials)
+};
+
+const KernelSet *kernels_fp64();
+const KernelSet *kernels_fp32();
+const KernelSet *kernels_fp16();
+
+}  // namespace lbmgb

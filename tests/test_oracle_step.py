@@ -1,0 +1,164 @@
+"""Whole-step pins of the FP64 oracle: invariants, closed-form limits of the
+heat half, symmetries and the two physics checks the method fixes (flat
+interface coexistence densities and the Laplace law).  No GPU."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1911_10747_gb300 import workloads as W
+
+WL = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+
+
+def uniform_f(rho, nf, nx):
+    return np.broadcast_to(WL[:, None, None] * rho, (9, nf, nx)).copy()
+
+
+def test_uniform_box_stays_at_rest():
+    """Uniform density in a periodic box: the pseudopotential force cancels
+    pairwise (Eq. 11), u = 0 and the populations stay at equilibrium."""
+    cfg = W.periodic_box(8, 8, liquid_rows=8)
+    r = O.OracleRun(cfg)
+    f0 = r.f
+    r.step(50)
+    assert r.err == 0
+    np.testing.assert_array_equal(r.ux, 0.0)
+    np.testing.assert_array_equal(r.uy, 0.0)
+    np.testing.assert_allclose(r.f, f0, rtol=2e-15, atol=0)
+
+
+def test_rk4_amplification_of_a_conduction_mode():
+    """Frozen uniform fluid, T = T_sat + eps cos(k x): Eq. 24 reduces to
+    dT/dt = alpha Lap T with alpha = C_V chi / C_V, the Laplacian (Eq. 28)
+    has eigenvalue 2 (cos k - 1), so each RK4 step (Eq. 25-26) multiplies the
+    amplitude by 1 + z + z^2/2 + z^3/6 + z^4/24, z = 2 alpha (cos k - 1)."""
+    nx, ny = 16, 4
+    cfg = W.periodic_box(nx, ny, liquid_rows=ny, isothermal=False, frozen_flow=True,
+                         cv_chi=0.9, c_v=1.0)
+    r = O.OracleRun(cfg)
+    tsat = 0.86 * r.Tc
+    k = 2 * math.pi * 2 / nx
+    x = np.arange(nx)
+    eps = 1e-3 * tsat
+    r.set_T(np.broadcast_to(tsat + eps * np.cos(k * x), (ny, nx)))
+    z = 2 * (cfg.cv_chi / cfg.c_v) * (math.cos(k) - 1)
+    amp = 1 + z + z ** 2 / 2 + z ** 3 / 6 + z ** 4 / 24
+    r.step(10)
+    expect = tsat + eps * amp ** 10 * np.cos(k * x)
+    np.testing.assert_allclose(r.T, np.broadcast_to(expect, (ny, nx)), rtol=0, atol=1e-15)
+    assert abs(amp) < 1 and amp ** 10 < 0.5  # the mode really decays
+
+
+def test_steady_conduction_through_heater_and_fluid_slab():
+    """Frozen liquid over the heater, bottom T_b, top T_sat: the steady
+    discrete solution is piecewise linear with the flux set by the series sum
+    of the link resistances 1/lambda_face (harmonic means at the jump)."""
+    nx, ns, nf = 4, 6, 6
+    cfg = W.RunConfig(nx=nx, nf=nf, ns=ns, liquid_rows=nf, frozen_flow=True, bc_mode="spots",
+                      init_noise=0.0, lambda_s=3.25, rho_c_s=39.0, T_b_over_Tc=0.96, g=0.0)
+    r = O.OracleRun(cfg)
+    r.step(40000)
+    tc = r.Tc
+    tb, tsat = 0.96 * tc, 0.86 * tc
+    lam = np.array([3.25] * ns + [0.05 * 6.5] * nf + [0.05 * 6.5])  # rows 0..nt, ghost last
+    faces = 2 * lam[:-1] * lam[1:] / (lam[:-1] + lam[1:])
+    q = (tsat - tb) / np.sum(1 / faces)
+    prof = tb + q * np.concatenate([[0.0], np.cumsum(1 / faces)[:-1]])
+    np.testing.assert_allclose(r.T, np.broadcast_to(prof[:, None], (ns + nf, nx)), rtol=0, atol=1e-13)
+    d = r.diagnostics()
+    # Eq. 36 on a linear profile inside the heater is exact: Q = -lambda_s dT/dy = -q
+    assert d["q_bottom"] == pytest.approx(-q, rel=1e-9)
+    assert d["q_top"] == pytest.approx(-q, rel=1e-9)
+
+
+def test_wall_flux_formula_exact_on_quadratic_profile():
+    """Eq. 36 is second-order one-sided: exact for T = T_b + alpha y + beta y^2."""
+    nx, ns, nf = 6, 4, 4
+    cfg = W.RunConfig(nx=nx, nf=nf, ns=ns, liquid_rows=nf, frozen_flow=True, isothermal=True,
+                      init_noise=0.0, lambda_s=3.25, g=0.0)
+    r = O.OracleRun(cfg)
+    tb = 0.96 * r.Tc
+    y = np.arange(ns + nf, dtype=float)[:, None]
+    alpha, beta = -2e-4, 3e-5
+    r.set_T(np.broadcast_to(tb + alpha * y + beta * y ** 2, (ns + nf, nx)))
+    r.step(1)
+    assert r.diagnostics()["q_bottom"] == pytest.approx(-3.25 * alpha, rel=1e-11)
+
+
+def test_mass_is_conserved_with_bounce_back_walls():
+    cfg = W.small_parity()
+    r = O.OracleRun(cfg)
+    r.step(1)
+    m0 = r.diagnostics()["mass"]
+    r.step(300)
+    assert r.err == 0
+    assert r.diagnostics()["mass"] == pytest.approx(m0, rel=1e-12)
+    # and the post-stream populations carry the same mass
+    assert r.f.sum() == pytest.approx(m0, rel=1e-12)
+
+
+def test_column_invariance_without_spots_or_noise():
+    """With every column identical (no spots, no noise, constant bottom) the
+    periodic step keeps the columns bit-identical: each column does the same
+    arithmetic in the same order."""
+    cfg = W.RunConfig(nx=8, nf=24, ns=4, liquid_rows=8, init_noise=0.0, bc_mode="spots",
+                      lambda_s=3.25, rho_c_s=39.0)
+    r = O.OracleRun(cfg)
+    r.step(100)
+    for a in (r.rho, r.ux, r.uy, r.T):
+        assert np.array_equal(a, np.broadcast_to(a[:, :1], a.shape))
+    np.testing.assert_array_equal(r.ux, 0.0)
+
+
+def test_mirror_symmetry():
+    """A mirror-symmetric start (one spot centred on column 0, no noise) stays
+    mirror-symmetric: rho(x) = rho(-x), u_x(x) = -u_x(-x).  A wrong velocity
+    sign, opposite index or neighbour offset breaks it."""
+    nx = 32
+    cfg = W.RunConfig(nx=nx, nf=24, ns=4, liquid_rows=8, init_noise=0.0, bc_mode="spots",
+                      spot_x=(0,), spot_half_width=2, c_w_spot=(-0.5,), lambda_s=3.25,
+                      rho_c_s=39.0, T_b_over_Tc=1.0)
+    r = O.OracleRun(cfg)
+    r.step(200)
+    mir = (-np.arange(nx)) % nx
+    rho, ux, uy, T = r.rho, r.ux, r.uy, r.T
+    assert np.abs(ux).max() > 1e-8  # the spot really drives a flow
+    np.testing.assert_allclose(rho[:, mir], rho, rtol=1e-12)
+    np.testing.assert_allclose(-ux[:, mir], ux, atol=1e-14)
+    np.testing.assert_allclose(uy[:, mir], uy, atol=1e-14)
+    np.testing.assert_allclose(T[:, mir], T, rtol=1e-13)
+
+
+def test_fluctuating_bottom_temperature_statistics():
+    cfg = W.RunConfig(nx=256, nf=4, ns=4, liquid_rows=4, bc_mode="noise", isothermal=True,
+                      frozen_flow=True, bc_noise=0.01, init_noise=0.0)
+    r = O.OracleRun(cfg)
+    tb = 0.96 * r.Tc
+    rows = []
+    for _ in range(4):
+        r.step(1)
+        rows.append(r.T[0].copy())
+    rows = np.array(rows)
+    assert np.all(np.abs(rows / tb - 1) <= 0.01)
+    assert abs((rows / tb - 1).mean()) < 0.002
+    assert (rows / tb - 1).std() == pytest.approx(0.01 / math.sqrt(3), rel=0.1)
+    assert not np.array_equal(rows[0], rows[1])
+
+
+def test_flat_interface_coexistence_matches_maxwell():
+    """Sec. 3.1: at 0.86 Tc the two phases must sit at the Maxwell densities.
+    Pins the improved forcing of Eq. 9 with the default varpi: without the
+    epsilon term (varpi = 0) the vapour density is off by tens of percent."""
+    rl, rv, _ = O.maxwell(0.86)
+    cfg = W.periodic_box(4, 160, liquid_rows=80)
+    r = O.OracleRun(cfg)
+    r.step(10000)
+    rho = r.rho[:, 0]
+    assert r.err == 0
+    assert rho[40] == pytest.approx(rl, rel=0.02)
+    assert rho[120] == pytest.approx(rv, rel=0.02)
+    plain = O.OracleRun(cfg.replace(varpi=0.0))
+    plain.step(10000)
+    assert abs(plain.rho[120, 0] / rv - 1) > 0.2
