@@ -1,0 +1,327 @@
+"""Throughput of the boiling time step on GB300 (MLUPS and HBM roofline).
+
+Workload: 2048 x 2048 fluid sites over a 64-row heater, fluctuating bottom
+temperature (+-1 % per column and step), FP32 shifted populations; one step =
+flow kernel (collision + force + streaming), heat kernel (RK4 of the energy
+equation) and diagnostics kernel.  The FP64 path is measured on the same
+workload and reported beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs under torchrun: independent replicas, one per GPU (the method has
+no exchange between runs), value = all ranks' site updates / max time.
+--impl reference times the FP64 CPU oracle on a bounded sample of the same
+workload (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "boiling step, 2048x2048 fluid + 64 heater rows, noisy bottom, FP32 shifted populations"
+METRIC = "MLUPS (fluid-site updates per second), one GB300"
+# algorithmic bytes per fluid site per step (9 populations read + written,
+# temperature read + written) and per launch of the flow kernel (populations
+# read + written, temperature read)
+ALG_STEP_BYTES = {"fp32": 80, "fp64": 160, "fp16": 44}
+ALG_FLOW_BYTES = {"fp32": 76, "fp64": 152, "fp16": 40}
+PROFILE = os.path.join(ROOT, "profiles", "flow_kernel_2048x2048_fp32.md")
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    with open(os.path.join(ROOT, "paper_1911_10747_gb300", "csrc", "lbm_device.cuh"), "rb") as fh:
+        h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic():
+    """DRAM bytes per flow-kernel launch from the committed ncu summary, or
+    None when absent or taken on a different kernel source."""
+    try:
+        text = open(PROFILE).read()
+    except OSError:
+        return None
+    m = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", text)
+    t = re.search(r"dram_bytes_per_full_launch:\s*([0-9.eE+]+)", text)
+    if not m or not t or m.group(1) != kernel_source_hash():
+        return None
+    return float(t.group(1))
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def oracle_sample(cfg, steps: int):
+    """Time the FP64 oracle as it stands (single thread) on `steps` steps of
+    the workload; returns (MLUPS, seconds)."""
+    from oracle import oracle as O
+    O.build()
+    r = O.OracleRun(cfg.replace(precision="fp64"))
+    t0 = time.perf_counter()
+    r.step(steps)
+    dt = time.perf_counter() - t0
+    return cfg.fluid_sites * steps / dt / 1e6, dt
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    from paper_1911_10747_gb300 import workloads as W
+    cfg = W.large(precision="fp64")
+    for _ in range(args.warmup and 1):
+        oracle_sample(cfg, 1)  # warm caches / page in once
+    mlups, dt = oracle_sample(cfg, max(1, args.steps))
+    sample = f"{max(1, args.steps)} step(s) of the full 2048x2048+64 workload, FP64 oracle, 1 thread"
+    line = {"impl": "reference", "metric": METRIC, "value": mlups, "unit": "MLUPS", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1000 / max(1, args.steps),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded initial density noise and bottom-temperature noise)",
+            "config": {"workload": WORKLOAD.replace("FP32 shifted populations", "FP64 CPU oracle"),
+                       "nx": cfg.nx, "ny_fluid": cfg.nf, "ny_solid": cfg.ns},
+            "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+
+    from paper_1911_10747_gb300 import build as B
+    from paper_1911_10747_gb300 import lbm
+    from paper_1911_10747_gb300 import workloads as W
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if rank == 0 or not os.path.exists(B.LIB):
+        B.build()
+    if ws > 1:
+        torch.distributed.barrier()
+    lbm.load()
+
+    cfg = W.large(precision=args.precision, seed=3 + rank)
+    stream = torch.cuda.Stream(device=dev)
+    run = lbm.Run(cfg, stream=stream.cuda_stream, device=local)
+    kps = run.kernels_per_step()
+    sites = cfg.fluid_sites
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+
+    # warm-up (also builds the two-step graph)
+    run.step(max(args.warmup, 3))
+    run.sync()
+    # ---- timed region: K steps, CUDA events on the run's stream ----
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        run.step(args.steps)
+        e1.record(stream)
+        e1.synchronize()
+    torch.cuda.synchronize(dev)
+    barrier()
+    ms = e0.elapsed_time(e1)
+    run.sync()
+    t_all = torch.tensor([ms], device=dev, dtype=torch.float64)
+    if ws > 1:
+        torch.distributed.all_reduce(t_all, op=torch.distributed.ReduceOp.MAX)
+    ms_max = float(t_all.item())
+    value = ws * sites * args.steps / (ms_max / 1e3) / 1e6
+
+    # ---- per-kernel durations over K more steps (events around each launch) ----
+    run.set_timing(True)
+    run.step(args.steps)
+    kms, nl = run.kernel_times()
+    run.set_timing(False)
+    hbm, peak_kind = peaks()
+    flow_bytes = ALG_FLOW_BYTES[args.precision] * sites
+    achieved = flow_bytes / (kms[0] / 1e3) / 1e9
+    traffic = ncu_traffic() if args.precision == "fp32" else None
+    step_ms = ms_max / args.steps
+    step_achieved = ALG_STEP_BYTES[args.precision] * sites / (step_ms / 1e3) / 1e9
+
+    # ---- end to end through the C ABI with pinned host buffers ----
+    e2e = None
+    if not args.no_e2e:
+        nfl, ntl = cfg.fluid_sites, cfg.temperature_sites
+        st = run.fields(("f", "T"))
+        hf = torch.from_numpy(st["f"].reshape(-1)).pin_memory()
+        hT = torch.from_numpy(st["T"].reshape(-1)).pin_memory()
+        e2e_steps = max(2, min(args.steps, 10))
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for k in range(e2e_steps):
+            run.set_state(hf.data_ptr(), hT.data_ptr(), step=1000 + k, src_is_device=False)
+            run.step(1)
+            run.wall_heat_flux()
+            run.vapour_fraction()
+        dt = time.perf_counter() - t0
+        e2e = {"value": ws * sites * e2e_steps / dt / 1e6, "unit": "MLUPS",
+               "h2d_bytes_per_step": (9 * nfl + ntl) * 8, "d2h_bytes_per_step": 16,
+               "note": "per step: lbm_set_state from pinned float64 host arrays, lbm_step(1), "
+                       "lbm_wall_heat_flux + lbm_vapour_fraction read-back"}
+
+    # ---- FP64 path on the same workload ----
+    fp64 = None
+    if not args.no_fp64 and args.precision != "fp64":
+        run.close()
+        torch.cuda.empty_cache()
+        r64 = lbm.Run(W.large(precision="fp64", seed=3 + rank), stream=stream.cuda_stream, device=local)
+        r64.step(3)
+        r64.sync()
+        k64 = max(4, args.steps // 10)
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        r64.step(k64)
+        a1.record(stream)
+        a1.synchronize()
+        ms64 = a0.elapsed_time(a1) / k64
+        r64.set_timing(True)
+        r64.step(k64)
+        k64ms, _ = r64.kernel_times()
+        r64.close()
+        fp64 = {"value": sites / (ms64 / 1e3) / 1e6, "unit": "MLUPS", "ms_per_step": ms64,
+                "kernel_ms": {"flow": k64ms[0], "heat": k64ms[1], "diag": k64ms[2]},
+                "flow_hbm_frac": ALG_FLOW_BYTES["fp64"] * sites / (k64ms[0] / 1e3) / 1e9 / hbm}
+    else:
+        run.close()
+
+    # ---- CPU baseline: the oracle on a bounded sample (rank 0, N = 1) ----
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        csteps = 2
+        cm, cdt = oracle_sample(W.large(precision="fp64"), csteps)
+        cpu = {"value": cm, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+               "sample": f"{csteps} steps of the full 2048x2048+64 workload in FP64 ({cdt:.1f} s, 1 thread)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": {"fp32": "f32", "fp64": "f64", "fp16": "f16-storage/f32"}[args.precision],
+            "data": "synthetic (seeded initial density noise and bottom-temperature noise)",
+            "config": {"workload": WORKLOAD if args.precision == "fp32" else WORKLOAD.replace("FP32 shifted", args.precision.upper()),
+                       "nx": cfg.nx, "ny_fluid": cfg.nf, "ny_solid": cfg.ns,
+                       "l2": "inputs larger than L2 (populations alone 2 x 151 MB in FP32)",
+                       "parallelism": f"replicas x{ws}" if ws > 1 else "single run"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                         "frac": achieved / hbm, "traffic": traffic, "kernel": "k_flow",
+                         "peak_source": peak_kind,
+                         "step": {"achieved": step_achieved, "frac": step_achieved / hbm,
+                                  "bytes_per_site": ALG_STEP_BYTES[args.precision]}},
+            "kernel_ms": {"flow": kms[0], "heat": kms[1], "diag": kms[2], "launches_timed": nl},
+            "gpu_launches": kps * args.steps,
+            "clocks": clk.summary(),
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+            "fp64": fp64,
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "fp16"])
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

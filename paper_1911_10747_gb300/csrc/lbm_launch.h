@@ -73,6 +73,7 @@ struct KernelSet {
     cudaError_t (*export_fields)(const DevParams &, const StepBuffers &, double *rho, double *ux,
                                  double *uy, double *T, double *f, cudaStream_t);
     int (*blocks)(const DevParams &);   // number of flow-kernel blocks (partials)
+    cudaError_t (*prepare)();           // per-device kernel attributes
 };
 
 const KernelSet *kernels_fp64();

@@ -1,0 +1,531 @@
+// Host runtime behind the C ABI of include/lbm.h: configuration checks,
+// device allocation, the per-step launch sequence (flow kernel, heat kernel,
+// diagnostics kernel), CUDA-graph replay, state import/export and read-back.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "lbm.h"
+#include "lbm_launch.h"
+
+using namespace lbmgb;
+
+namespace {
+thread_local std::string g_create_error;
+
+struct EventPair {
+    cudaEvent_t a = nullptr, b = nullptr;
+};
+}  // namespace
+
+struct lbm_run {
+    DevParams p{};
+    const KernelSet *ks = nullptr;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    bool use_graphs = true;
+    int parity = 0;                 // 0: state in buffers [0], 1: in [1]
+    int64_t steps = 0;
+    void *f[2] = {nullptr, nullptr};
+    void *T[2] = {nullptr, nullptr};
+    void *rho = nullptr, *ux = nullptr, *uy = nullptr;
+    double *cw = nullptr, *part = nullptr, *series = nullptr, *q_top = nullptr, *last = nullptr;
+    double *scratch = nullptr;
+    double *stage = nullptr;        // float64 staging for read-back / import
+    size_t stage_elems = 0;
+    unsigned *err = nullptr;
+    long long *dstep = nullptr;
+    int series_cap = 4096;
+    int nblk = 0;
+    cudaGraphExec_t graph = nullptr;
+    bool timing = false;
+    std::vector<EventPair> ev[3];
+    double t_ms[3] = {0, 0, 0};
+    int64_t t_count = 0;
+    std::string msg;
+};
+
+static int fail(lbm_run *h, int code, const std::string &m) {
+    if (h) h->msg = m; else g_create_error = m;
+    return code;
+}
+static int cuda_fail(lbm_run *h, cudaError_t e, const char *where) {
+    return fail(h, LBM_E_CUDA, std::string(where) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")");
+}
+#define CK(h, call)                                     \
+    do {                                                \
+        cudaError_t e_ = (call);                        \
+        if (e_ != cudaSuccess) return cuda_fail(h, e_, #call); \
+    } while (0)
+
+static StepBuffers buffers(lbm_run *h, int par) {
+    StepBuffers b{};
+    b.f_in = h->f[par];
+    b.f_out = h->f[par ^ 1];
+    b.T_in = h->T[par];
+    b.T_out = h->T[par ^ 1];
+    b.rho = h->rho;
+    b.ux = h->ux;
+    b.uy = h->uy;
+    b.cw = h->cw;
+    b.part = h->part;
+    b.err = h->err;
+    b.step = h->dstep;
+    b.series = h->series;
+    b.series_cap = h->series_cap;
+    b.q_top = h->q_top;
+    b.last = h->last;
+    b.scratch = h->scratch;
+    return b;
+}
+// Buffers describing the current state as the "output" side (init / import)
+// and as the "input" side (export).
+static StepBuffers state_as_out(lbm_run *h) { return buffers(h, h->parity ^ 1); }
+static StepBuffers state_as_in(lbm_run *h) { return buffers(h, h->parity); }
+
+static void free_all(lbm_run *h) {
+    if (h->graph) cudaGraphExecDestroy(h->graph);
+    for (int k = 0; k < 2; k++) {
+        cudaFree(h->f[k]);
+        cudaFree(h->T[k]);
+    }
+    cudaFree(h->rho); cudaFree(h->ux); cudaFree(h->uy);
+    cudaFree(h->cw); cudaFree(h->part); cudaFree(h->series); cudaFree(h->q_top); cudaFree(h->last);
+    cudaFree(h->scratch); cudaFree(h->stage); cudaFree(h->err); cudaFree(h->dstep);
+    for (auto &v : h->ev)
+        for (auto &e : v) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+}
+
+// Host-side constants, evaluated in FP64 in the order the formulas are written
+// (the library is built with -ffp-contract=off).
+static int fill_params(const lbm_domain_t *d, const lbm_heater_t *ht, const lbm_eos_t *eo, const lbm_bc_t *bc,
+                       DevParams &p, std::string &why) {
+    if (d->nx < 1) { why = "domain.nx must be >= 1"; return 0; }
+    if (d->ny_fluid < 2) { why = "domain.ny_fluid must be >= 2"; return 0; }
+    if (d->liquid_rows < 0 || d->liquid_rows > d->ny_fluid) { why = "domain.liquid_rows out of range"; return 0; }
+    if (d->top_mode != LBM_TOP_WALL && d->top_mode != LBM_TOP_OUTFLOW) { why = "domain.top_mode invalid"; return 0; }
+    if (d->flags & ~7) { why = "domain.flags has unknown bits"; return 0; }
+    const bool py = (d->flags & LBM_PERIODIC_Y) != 0;
+    if (py && ht->ny_solid != 0) { why = "periodic-y test mode needs heater.ny_solid = 0"; return 0; }
+    if (!py && ht->ny_solid < 3) { why = "heater.ny_solid must be >= 3 (bottom flux uses rows 0..2)"; return 0; }
+    if ((double)d->nx * (double)(d->ny_fluid + ht->ny_solid) > 2.0e9) { why = "domain too large for 32-bit row indexing"; return 0; }
+    if (!(eo->G < 0)) { why = "eos.G must be negative (psi real for p_EOS < rho/3)"; return 0; }
+    if (!(eo->a > 0 && eo->b > 0 && eo->R > 0)) { why = "eos.a, eos.b, eos.R must be positive"; return 0; }
+    if (!(eo->rho_L > eo->rho_V && eo->rho_V > 0)) { why = "eos needs rho_L > rho_V > 0"; return 0; }
+    if (!(d->nu_L > 0 && d->nu_V > 0)) { why = "viscosities must be positive"; return 0; }
+    for (int k = 0; k < 9; k++)
+        if (!(d->s[k] > 0 && d->s[k] < 2)) { why = "MRT rates must lie in (0, 2)"; return 0; }
+    if (!(d->c_v > 0 && d->cv_chi > 0)) { why = "c_v and cv_chi must be positive"; return 0; }
+    if (!py && !(ht->lambda_s > 0 && ht->rho_c_s > 0)) { why = "heater lambda_s and rho_c_s must be positive"; return 0; }
+    if (bc->mode < 0 || bc->mode > 2) { why = "bc.mode invalid"; return 0; }
+    if (bc->n_spots < 0 || bc->n_spots > 8) { why = "bc.n_spots must be in 0..8"; return 0; }
+    if (bc->mode == LBM_BC_SINE && !(bc->sine_wavelength > 0)) { why = "bc.sine_wavelength must be positive"; return 0; }
+    p.nx = d->nx;
+    p.nf = d->ny_fluid;
+    p.ns = ht->ny_solid;
+    p.nt = p.ns + p.nf;
+    p.flags = d->flags;
+    p.top_mode = d->top_mode;
+    p.bc_mode = bc->mode;
+    p.liquid_rows = d->liquid_rows;
+    p.a = eo->a; p.b = eo->b; p.R = eo->R; p.G = eo->G;
+    p.Tc = (0.0778 * eo->a) / ((0.45724 * eo->b) * eo->R);
+    p.kappa = 0.37464 + 1.54226 * eo->omega - 0.26992 * eo->omega * eo->omega;
+    p.T_sat = eo->T_sat_over_Tc * p.Tc;
+    p.T_b = bc->T_b_over_Tc * p.Tc;
+    p.rho_L = eo->rho_L; p.rho_V = eo->rho_V;
+    p.rho_mean = d->rho_mean;
+    p.g = d->g; p.c_v = d->c_v; p.cv_chi = d->cv_chi;
+    p.lambda_s = ht->lambda_s; p.rho_c_s = ht->rho_c_s;
+    p.tau_L = 3.0 * d->nu_L + 0.5;
+    p.tau_V = 3.0 * d->nu_V + 0.5;
+    p.drho_LV = eo->rho_L - eo->rho_V;
+    p.dtau_LV = p.tau_L - p.tau_V;
+    for (int k = 0; k < 9; k++) {
+        p.s[k] = d->s[k];
+        p.hs[k] = 1.0 - 0.5 * d->s[k];
+    }
+    p.tau_e_m = 1.0 / d->s[1] - 0.5;
+    p.tau_s_m = 1.0 / d->s[2] - 0.5;
+    p.varpi12 = 12.0 * d->varpi;
+    p.sign_eps = d->sign_eps;
+    p.c_w_top = bc->c_w_top;
+    p.bc_noise = bc->noise_amp;
+    p.sine_amp = bc->sine_amp_over_Tc * p.Tc;
+    p.sine_wl = bc->sine_wavelength;
+    p.sine_t0 = bc->sine_t0;
+    p.sine_t1 = bc->sine_t1;
+    p.init_noise = d->init_noise;
+    p.vap_threshold = 0.5 * (eo->rho_L + eo->rho_V);
+    p.seed = d->seed;
+    return 1;
+}
+
+static int ensure_stage(lbm_run *h, size_t elems) {
+    if (h->stage_elems >= elems) return LBM_OK;
+    cudaFree(h->stage);
+    h->stage = nullptr;
+    h->stage_elems = 0;
+    if (cudaMalloc(&h->stage, elems * sizeof(double)) != cudaSuccess) return fail(h, LBM_E_NOMEM, "staging allocation failed");
+    h->stage_elems = elems;
+    return LBM_OK;
+}
+
+static int check_err_word(lbm_run *h) {
+    unsigned e = 0;
+    CK(h, cudaMemcpyAsync(&e, h->err, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    if (e) {
+        std::string m = "numerical fault latched by the kernels:";
+        if (e & ERRW_PSI) m += " negative pseudopotential radicand;";
+        if (e & ERRW_NONFINITE_RHO) m += " non-finite density;";
+        if (e & ERRW_NONFINITE_T) m += " non-finite temperature;";
+        return fail(h, LBM_E_NUMERIC, m);
+    }
+    return LBM_OK;
+}
+
+extern "C" {
+
+const char *lbm_status_string(int s) {
+    switch (s) {
+        case LBM_OK: return "LBM_OK";
+        case LBM_E_INVAL: return "LBM_E_INVAL";
+        case LBM_E_NOMEM: return "LBM_E_NOMEM";
+        case LBM_E_CUDA: return "LBM_E_CUDA";
+        case LBM_E_NUMERIC: return "LBM_E_NUMERIC";
+        case LBM_E_TIMEOUT: return "LBM_E_TIMEOUT";
+        case LBM_E_STATE: return "LBM_E_STATE";
+        default: return "unknown status";
+    }
+}
+
+const char *lbm_last_error(lbm_handle h) { return h ? h->msg.c_str() : g_create_error.c_str(); }
+
+int lbm_create(const lbm_domain_t *domain, const lbm_heater_t *heater, const lbm_eos_t *eos, const lbm_bc_t *bc,
+               const lbm_opts_t *opts, lbm_handle *out) {
+    if (!out) return fail(nullptr, LBM_E_INVAL, "out is NULL");
+    *out = nullptr;
+    if (!domain || !heater || !eos || !bc || !opts) return fail(nullptr, LBM_E_INVAL, "a configuration struct is NULL");
+    lbm_run *h = new (std::nothrow) lbm_run();
+    if (!h) return fail(nullptr, LBM_E_NOMEM, "host allocation failed");
+    std::string why;
+    if (!fill_params(domain, heater, eos, bc, h->p, why)) {
+        delete h;
+        return fail(nullptr, LBM_E_INVAL, why);
+    }
+    switch (opts->precision) {
+        case LBM_FP64: h->ks = kernels_fp64(); break;
+        case LBM_FP32: h->ks = kernels_fp32(); break;
+        case LBM_FP16: h->ks = kernels_fp16(); break;
+        default: delete h; return fail(nullptr, LBM_E_INVAL, "opts.precision invalid");
+    }
+    h->device = opts->device;
+    h->use_graphs = opts->use_graphs != 0;
+    if (opts->series_capacity < 0) { delete h; return fail(nullptr, LBM_E_INVAL, "opts.series_capacity negative"); }
+    if (opts->series_capacity > 0) h->series_cap = opts->series_capacity;
+    int rc = LBM_OK;
+    auto bad = [&](int code) { rc = code; free_all(h); std::string m = h->msg; delete h; g_create_error = m; return rc; };
+    cudaError_t e = cudaSetDevice(h->device);
+    if (e != cudaSuccess) { cuda_fail(h, e, "cudaSetDevice"); return bad(LBM_E_CUDA); }
+    if (opts->stream) {
+        h->stream = (cudaStream_t)opts->stream;
+    } else {
+        e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) { cuda_fail(h, e, "cudaStreamCreate"); return bad(LBM_E_CUDA); }
+        h->own_stream = true;
+    }
+    if ((e = h->ks->prepare()) != cudaSuccess) { cuda_fail(h, e, "kernel attributes"); return bad(LBM_E_CUDA); }
+    const DevParams &p = h->p;
+    const size_t nfl = (size_t)p.nx * p.nf, ntl = (size_t)p.nx * p.nt;
+    h->nblk = h->ks->blocks(p);
+    struct A { void **ptr; size_t bytes; } allocs[] = {
+        {&h->f[0], 9 * nfl * h->ks->f_elem}, {&h->f[1], 9 * nfl * h->ks->f_elem},
+        {&h->T[0], ntl * h->ks->T_elem}, {&h->T[1], ntl * h->ks->T_elem},
+        {&h->rho, nfl * h->ks->m_elem}, {&h->ux, nfl * h->ks->m_elem}, {&h->uy, nfl * h->ks->m_elem},
+        {(void **)&h->cw, (size_t)p.nx * sizeof(double)}, {(void **)&h->part, 2 * (size_t)h->nblk * sizeof(double)},
+        {(void **)&h->series, (size_t)h->series_cap * SERIES_WIDTH * sizeof(double)},
+        {(void **)&h->q_top, (size_t)p.nx * sizeof(double)}, {(void **)&h->last, SERIES_WIDTH * sizeof(double)},
+        {(void **)&h->scratch, 1024 * sizeof(double)}, {(void **)&h->err, sizeof(unsigned)},
+        {(void **)&h->dstep, sizeof(long long)},
+    };
+    for (auto &a : allocs) {
+        e = cudaMalloc(a.ptr, a.bytes);
+        if (e != cudaSuccess) {
+            fail(h, LBM_E_NOMEM, std::string("device allocation of ") + std::to_string(a.bytes) + " bytes failed: " + cudaGetErrorString(e));
+            return bad(LBM_E_NOMEM);
+        }
+    }
+    // heater-surface wettability per column (nucleate spots: columns within
+    // spot_half_width periodic distance of a spot centre, Sec. 4.1)
+    std::vector<double> cwh(p.nx);
+    for (int x = 0; x < p.nx; x++) {
+        double c = bc->c_w_base;
+        for (int k = 0; k < bc->n_spots; k++) {
+            int dx = ((x - bc->spot_x[k]) % p.nx + p.nx) % p.nx;
+            if (dx > p.nx - dx) dx = p.nx - dx;
+            if (dx <= bc->spot_half_width) c = bc->c_w_spot[k];
+        }
+        cwh[x] = c;
+    }
+    long long zero = 0;
+    unsigned zu = 0;
+    if ((e = cudaMemcpyAsync(h->cw, cwh.data(), p.nx * sizeof(double), cudaMemcpyHostToDevice, h->stream)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(h->dstep, &zero, sizeof(zero), cudaMemcpyHostToDevice, h->stream)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(h->err, &zu, sizeof(zu), cudaMemcpyHostToDevice, h->stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(h->last, 0, SERIES_WIDTH * sizeof(double), h->stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(h->q_top, 0, p.nx * sizeof(double), h->stream)) != cudaSuccess) {
+        cuda_fail(h, e, "initial copies");
+        return bad(LBM_E_CUDA);
+    }
+    // initial state (Sec. 3.1): densities, their mean, then populations and T
+    StepBuffers b = state_as_out(h);
+    if ((e = h->ks->init(h->p, b, 0, h->stream)) != cudaSuccess) { cuda_fail(h, e, "init kernels"); return bad(LBM_E_CUDA); }
+    double sum = 0;
+    if ((e = cudaMemcpyAsync(&sum, h->scratch, sizeof(double), cudaMemcpyDeviceToHost, h->stream)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(h->stream)) != cudaSuccess) {
+        cuda_fail(h, e, "initial density read-back");
+        return bad(LBM_E_CUDA);
+    }
+    if (!(h->p.rho_mean > 0)) h->p.rho_mean = sum / (double)nfl;
+    h->p.rho_shift = (opts->rho_shift > 0) ? opts->rho_shift : h->p.rho_mean;
+    if ((e = h->ks->init(h->p, b, 1, h->stream)) != cudaSuccess) { cuda_fail(h, e, "init kernels"); return bad(LBM_E_CUDA); }
+    if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) { cuda_fail(h, e, "init sync"); return bad(LBM_E_CUDA); }
+    *out = h;
+    return LBM_OK;
+}
+
+int lbm_destroy(lbm_handle h) {
+    if (!h) return LBM_OK;
+    cudaSetDevice(h->device);
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    free_all(h);
+    delete h;
+    return LBM_OK;
+}
+
+static int launch_step(lbm_run *h, bool timed) {
+    StepBuffers b = buffers(h, h->parity);
+    cudaError_t e;
+    cudaError_t (*fn[3])(const DevParams &, const StepBuffers &, cudaStream_t) = {h->ks->lbm, h->ks->fd, h->ks->diag};
+    for (int k = 0; k < 3; k++) {
+        EventPair ep;
+        if (timed) {
+            CK(h, cudaEventCreate(&ep.a));
+            CK(h, cudaEventCreate(&ep.b));
+            CK(h, cudaEventRecord(ep.a, h->stream));
+        }
+        if ((e = fn[k](h->p, b, h->stream)) != cudaSuccess) return cuda_fail(h, e, k == 0 ? "flow kernel" : (k == 1 ? "heat kernel" : "diagnostics kernel"));
+        if (timed) {
+            CK(h, cudaEventRecord(ep.b, h->stream));
+            h->ev[k].push_back(ep);
+        }
+    }
+    h->parity ^= 1;
+    return LBM_OK;
+}
+
+static int build_graph(lbm_run *h) {
+    cudaGraph_t g = nullptr;
+    CK(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    int rc = launch_step(h, false);
+    if (rc == LBM_OK) rc = launch_step(h, false);
+    cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+    if (rc != LBM_OK) { if (g) cudaGraphDestroy(g); return rc; }
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&h->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) { h->graph = nullptr; return cuda_fail(h, e, "cudaGraphInstantiate"); }
+    return LBM_OK;
+}
+
+int lbm_step(lbm_handle h, int64_t n) {
+    if (!h) return LBM_E_INVAL;
+    if (n < 0) return fail(h, LBM_E_INVAL, "negative step count");
+    CK(h, cudaSetDevice(h->device));
+    int rc;
+    const bool graphs = h->use_graphs && !h->timing && h->stream != nullptr;
+    while (n > 0) {
+        if (graphs && n >= 2 && h->parity == 0) {
+            if (!h->graph && (rc = build_graph(h)) != LBM_OK) return rc;
+            CK(h, cudaGraphLaunch(h->graph, h->stream));
+            n -= 2;
+            h->steps += 2;
+            continue;
+        }
+        if ((rc = launch_step(h, h->timing)) != LBM_OK) return rc;
+        n -= 1;
+        h->steps += 1;
+    }
+    return LBM_OK;
+}
+
+int lbm_sync(lbm_handle h) {
+    if (!h) return LBM_E_INVAL;
+    CK(h, cudaSetDevice(h->device));
+    CK(h, cudaStreamSynchronize(h->stream));
+    return check_err_word(h);
+}
+
+int64_t lbm_step_count(lbm_handle h) { return h ? h->steps : -1; }
+
+int lbm_fields(lbm_handle h, unsigned mask, double *const *dst, int dst_is_device) {
+    if (!h) return LBM_E_INVAL;
+    if (mask & ~31u) return fail(h, LBM_E_INVAL, "unknown field bits");
+    if (mask && !dst) return fail(h, LBM_E_INVAL, "dst is NULL");
+    CK(h, cudaSetDevice(h->device));
+    const size_t nfl = (size_t)h->p.nx * h->p.nf, ntl = (size_t)h->p.nx * h->p.nt;
+    const size_t sizes[5] = {nfl, nfl, nfl, ntl, 9 * nfl};
+    double *dptr[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    size_t off[5] = {0, 0, 0, 0, 0}, total = 0;
+    int j = 0;
+    for (int k = 0; k < 5; k++) {
+        if (!(mask & (1u << k))) continue;
+        if (!dst[j]) return fail(h, LBM_E_INVAL, "a destination pointer is NULL");
+        off[k] = total;
+        total += sizes[k];
+        j++;
+    }
+    int rc;
+    if (!dst_is_device && total) {
+        if ((rc = ensure_stage(h, total)) != LBM_OK) return rc;
+    }
+    j = 0;
+    for (int k = 0; k < 5; k++) {
+        if (!(mask & (1u << k))) continue;
+        dptr[k] = dst_is_device ? dst[j] : h->stage + off[k];
+        j++;
+    }
+    StepBuffers b = state_as_in(h);
+    cudaError_t e = h->ks->export_fields(h->p, b, dptr[0], dptr[1], dptr[2], dptr[3], dptr[4], h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "export kernel");
+    if (!dst_is_device) {
+        j = 0;
+        for (int k = 0; k < 5; k++) {
+            if (!(mask & (1u << k))) continue;
+            CK(h, cudaMemcpyAsync(dst[j], dptr[k], sizes[k] * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+            j++;
+        }
+    }
+    CK(h, cudaStreamSynchronize(h->stream));
+    return check_err_word(h);
+}
+
+int lbm_set_state(lbm_handle h, const double *f, const double *T, int64_t step, int src_is_device) {
+    if (!h) return LBM_E_INVAL;
+    if (step < 0) return fail(h, LBM_E_INVAL, "negative step");
+    CK(h, cudaSetDevice(h->device));
+    const size_t nfl = (size_t)h->p.nx * h->p.nf, ntl = (size_t)h->p.nx * h->p.nt;
+    const double *df = f, *dT = T;
+    int rc;
+    if (!src_is_device && (f || T)) {
+        if ((rc = ensure_stage(h, 9 * nfl + ntl)) != LBM_OK) return rc;
+        if (f) {
+            CK(h, cudaMemcpyAsync(h->stage, f, 9 * nfl * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+            df = h->stage;
+        }
+        if (T) {
+            CK(h, cudaMemcpyAsync(h->stage + 9 * nfl, T, ntl * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+            dT = h->stage + 9 * nfl;
+        }
+    }
+    // write into the current state buffers
+    StepBuffers b = buffers(h, h->parity ^ 1);
+    b.f_out = h->f[h->parity];
+    b.T_out = h->T[h->parity];
+    if (df || dT) {
+        cudaError_t e = h->ks->import_state(h->p, df, dT, b, h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "import kernel");
+    }
+    long long s = step;
+    CK(h, cudaMemcpyAsync(h->dstep, &s, sizeof(s), cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));  // host sources may be freed after return
+    h->steps = step;
+    return LBM_OK;
+}
+
+int lbm_wall_heat_flux(lbm_handle h, double *q_bottom_mean, double *q_top_local) {
+    if (!h) return LBM_E_INVAL;
+    CK(h, cudaSetDevice(h->device));
+    double last[SERIES_WIDTH];
+    CK(h, cudaMemcpyAsync(last, h->last, sizeof(last), cudaMemcpyDeviceToHost, h->stream));
+    if (q_top_local) CK(h, cudaMemcpyAsync(q_top_local, h->q_top, h->p.nx * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    if (q_bottom_mean) *q_bottom_mean = last[0];
+    return check_err_word(h);
+}
+
+static int read_last(lbm_run *h, int k, double *out) {
+    if (!h || !out) return LBM_E_INVAL;
+    CK(h, cudaSetDevice(h->device));
+    double last[SERIES_WIDTH];
+    CK(h, cudaMemcpyAsync(last, h->last, sizeof(last), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    *out = last[k];
+    return check_err_word(h);
+}
+
+int lbm_vapour_fraction(lbm_handle h, double *out) { return read_last(h, 2, out); }
+int lbm_mass(lbm_handle h, double *out) { return read_last(h, 3, out); }
+
+int lbm_series(lbm_handle h, int64_t first, int64_t count, double *out) {
+    if (!h) return LBM_E_INVAL;
+    if (count < 0 || (count > 0 && !out)) return fail(h, LBM_E_INVAL, "bad count or NULL out");
+    if (count == 0) return LBM_OK;
+    if (first < 0 || first + count > h->steps || h->steps - first > h->series_cap)
+        return fail(h, LBM_E_INVAL, "requested steps are not in the diagnostics ring");
+    CK(h, cudaSetDevice(h->device));
+    for (int64_t k = 0; k < count;) {
+        const int64_t slot = (first + k) % h->series_cap;
+        const int64_t run = std::min<int64_t>(count - k, h->series_cap - slot);
+        CK(h, cudaMemcpyAsync(out + k * SERIES_WIDTH, h->series + slot * SERIES_WIDTH, run * SERIES_WIDTH * sizeof(double),
+                              cudaMemcpyDeviceToHost, h->stream));
+        k += run;
+    }
+    CK(h, cudaStreamSynchronize(h->stream));
+    return check_err_word(h);
+}
+
+int lbm_set_timing(lbm_handle h, int enable) {
+    if (!h) return LBM_E_INVAL;
+    CK(h, cudaSetDevice(h->device));
+    CK(h, cudaStreamSynchronize(h->stream));
+    for (auto &v : h->ev) {
+        for (auto &e : v) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
+        v.clear();
+    }
+    for (double &t : h->t_ms) t = 0;
+    h->t_count = 0;
+    h->timing = enable != 0;
+    return LBM_OK;
+}
+
+int lbm_kernel_times(lbm_handle h, double *avg_ms, int64_t *launches) {
+    if (!h || !avg_ms) return LBM_E_INVAL;
+    CK(h, cudaSetDevice(h->device));
+    CK(h, cudaStreamSynchronize(h->stream));
+    for (int k = 0; k < 3; k++) {
+        for (auto &e : h->ev[k]) {
+            float ms = 0;
+            CK(h, cudaEventElapsedTime(&ms, e.a, e.b));
+            h->t_ms[k] += ms;
+            cudaEventDestroy(e.a);
+            cudaEventDestroy(e.b);
+        }
+        if (k == 0) h->t_count += (int64_t)h->ev[0].size();
+        h->ev[k].clear();
+    }
+    for (int k = 0; k < 3; k++) avg_ms[k] = h->t_count ? h->t_ms[k] / (double)h->t_count : 0.0;
+    if (launches) *launches = h->t_count;
+    return LBM_OK;
+}
+
+int lbm_kernels_per_step(lbm_handle h) { return h ? 3 : 0; }
+
+}  // extern "C"

@@ -1,0 +1,145 @@
+"""GPU path (C ABI) against the FP64 oracle on the same seeded inputs.
+
+FP64 path: every field within 1e-12 relative per site (u relative to its
+maximum) after the steps run, and the per-step diagnostics series within
+1e-12.  The sizes span several tiles of both kernels and ragged tails."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1911_10747_gb300 import lbm
+from paper_1911_10747_gb300 import workloads as W
+
+from gpu_util import field_errors, rel_err, run_both
+
+pytestmark = pytest.mark.gpu
+TOL64 = 1e-12
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_1911_10747_gb300 import build
+    build.build()
+    lbm.load()
+
+
+def check_fp64(g, o, steps):
+    errs = field_errors(g, o)
+    assert all(v <= TOL64 for v in errs.values()), errs
+    ser = g.series(0, steps)
+    d = o.diagnostics()
+    last = ser[-1]
+    assert last[0] == pytest.approx(d["q_bottom"], rel=TOL64, abs=1e-15)
+    assert last[1] == pytest.approx(d["q_top"], rel=TOL64, abs=1e-15)
+    assert last[2] == pytest.approx(d["vapour_fraction"], abs=1e-15)
+    assert last[3] == pytest.approx(d["mass"], rel=TOL64)
+    return errs
+
+
+def test_fp64_parity_small_boiling_case_200_steps():
+    """64 x 96 fluid over 8 heater rows, three nucleate spots, 200 steps."""
+    cfg = W.small_parity().replace(rho_mean=2.42)
+    g, o = run_both(cfg, 200)
+    errs = check_fp64(g, o, 200)
+    print("fp64 200-step errors", errs)
+    # the flow really moved and the heater really heated
+    assert np.abs(o.uy).max() > 1e-4
+    assert o.diagnostics()["q_bottom"] != 0.0
+
+
+def test_fp64_series_matches_every_step():
+    cfg = W.small_parity().replace(rho_mean=2.42)
+    g = lbm.Run(cfg)
+    o = O.OracleRun(cfg)
+    ser = []
+    for _ in range(30):
+        o.step(1)
+        d = o.diagnostics()
+        ser.append([d["q_bottom"], d["q_top"], d["vapour_fraction"], d["mass"]])
+    g.step(30)
+    got = g.series(0, 30)
+    np.testing.assert_allclose(got, np.array(ser), rtol=TOL64, atol=1e-15)
+
+
+def test_fp64_parity_computed_mean_density():
+    """rho_mean left to each side (its own reduction of the initial density)."""
+    cfg = W.small_parity()
+    g, o = run_both(cfg, 50)
+    check_fp64(g, o, 50)
+
+
+@pytest.mark.parametrize("kw", [
+    dict(nx=37, nf=45, ns=5, liquid_rows=15, bc_mode="noise", spot_x=(), c_w_spot=()),
+    dict(nx=70, nf=33, ns=3, liquid_rows=11, bc_mode="spots", spot_x=(3, 40, 69), spot_half_width=2,
+         c_w_spot=(-0.9, -0.8, -0.7), top_mode="outflow"),
+    dict(nx=33, nf=40, ns=9, liquid_rows=12, bc_mode="sine", sine_t0=3, sine_t1=40, sine_wavelength=33.0,
+         spot_x=(), c_w_spot=()),
+])
+def test_fp64_parity_ragged_domains_and_bc_modes(kw):
+    cfg = W.small_parity().replace(rho_mean=2.3, **kw)
+    g, o = run_both(cfg, 60)
+    check_fp64(g, o, 60)
+
+
+def test_fp64_parity_periodic_box_and_test_modes():
+    cfg = W.periodic_box(24, 40, liquid_rows=20, init_noise=1e-3)
+    g, o = run_both(cfg, 80)
+    errs = field_errors(g, o)
+    assert all(v <= TOL64 for v in errs.values()), errs
+    cfg = W.periodic_box(16, 8, liquid_rows=8, isothermal=False, frozen_flow=True, init_noise=1e-3)
+    g, o = run_both(cfg, 20)
+    errs = field_errors(g, o)
+    assert all(v <= TOL64 for v in errs.values()), errs
+
+
+def test_fp64_frozen_flow_conduction_mode():
+    cfg = W.small_parity().replace(frozen_flow=True, rho_mean=2.42)
+    g, o = run_both(cfg, 40)
+    check_fp64(g, o, 40)
+
+
+def test_graph_replay_is_bitwise_identical_to_plain_launches():
+    cfg = W.small_parity().replace(bc_mode="noise", spot_x=(), c_w_spot=())
+    a = lbm.Run(cfg, use_graphs=True).step(21)
+    b = lbm.Run(cfg, use_graphs=False).step(21)
+    fa, fb = a.fields(("rho", "ux", "uy", "T", "f")), b.fields(("rho", "ux", "uy", "T", "f"))
+    for k in fa:
+        assert np.array_equal(fa[k], fb[k]), k
+    assert np.array_equal(a.series(0, 21), b.series(0, 21))
+
+
+def test_set_state_round_trip_and_restart_is_exact():
+    cfg = W.small_parity().replace(bc_mode="noise", spot_x=(), c_w_spot=(), rho_mean=2.42)
+    a = lbm.Run(cfg).step(10)
+    st = a.fields(("f", "T"))
+    a.step(10)
+    b = lbm.Run(cfg)
+    b.set_state(st["f"], st["T"], step=10)
+    back = b.fields(("f", "T"))
+    assert np.array_equal(back["f"], st["f"]) and np.array_equal(back["T"], st["T"])
+    b.step(10)
+    fa, fb = a.fields(("rho", "T", "f")), b.fields(("rho", "T", "f"))
+    for k in fa:
+        assert np.array_equal(fa[k], fb[k]), k
+
+
+def test_full_size_domain_fp64_against_oracle():
+    """The 2048 x 2048 + 64 domain of the throughput run, two steps, FP64."""
+    cfg = W.large(precision="fp64").replace(rho_mean=2.41)
+    g, o = run_both(cfg, 2)
+    errs = field_errors(g, o)
+    assert all(v <= TOL64 for v in errs.values()), errs
+
+
+def test_numerical_fault_is_reported():
+    """A population state whose density exceeds 1/b makes the EOS radicand
+    negative: the kernels latch it and the next sync returns LBM_E_NUMERIC."""
+    cfg = W.small_parity()
+    g = lbm.Run(cfg)
+    f = g.fields(("f",))["f"]
+    f[:, 10, 10] *= 3.0
+    g.set_state(f, None, step=0)
+    g.step(1)
+    with pytest.raises(lbm.LbmError) as ei:
+        g.sync()
+    assert ei.value.code == lbm.LBM_E_NUMERIC
