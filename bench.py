@@ -213,7 +213,7 @@ def run_ours(args):
 
     # ---- per-kernel durations over K more steps (events around each launch) ----
     run.set_timing(True)
-    run.step(args.steps)
+    run.step(min(args.steps, 200))
     kms, nl = run.kernel_times()
     run.set_timing(False)
     hbm, peak_kind = peaks()
@@ -252,7 +252,7 @@ def run_ours(args):
         r64 = lbm.Run(W.large(precision="fp64", seed=3 + rank), stream=stream.cuda_stream, device=local)
         r64.step(3)
         r64.sync()
-        k64 = max(4, args.steps // 10)
+        k64 = max(4, min(100, args.steps // 10))
         a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a0.record(stream)
         r64.step(k64)
@@ -308,8 +308,8 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "fp16"])
     ap.add_argument("--no-fp64", action="store_true")

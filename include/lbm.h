@@ -191,6 +191,22 @@ int lbm_kernel_times(lbm_handle h, double *avg_ms /* [3] */, int64_t *launches);
 /* Kernels queued per time step (for launch accounting). */
 int lbm_kernels_per_step(lbm_handle h);
 
+/* Launch-shape variants.  The library compiles several tilings of the flow
+ * kernel (kind 0) and the heat kernel (kind 1); every variant computes the
+ * same per-site arithmetic.  lbm_variants reports how many there are and
+ * which one is in use; lbm_variant_name returns a static name ("" for a bad
+ * index); lbm_select_variants picks a pair (drops the captured graph). */
+int lbm_variants(lbm_handle h, int kind, int *count, int *selected);
+const char *lbm_variant_name(lbm_handle h, int kind, int index);
+int lbm_select_variants(lbm_handle h, int flow, int heat);
+
+/* Autotuner: time `iters` launches of every flow variant and every heat
+ * variant on the run's current state and keep the fastest pair.  The state,
+ * the step counter and the diagnostics are left unchanged (the kernels write
+ * only buffers that the next step overwrites).  best_ms (nullable, [2])
+ * receives the winning average milliseconds per launch.  Synchronises. */
+int lbm_autotune(lbm_handle h, int iters, double *best_ms);
+
 /* Message of the last error on h (or of the last failed lbm_create when h is
  * NULL).  Valid until the next call on the same handle. */
 const char *lbm_last_error(lbm_handle h);

@@ -374,6 +374,11 @@ static void lbm_part(orc_run *r)
                     double t = WF[i] * r->psi[(size_t)yn * nx + xn];
                     if (EX[i]) sx += EX[i] * t;
                     if (EY[i]) sy += EY[i] * t;
+                } else if (yn >= nf && p->top_mode == TOP_OUTFLOW) {
+                    /* reading: open top, psi has zero normal gradient */
+                    double t = WF[i] * r->psi[(size_t)(nf - 1) * nx + xn];
+                    if (EX[i]) sx += EX[i] * t;
+                    if (EY[i]) sy += EY[i] * t;
                 } else {
                     double cw = (yn < 0) ? r->cw[xn] : p->c_w_top;
                     double t = WF[i] * cw;

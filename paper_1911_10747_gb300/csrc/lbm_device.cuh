@@ -328,6 +328,11 @@ k_flow(const DevParams p, const typename P::fst *__restrict__ fin, typename P::f
                 const R t = wf<R>(i) * s_psi[(ly + 1 + cy(i)) * SW + (lx + 1 + cx(i))];
                 if (cx(i) > 0) sx = sx + t; else if (cx(i) < 0) sx = sx - t;
                 if (cy(i) > 0) sy = sy + t; else if (cy(i) < 0) sy = sy - t;
+            } else if (yn >= nf && p.top_mode == TOP_OUTFLOW) {
+                // open top: psi continued with zero normal gradient (same row)
+                const R t = wf<R>(i) * s_psi[(ly + 1) * SW + (lx + 1 + cx(i))];
+                if (cx(i) > 0) sx = sx + t; else if (cx(i) < 0) sx = sx - t;
+                if (cy(i) > 0) sy = sy + t; else if (cy(i) < 0) sy = sy - t;
             } else {
                 const R c = (yn < 0) ? R(cw[wrap1(x + cx(i), nx)]) : R(p.c_w_top);
                 const R t = wf<R>(i) * c;

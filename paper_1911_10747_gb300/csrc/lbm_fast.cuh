@@ -1,0 +1,554 @@
+// Throughput kernels of the FP32 path (shifted populations g = f - w rho0,
+// theta = T - T_sat, FP32 arithmetic with hardware reciprocal / square-root
+// approximations).  Same method and boundary treatment as the FP64 kernels of
+// lbm_device.cuh, rearranged for speed:
+//   flow: the 9-point force sums and the push targets are written out in
+//         closed form; wall-side work happens only on the two boundary rows;
+//   heat: per cell, once per step, the conduction link weights (harmonic mean
+//         conductance x lattice weight x 6 / (rho c)), the velocity and the
+//         phase-change source coefficients are precomputed, so that each RK
+//         stage costs ~30 FMA-class operations per cell.  The source
+//         -(T / rho C_V) (dp/dT)_rho div u is exactly C1 T + C2 sqrt(T) with
+//         C1, C2 functions of rho and div u only (Eq. 13 differentiated:
+//         (dp/dT)_rho = A(rho) + B(rho) / sqrt(T)).
+#pragma once
+#include "lbm_device.cuh"
+
+namespace lbmgb {
+
+__device__ __forceinline__ float frcp(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ float fast_rcp(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ float fast_sqrt(float x) { return x * rsqrtf(x); }  // x > 0
+
+// psi(rho, T) of Eq. 12-13 in FP32 with approximate reciprocals / roots.
+__device__ __forceinline__ float psi_fast(const DevParams &p, float rho, float T, unsigned &errbits) {
+    const float t1 = fast_sqrt(T * float(1.0 / p.Tc));
+    const float t2 = 1.0f + float(p.kappa) * (1.0f - t1);
+    const float phi = t2 * t2;
+    const float br = float(p.b) * rho;
+    const float p1 = rho * float(p.R) * T * fast_rcp(1.0f - br);
+    const float den = 1.0f + br * (2.0f - br);
+    const float p2 = float(p.a) * phi * rho * rho * fast_rcp(den);
+    const float arg = float(2.0 / p.G) * ((p1 - p2) - rho * (1.0f / 3.0f));
+    if (!(arg > 0.0f)) {
+        if (!(arg == 0.0f)) errbits |= ERRW_PSI;
+        return 0.0f;
+    }
+    return fast_sqrt(arg);
+}
+
+// ============================================================================
+// Flow kernel, FP32 shifted populations.  Tile TX = BX columns x TY = BY * RY
+// rows; thread (tx, ty) owns rows ty + k BY.  psi tile with a one-site halo
+// in shared memory; the halo ring is recomputed from the neighbours'
+// populations (L2 hits).  Rows outside the fluid hold psi = 0 (walls add
+// their pull through F_ads) or, for an open top, the psi of the top row.
+// ============================================================================
+template <class P, int BX, int BY, int RY, int MINB>
+__global__ void __launch_bounds__(BX *BY, MINB)
+k_flow_fast(const DevParams p, const typename P::fst *__restrict__ fin, typename P::fst *__restrict__ fout,
+            const typename P::tst *__restrict__ Tin, float *__restrict__ rho_o, float *__restrict__ ux_o,
+            float *__restrict__ uy_o, const double *__restrict__ cw, double *__restrict__ part,
+            unsigned *__restrict__ err) {
+    using S = typename P::fst;
+    constexpr int TX = BX, TY = BY * RY, SW = TX + 2, SH = TY + 2, NT = BX * BY;
+    __shared__ float s_psi[SH * SW];
+    __shared__ float s_red[2][NT / 32];
+
+    const int nx = p.nx, nf = p.nf;
+    const size_t plane = (size_t)nf * nx;
+    const bool py = (p.flags & FLAG_PERIODIC_Y) != 0;
+    const bool frozen = (p.flags & FLAG_FROZEN_FLOW) != 0;
+    const bool outflow = p.top_mode == TOP_OUTFLOW;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int tid = threadIdx.y * BX + threadIdx.x;
+    const float rho0 = float(p.rho_shift);
+    const float tsat = float(p.T_sat);
+    unsigned errbits = 0;
+
+    float g[RY][9];
+    float dd[RY];
+
+    // ---- own sites: load, density, psi ----
+    #pragma unroll
+    for (int r = 0; r < RY; r++) {
+        const int lx = threadIdx.x, ly = threadIdx.y + r * BY;
+        const int x = (x0 + lx < nx) ? x0 + lx : wrapi(x0 + lx, nx);
+        int y = y0 + ly;
+        const bool has = py || y < nf;
+        if (py) y = wrapi(y, nf);
+        float psi = 0.0f;
+        dd[r] = 0.0f;
+        if (has) {
+            const size_t k = (size_t)y * nx + x;
+            #pragma unroll
+            for (int i = 0; i < 9; i++) g[r][i] = ld_as<float>(fin + i * plane + k);
+            const float d = ((g[r][0] + g[r][1]) + (g[r][2] + g[r][3])) + ((g[r][4] + g[r][5]) + (g[r][6] + g[r][7])) + g[r][8];
+            dd[r] = d;
+            const float T = ld_as<float>(Tin + (size_t)(p.ns + y) * nx + x) + tsat;
+            if (!frozen) psi = psi_fast(p, d + rho0, T, errbits);
+        } else {
+            #pragma unroll
+            for (int i = 0; i < 9; i++) g[r][i] = 0.0f;
+        }
+        s_psi[(ly + 1) * SW + lx + 1] = psi;
+    }
+    // ---- halo ring ----
+    if (!frozen) {
+        for (int k = tid; k < 2 * SW + 2 * TY; k += NT) {
+            int hx, hy;
+            if (k < SW) { hx = k; hy = 0; }
+            else if (k < 2 * SW) { hx = k - SW; hy = SH - 1; }
+            else if (k < 2 * SW + TY) { hx = 0; hy = 1 + (k - 2 * SW); }
+            else { hx = SW - 1; hy = 1 + (k - 2 * SW - TY); }
+            const int x = wrapi(x0 + hx - 1, nx);
+            int y = y0 + hy - 1;
+            if (py) y = wrapi(y, nf);
+            float psi = 0.0f;
+            if (y >= 0 && y < nf) {
+                const size_t kk = (size_t)y * nx + x;
+                float v[9];
+                #pragma unroll
+                for (int i = 0; i < 9; i++) v[i] = ld_as<float>(fin + i * plane + kk);
+                const float d = ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7])) + v[8];
+                const float T = ld_as<float>(Tin + (size_t)(p.ns + y) * nx + x) + tsat;
+                psi = psi_fast(p, d + rho0, T, errbits);
+            }
+            s_psi[hy * SW + hx] = psi;
+        }
+    }
+    __syncthreads();
+
+    // ---- collide and push ----
+    const float w1 = 1.0f / 3.0f, w2 = 1.0f / 12.0f;
+    const float mG = float(-p.G);
+    const float inv_drho = float(1.0 / p.drho_LV), dtau = float(p.dtau_LV);
+    float mass = 0.0f, nvap = 0.0f;
+    #pragma unroll
+    for (int r = 0; r < RY; r++) {
+        const int lx = threadIdx.x, ly = threadIdx.y + r * BY;
+        const int x = x0 + lx, y = y0 + ly;
+        if (x >= nx || y >= nf) continue;
+        const size_t k = (size_t)y * nx + x;
+        const float d = dd[r];
+        const float rho = d + rho0;
+        if (!(fabsf(rho) < 1e30f)) errbits |= ERRW_NONFINITE_RHO;
+        mass += rho;
+        nvap += (rho < float(p.vap_threshold)) ? 1.0f : 0.0f;
+        if (frozen) {
+            #pragma unroll
+            for (int i = 0; i < 9; i++) st_as(fout + i * plane + k, g[r][i]);
+            rho_o[k] = rho;
+            ux_o[k] = 0.0f;
+            uy_o[k] = 0.0f;
+            continue;
+        }
+        const float *sp = s_psi + (ly + 1) * SW + (lx + 1);
+        const float psi = sp[0];
+        const float pE = sp[1], pW = sp[-1], pN = sp[SW], pS = sp[-SW];
+        float pNE = sp[SW + 1], pNW = sp[SW - 1];
+        const float pSW = sp[-SW - 1], pSE = sp[-SW + 1];
+        const bool bot = !py && y == 0, top = !py && y == nf - 1;
+        float pNx = pN;
+        if (top && outflow) { pNx = psi; pNE = pE; pNW = pW; }  // open top: zero normal gradient
+        const float a = pNE - pSW, b = pSE - pNW;
+        const float pre = mG * psi;
+        const float Fmx = pre * (w1 * (pE - pW) + w2 * (a + b));
+        const float Fmy = pre * (w1 * (pNx - pS) + w2 * (a - b));
+        const int xm = wrap1(x - 1, nx), xp = wrap1(x + 1, nx);
+        float Fax = 0.0f, Fay = 0.0f;
+        if (bot) {  // Eq. 14 with the heater sites below (i = 4, 7, 8)
+            const float cm = float(cw[xm]), c0 = float(cw[x]), cp = float(cw[xp]);
+            Fax = -psi * (w2 * (cp - cm));
+            Fay = psi * (w1 * c0 + w2 * (cm + cp));
+        }
+        if (top && !outflow) Fay += -psi * ((w1 + 2.0f * w2) * float(p.c_w_top));
+        const float Fx = Fmx + Fax;
+        const float Fy = (Fmy + Fay) - (rho - float(p.rho_mean)) * float(p.g);
+
+        const float *f = g[r];
+        // moments of g (Eq. 6 with the rho0 shift of m0..m2 folded into q0..q2)
+        const float s14 = (f[1] + f[2]) + (f[3] + f[4]);
+        const float s58 = (f[5] + f[6]) + (f[7] + f[8]);
+        const float m1 = -4.0f * f[0] - s14 + 2.0f * s58;
+        const float m2 = 4.0f * f[0] - 2.0f * s14 + s58;
+        const float f13 = f[1] - f[3], f24 = f[2] - f[4];
+        const float f57 = f[5] - f[7], f86 = f[8] - f[6];
+        const float m3 = f13 + (f57 + f86);
+        const float m4 = -2.0f * f13 + (f57 + f86);
+        const float m5 = f24 + (f57 - f86);
+        const float m6 = -2.0f * f24 + (f57 - f86);
+        const float m7 = (f[1] + f[3]) - (f[2] + f[4]);
+        const float m8 = (f[5] + f[7]) - (f[6] + f[8]);
+        const float irho = fast_rcp(rho);
+        const float ux = (m3 + 0.5f * Fx) * irho, uy = (m5 + 0.5f * Fy) * irho;
+        const float tau = float(p.tau_V) + (rho - float(p.rho_V)) * inv_drho * dtau;
+        const float s78 = fast_rcp(tau);
+        const float ru2 = rho * (ux * ux + uy * uy);
+        const float q1 = -2.0f * d + 3.0f * ru2, q2 = d - 3.0f * ru2;
+        const float q3 = rho * ux, q5 = rho * uy;
+        const float q7 = rho * (ux * ux - uy * uy), q8 = rho * (ux * uy);
+        const float uF = ux * Fx + uy * Fy;
+        const float eps = (psi > 0.0f) ? float(p.varpi12) * (Fmx * Fmx + Fmy * Fmy) * fast_rcp(psi * psi) : 0.0f;
+        const float S1 = 6.0f * uF + eps * float(1.0 / p.tau_e_m);
+        const float S2 = -6.0f * uF + eps * float(p.sign_eps / p.tau_s_m);
+        // Eq. 7 (m0 unchanged; q4 = -q3, q6 = -q5)
+        const float z1 = m1 - float(p.s[1]) * (m1 - q1) + float(p.hs[1]) * S1;
+        const float z2 = m2 - float(p.s[2]) * (m2 - q2) + float(p.hs[2]) * S2;
+        const float z3 = m3 - float(p.s[3]) * (m3 - q3) + float(p.hs[3]) * Fx;
+        const float z4 = m4 - float(p.s[4]) * (m4 + q3) - float(p.hs[4]) * Fx;
+        const float z5 = m5 - float(p.s[5]) * (m5 - q5) + float(p.hs[5]) * Fy;
+        const float z6 = m6 - float(p.s[6]) * (m6 + q5) - float(p.hs[6]) * Fy;
+        const float h78 = 1.0f - 0.5f * s78;
+        const float z7 = m7 - s78 * (m7 - q7) + h78 * (2.0f * (ux * Fx - uy * Fy));
+        const float z8 = m8 - s78 * (m8 - q8) + h78 * (ux * Fy + uy * Fx);
+        const float e0 = d * (1.0f / 9.0f), e1 = z1 * (1.0f / 36.0f), e2 = z2 * (1.0f / 36.0f);
+        const float e3 = z3 * (1.0f / 6.0f), e4 = z4 * (1.0f / 12.0f), e5 = z5 * (1.0f / 6.0f);
+        const float e6 = z6 * (1.0f / 12.0f), e7 = z7 * 0.25f, e8 = z8 * 0.25f;
+        const float A0 = e0 - e1 - 2.0f * e2;       // axis-direction common part
+        const float B0 = e0 + 2.0f * e1 + e2;       // diagonal common part
+        const float fo0 = e0 - 4.0f * e1 + 4.0f * e2;
+        const float fo1 = A0 + (e3 - 2.0f * e4) + e7;
+        const float fo3 = A0 - (e3 - 2.0f * e4) + e7;
+        const float fo2 = A0 + (e5 - 2.0f * e6) - e7;
+        const float fo4 = A0 - (e5 - 2.0f * e6) - e7;
+        const float cxx = e3 + e4, cyy = e5 + e6;
+        const float fo5 = B0 + cxx + cyy + e8;
+        const float fo6 = B0 - cxx + cyy - e8;
+        const float fo7 = B0 - cxx - cyy + e8;
+        const float fo8 = B0 + cxx - cyy - e8;
+        rho_o[k] = rho;
+        ux_o[k] = ux;
+        uy_o[k] = uy;
+        // Eq. 8, push; halfway bounce-back at the heater and the top wall
+        S *o = fout;
+        const size_t ro = (size_t)y * nx;
+        st_as(o + ro + x, fo0);
+        st_as(o + plane + ro + xp, fo1);
+        st_as(o + 3 * plane + ro + xm, fo3);
+        const size_t ru = (size_t)(py && y == nf - 1 ? 0 : y + 1) * nx;
+        const size_t rd = (size_t)(py && y == 0 ? nf - 1 : y - 1) * nx;
+        if (!top) {
+            st_as(o + 2 * plane + ru + x, fo2);
+            st_as(o + 5 * plane + ru + xp, fo5);
+            st_as(o + 6 * plane + ru + xm, fo6);
+        } else if (!outflow) {
+            st_as(o + 4 * plane + ro + x, fo2);
+            st_as(o + 7 * plane + ro + x, fo5);
+            st_as(o + 8 * plane + ro + x, fo6);
+        }
+        if (!bot) {
+            st_as(o + 4 * plane + rd + x, fo4);
+            st_as(o + 7 * plane + rd + xm, fo7);
+            st_as(o + 8 * plane + rd + xp, fo8);
+        } else {
+            st_as(o + 2 * plane + ro + x, fo4);
+            st_as(o + 5 * plane + ro + x, fo7);
+            st_as(o + 6 * plane + ro + x, fo8);
+        }
+        if (top && outflow) {
+            st_as(o + 4 * plane + ro + x, fo4);
+            st_as(o + 7 * plane + ro + xm, fo7);
+            st_as(o + 8 * plane + ro + xp, fo8);
+        }
+    }
+    // per-block mass and vapour count: FP32 inside the block, FP64 across blocks
+    #pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        mass += __shfl_down_sync(0xffffffffu, mass, o);
+        nvap += __shfl_down_sync(0xffffffffu, nvap, o);
+    }
+    if ((tid & 31) == 0) { s_red[0][tid >> 5] = mass; s_red[1][tid >> 5] = nvap; }
+    __syncthreads();
+    if (tid == 0) {
+        double m = 0.0, v = 0.0;
+        #pragma unroll
+        for (int w = 0; w < NT / 32; w++) { m += (double)s_red[0][w]; v += (double)s_red[1][w]; }
+        const int bi = blockIdx.y * gridDim.x + blockIdx.x;
+        part[2 * bi] = m;
+        part[2 * bi + 1] = v;
+    }
+    if (errbits) atomicOr(err, errbits);
+}
+
+// ============================================================================
+// Heat kernel, FP32.  Output tile TX x TY, 4-cell halo.  Shared arrays per
+// cell: three temperature buffers, eight link coefficients k_a, their sum,
+// -3 u_x w, -3 u_y w folded advection factors, the source coefficients C1, C2.
+// Threads are laid out 2-D (BXH x BYH) and stride over the region, so no
+// integer division appears in the stage loops.
+// ============================================================================
+template <int TX, int TY>
+struct HeatFastLayout {
+    static constexpr int H = 4, SW = TX + 2 * H, SH = TY + 2 * H, NC = SW * SH;
+    static constexpr int NARR = 3 + 8 + 1 + 2 + 2;  // T x3, k x8, ksum, adv x2, C1, C2
+    static constexpr size_t bytes = (size_t)NC * NARR * sizeof(float) + (size_t)TX * TY * sizeof(float) + NC + 64;
+};
+
+template <class P, int TX, int TY, int BXH, int BYH>
+__global__ void __launch_bounds__(BXH *BYH)
+k_heat_fast(const DevParams p, const typename P::tst *__restrict__ Tin, typename P::tst *__restrict__ Tout,
+            const float *__restrict__ rho_i, const float *__restrict__ ux_i, const float *__restrict__ uy_i,
+            const long long *__restrict__ stepp, unsigned *__restrict__ err) {
+    using L = HeatFastLayout<TX, TY>;
+    constexpr int H = L::H, SW = L::SW, SH = L::SH, NC = L::NC;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    float *base = reinterpret_cast<float *>(smraw);
+    float *sTn = base, *sA = base + NC, *sB = base + 2 * NC;
+    float *sk = base + 3 * NC;          // 8 arrays: k_a for a = 1..8
+    float *sks = base + 11 * NC;        // sum of k_a
+    float *sax = base + 12 * NC, *say = base + 13 * NC;
+    float *sc1 = base + 14 * NC, *sc2 = base + 15 * NC;
+    float *sAcc = base + 16 * NC;
+    unsigned char *kind = reinterpret_cast<unsigned char *>(sAcc + TX * TY);
+    // load phase: lambda in sA (neighbour reads), -3u in sax/say (final form,
+    // neighbour reads for div u), own-cell rho c in sc1 and rho in sc2
+    float *sLam = sA, *sRcv = sc1, *sRho = sc2;
+
+    const int nx = p.nx, nt = p.nt, ns = p.ns, nf = p.nf;
+    const bool py = (p.flags & FLAG_PERIODIC_Y) != 0;
+    const bool iso = (p.flags & FLAG_ISOTHERMAL) != 0;
+    const int x0 = blockIdx.x * TX, r0 = blockIdx.y * TY;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const long long n = *stepp;
+    unsigned errbits = 0;
+
+    // ---- load ----
+    for (int hy = ty; hy < SH; hy += BYH) {
+        int row = r0 + hy - H;
+        unsigned char kd;
+        if (py) { row = wrapi(row, nt); kd = 2; }
+        else if (row < 0 || row > nt) kd = 0;
+        else if (row == 0 || row == nt) kd = 3;
+        else kd = (row < ns) ? 1 : 2;
+        for (int hx = tx; hx < SW; hx += BXH) {
+            const int c = hy * SW + hx;
+            const int x = wrapi(x0 + hx - H, nx);
+            float T = 0.0f, lam = 0.0f, ux = 0.0f, uy = 0.0f, rcv = 1.0f, rho = 0.0f;
+            if (kd == 1) {
+                T = Tin[(size_t)row * nx + x];
+                lam = float(p.lambda_s);
+                rcv = float(p.rho_c_s);
+            } else if (kd == 2) {
+                const size_t kf = (size_t)(row - ns) * nx + x;
+                T = Tin[(size_t)row * nx + x];
+                rho = rho_i[kf];
+                ux = ux_i[kf];
+                uy = uy_i[kf];
+                lam = float(p.cv_chi) * rho;
+                rcv = rho * float(p.c_v);
+            } else if (kd == 3) {
+                if (row == 0) {
+                    T = float(bottom_temperature(p, x, n) - p.T_sat);
+                    lam = float(p.lambda_s);
+                } else {
+                    T = 0.0f;
+                    lam = float(p.cv_chi) * rho_i[(size_t)(nf - 1) * nx + x];
+                }
+            }
+            sTn[c] = T; sB[c] = T;
+            sLam[c] = lam; sax[c] = -3.0f * ux; say[c] = -3.0f * uy; sRcv[c] = rcv; sRho[c] = rho;
+            kind[c] = kd;
+        }
+    }
+    __syncthreads();
+    // ---- coefficients, same thread-cell map as the load (own-cell slots only
+    // are rewritten; neighbours are read from sA = lambda and sax/say) ----
+    // k_a = 6 w_a lambda_face / (rho c), lambda_face = harmonic mean
+    const float w1 = 1.0f / 9.0f, w2 = 1.0f / 36.0f;
+    const float sqTc = float(sqrt(p.Tc));
+    for (int hy = ty; hy < SH; hy += BYH) {
+        for (int hx = tx; hx < SW; hx += BXH) {
+            const int c = hy * SW + hx;
+            const unsigned char kd = kind[c];
+            float kk[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+            float ks = 0.0f, c1 = 0.0f, c2 = 0.0f;
+            const bool inner = hx >= 1 && hx < SW - 1 && hy >= 1 && hy < SH - 1;
+            if (inner && (kd == 1 || kd == 2)) {
+                const float l0 = sLam[c];
+                const float inv6 = 6.0f * fast_rcp(sRcv[c]);
+                const int off[8] = {1, SW, -1, -SW, SW + 1, SW - 1, -SW - 1, -SW + 1};
+                #pragma unroll
+                for (int a = 0; a < 8; a++) {
+                    const float la = sLam[c + off[a]];
+                    const float hm = 2.0f * l0 * la * fast_rcp(l0 + la);
+                    kk[a] = (a < 4 ? w1 : w2) * hm * inv6;
+                    ks += kk[a];
+                }
+                if (kd == 2) {
+                    // Eq. 27 divergence of the frozen velocity (sax, say hold -3 u)
+                    const float dx = w1 * (sax[c + 1] - sax[c - 1]) +
+                                     w2 * ((sax[c + SW + 1] - sax[c - SW - 1]) + (sax[c - SW + 1] - sax[c + SW - 1]));
+                    const float dy = w1 * (say[c + SW] - say[c - SW]) +
+                                     w2 * ((say[c + SW + 1] - say[c - SW - 1]) - (say[c - SW + 1] - say[c + SW - 1]));
+                    const float divu = -(dx + dy);  // 3 (sum w e.u) with the -3 folded out
+                    // (dp/dT)_rho = A + B / sqrt(T) (Eq. 13), rho-only A, B
+                    const float rho = sRho[c];
+                    const float br = float(p.b) * rho;
+                    const float iden = fast_rcp(1.0f + br * (2.0f - br));
+                    const float pa = float(p.a * p.kappa) * rho * rho * iden;
+                    const float A = rho * float(p.R) * fast_rcp(1.0f - br) - pa * float(p.kappa / p.Tc);
+                    const float B = pa * float((1.0 + p.kappa)) * (1.0f / sqTc);
+                    const float g0 = -divu * fast_rcp(sRcv[c]);
+                    c1 = g0 * A;   // times T
+                    c2 = g0 * B;   // times sqrt(T)
+                }
+            }
+            #pragma unroll
+            for (int a = 0; a < 8; a++) sk[a * NC + c] = kk[a];
+            sks[c] = ks;
+            sc1[c] = c1;
+            sc2[c] = c2;
+        }
+    }
+    __syncthreads();
+    for (int hy = ty; hy < SH; hy += BYH)
+        for (int hx = tx; hx < SW; hx += BXH) sA[hy * SW + hx] = sTn[hy * SW + hx];
+    __syncthreads();
+
+    // ---- four RK stages on shrinking regions ----
+    const float tsat = float(p.T_sat);
+    if (!iso) {
+        #pragma unroll 1
+        for (int st = 0; st < 4; st++) {
+            const int m = 1 + st;
+            const float *Tk = (st == 0) ? sTn : ((st == 2) ? sB : sA);
+            float *To = (st == 1) ? sB : sA;
+            for (int hy = m + ty; hy < SH - m; hy += BYH) {
+                for (int hx = m + tx; hx < SW - m; hx += BXH) {
+                    const int c = hy * SW + hx;
+                    const unsigned char kd = kind[c];
+                    if (kd != 1 && kd != 2) continue;
+                    const float T0 = Tk[c];
+                    const float T1 = Tk[c + 1], T2 = Tk[c + SW], T3 = Tk[c - 1], T4 = Tk[c - SW];
+                    const float T5 = Tk[c + SW + 1], T6 = Tk[c + SW - 1], T7 = Tk[c - SW - 1], T8 = Tk[c - SW + 1];
+                    float h = sk[c] * T1 + sk[NC + c] * T2 + sk[2 * NC + c] * T3 + sk[3 * NC + c] * T4 +
+                              sk[4 * NC + c] * T5 + sk[5 * NC + c] * T6 + sk[6 * NC + c] * T7 +
+                              sk[7 * NC + c] * T8 - sks[c] * T0;
+                    if (kd == 2) {
+                        const float a = T5 - T7, b = T8 - T6;
+                        const float gx = w1 * (T1 - T3) + w2 * (a + b);
+                        const float gy = w1 * (T2 - T4) + w2 * (a - b);
+                        const float Ta = fmaxf(T0 + tsat, 1e-30f);
+                        h += sax[c] * gx + say[c] * gy + sc1[c] * Ta + sc2[c] * fast_sqrt(Ta);
+                    }
+                    const bool in_tile = hx >= H && hx < H + TX && hy >= H && hy < H + TY;
+                    const int ai = (hy - H) * TX + (hx - H);
+                    const float Tn = sTn[c];
+                    if (st == 0) {
+                        if (in_tile) sAcc[ai] = h;
+                        To[c] = Tn + 0.5f * h;
+                    } else if (st == 1) {
+                        if (in_tile) sAcc[ai] += 2.0f * h;
+                        To[c] = Tn + 0.5f * h;
+                    } else if (st == 2) {
+                        if (in_tile) sAcc[ai] += 2.0f * h;
+                        To[c] = Tn + h;
+                    } else {
+                        sAcc[ai] += h;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    // ---- write ----
+    for (int yy = ty; yy < TY; yy += BYH) {
+        const int row = r0 + yy;
+        if (row >= nt) break;
+        for (int xx = tx; xx < TX; xx += BXH) {
+            const int x = x0 + xx;
+            if (x >= nx) break;
+            const int c = (yy + H) * SW + (xx + H);
+            const unsigned char kd = kind[c];
+            float v = sTn[c];
+            if ((kd == 1 || kd == 2) && !iso) v = sTn[c] + sAcc[yy * TX + xx] * (1.0f / 6.0f);
+            if (!(fabsf(v) < 1e30f)) errbits |= ERRW_NONFINITE_T;
+            Tout[(size_t)row * nx + x] = v;
+        }
+    }
+    if (errbits) atomicOr(err, errbits);
+}
+
+// ---- diagnostics for the FP32 path: per-column flux in FP32, FP64 sums ----
+template <class P, int NT>
+__global__ void __launch_bounds__(NT)
+k_diag_fast(const DevParams p, const float *__restrict__ T, const float *__restrict__ rho,
+            const double *__restrict__ part, int nblk, double *__restrict__ q_top, double *__restrict__ series,
+            int cap, double *__restrict__ last, long long *__restrict__ stepp) {
+    __shared__ double sh[2][NT / 32];
+    const int nx = p.nx, ns = p.ns;
+    const bool py = (p.flags & FLAG_PERIODIC_Y) != 0;
+    double mass = 0.0, nvap = 0.0;
+    for (int b = threadIdx.x; b < nblk; b += NT) {
+        mass += part[2 * b];
+        nvap += part[2 * b + 1];
+    }
+    block_sum2<NT>(mass, nvap, sh);
+    __syncthreads();
+    double qb = 0.0, qt = 0.0;
+    const float lams = float(p.lambda_s), cvchi = float(p.cv_chi);
+    if (!py && ns >= 3) {
+        for (int x = threadIdx.x; x < nx; x += NT) {
+            // theta differences: T_sat cancels in the gradients
+            const float t0 = T[x], t1 = T[nx + x], t2 = T[2 * nx + x];
+            qb += (double)(-lams * (0.5f * ((4.0f * t1 - t2) - 3.0f * t0)));
+            const float lf1 = cvchi * rho[x];
+            const float lf = 2.0f * lams * lf1 * fast_rcp(lams + lf1);
+            const float q = -lf * (T[(size_t)ns * nx + x] - T[(size_t)(ns - 1) * nx + x]);
+            q_top[x] = (double)q;
+            qt += (double)q;
+        }
+    }
+    block_sum2<NT>(qb, qt, sh);
+    if (threadIdx.x == 0) {
+        const long long n = *stepp;
+        const double nfl = (double)nx * (double)p.nf;
+        double v[SERIES_WIDTH] = {qb / (double)nx, qt / (double)nx, nvap / nfl, mass};
+        if (py || ns < 3) { v[0] = 0.0; v[1] = 0.0; }
+        const long long slot = n % cap;
+        #pragma unroll
+        for (int k = 0; k < SERIES_WIDTH; k++) {
+            series[slot * SERIES_WIDTH + k] = v[k];
+            last[k] = v[k];
+        }
+        *stepp = n + 1;
+    }
+}
+
+template <class P, int BX, int BY, int RY, int MINB>
+struct FlowFastShape {
+    static dim3 grid(const DevParams &p) { return dim3((p.nx + BX - 1) / BX, (p.nf + BY * RY - 1) / (BY * RY)); }
+    static int blocks(const DevParams &p) { dim3 g = grid(p); return (int)(g.x * g.y); }
+    static cudaError_t launch(const DevParams &p, const StepBuffers &b, cudaStream_t s) {
+        k_flow_fast<P, BX, BY, RY, MINB><<<grid(p), dim3(BX, BY), 0, s>>>(
+            p, (const typename P::fst *)b.f_in, (typename P::fst *)b.f_out, (const typename P::tst *)b.T_in,
+            (float *)b.rho, (float *)b.ux, (float *)b.uy, b.cw, b.part, b.err);
+        return cudaGetLastError();
+    }
+};
+
+template <class P, int TX, int TY, int BXH, int BYH>
+struct HeatFastShape {
+    static constexpr size_t smem = HeatFastLayout<TX, TY>::bytes;
+    static cudaError_t prepare() {
+        return cudaFuncSetAttribute(k_heat_fast<P, TX, TY, BXH, BYH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem);
+    }
+    static cudaError_t launch(const DevParams &p, const StepBuffers &b, cudaStream_t s) {
+        dim3 g((p.nx + TX - 1) / TX, (p.nt + TY - 1) / TY);
+        k_heat_fast<P, TX, TY, BXH, BYH><<<g, dim3(BXH, BYH), smem, s>>>(
+            p, (const typename P::tst *)b.T_in, (typename P::tst *)b.T_out, (const float *)b.rho,
+            (const float *)b.ux, (const float *)b.uy, b.step, b.err);
+        return cudaGetLastError();
+    }
+};
+
+template <class P, int NT>
+cudaError_t launch_diag_fast(const DevParams &p, const StepBuffers &b, int nblk, cudaStream_t s) {
+    k_diag_fast<P, NT><<<1, NT, 0, s>>>(p, (const float *)b.T_out, (const float *)b.rho, b.part, nblk, b.q_top,
+                                        b.series, b.series_cap, b.last, b.step);
+    return cudaGetLastError();
+}
+
+}  // namespace lbmgb

@@ -1,26 +1,38 @@
 // FP32 kernels: shifted populations g = f - w rho0 and theta = T - T_sat,
-// FP32 arithmetic; FP16 storage of g as a probe.
-#include "lbm_device.cuh"
+// FP32 arithmetic; FP16 storage of g as a probe.  Several launch shapes of
+// the flow and heat kernels are compiled; lbm_autotune picks among them.
+#include "lbm_fast.cuh"
 
 namespace lbmgb {
 namespace {
 template <class P>
-struct Set {
-    using Flow = FlowShape<P, 32, 8, 4>;
-    using Heat = HeatShape<P, 32, 16, 256>;
-    static cudaError_t flow(const DevParams &p, const StepBuffers &b, cudaStream_t s) { return Flow::launch(p, b, s); }
-    static cudaError_t heat(const DevParams &p, const StepBuffers &b, cudaStream_t s) { return Heat::launch(p, b, s); }
-    static cudaError_t diag(const DevParams &p, const StepBuffers &b, cudaStream_t s) { return launch_diag<P, 512>(p, b, Flow::blocks(p), s); }
-    static int blocks(const DevParams &p) { return Flow::blocks(p); }
+cudaError_t diag(const DevParams &p, const StepBuffers &b, int nblk, cudaStream_t s) {
+    return launch_diag_fast<P, 512>(p, b, nblk, s);
+}
+#define FLOWV(P, BX, BY, RY, MB) \
+    {"flow_" #BX "x" #BY "x" #RY "_b" #MB, FlowFastShape<P, BX, BY, RY, MB>::launch, FlowFastShape<P, BX, BY, RY, MB>::blocks}
+#define HEATV(P, TX, TY, BX, BY) \
+    {"heat_" #TX "x" #TY "_t" #BX "x" #BY, HeatFastShape<P, TX, TY, BX, BY>::launch, HeatFastShape<P, TX, TY, BX, BY>::prepare}
+
+const FlowVariant flows32[] = {
+    FLOWV(PolicyF32, 32, 8, 2, 3), FLOWV(PolicyF32, 32, 8, 4, 2), FLOWV(PolicyF32, 32, 16, 2, 2),
+    FLOWV(PolicyF32, 64, 4, 2, 3), FLOWV(PolicyF32, 32, 8, 1, 4), FLOWV(PolicyF32, 64, 8, 2, 2),
 };
-const KernelSet ks32 = {"fp32", sizeof(float), sizeof(float), sizeof(float), Set<PolicyF32>::flow,
-                        Set<PolicyF32>::heat, Set<PolicyF32>::diag, launch_init<PolicyF32>,
-                        launch_import<PolicyF32>, launch_export<PolicyF32>, Set<PolicyF32>::blocks,
-                        Set<PolicyF32>::Heat::prepare};
-const KernelSet ks16 = {"fp16", sizeof(__half), sizeof(float), sizeof(float), Set<PolicyF16>::flow,
-                        Set<PolicyF16>::heat, Set<PolicyF16>::diag, launch_init<PolicyF16>,
-                        launch_import<PolicyF16>, launch_export<PolicyF16>, Set<PolicyF16>::blocks,
-                        Set<PolicyF16>::Heat::prepare};
+const HeatVariant heats32[] = {
+    HEATV(PolicyF32, 32, 16, 32, 8), HEATV(PolicyF32, 32, 32, 32, 16), HEATV(PolicyF32, 64, 16, 64, 4),
+    HEATV(PolicyF32, 64, 32, 32, 16),
+};
+const FlowVariant flows16[] = {FLOWV(PolicyF16, 32, 8, 2, 3), FLOWV(PolicyF16, 32, 8, 4, 2)};
+const HeatVariant heats16[] = {HEATV(PolicyF16, 32, 16, 32, 8), HEATV(PolicyF16, 32, 32, 32, 16)};
+
+const KernelSet ks32 = {"fp32", sizeof(float), sizeof(float), sizeof(float),
+                        (int)(sizeof(flows32) / sizeof(flows32[0])), flows32,
+                        (int)(sizeof(heats32) / sizeof(heats32[0])), heats32, diag<PolicyF32>,
+                        launch_init<PolicyF32>, launch_import<PolicyF32>, launch_export<PolicyF32>};
+const KernelSet ks16 = {"fp16", sizeof(__half), sizeof(float), sizeof(float),
+                        (int)(sizeof(flows16) / sizeof(flows16[0])), flows16,
+                        (int)(sizeof(heats16) / sizeof(heats16[0])), heats16, diag<PolicyF16>,
+                        launch_init<PolicyF16>, launch_import<PolicyF16>, launch_export<PolicyF16>};
 }  // namespace
 const KernelSet *kernels_fp32() { return &ks32; }
 const KernelSet *kernels_fp16() { return &ks16; }

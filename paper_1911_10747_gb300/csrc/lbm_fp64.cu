@@ -8,12 +8,13 @@ namespace {
 using P = PolicyF64;
 using Flow = FlowShape<P, 32, 8, 2>;
 using Heat = HeatShape<P, 32, 16, 256>;
-cudaError_t flow(const DevParams &p, const StepBuffers &b, cudaStream_t s) { return Flow::launch(p, b, s); }
-cudaError_t heat(const DevParams &p, const StepBuffers &b, cudaStream_t s) { return Heat::launch(p, b, s); }
-cudaError_t diag(const DevParams &p, const StepBuffers &b, cudaStream_t s) { return launch_diag<P, 512>(p, b, Flow::blocks(p), s); }
-int blocks(const DevParams &p) { return Flow::blocks(p); }
-const KernelSet ks = {"fp64", sizeof(double), sizeof(double), sizeof(double), flow, heat, diag,
-                      launch_init<P>, launch_import<P>, launch_export<P>, blocks, Heat::prepare};
+cudaError_t diag(const DevParams &p, const StepBuffers &b, int nblk, cudaStream_t s) {
+    return launch_diag<P, 512>(p, b, nblk, s);
+}
+const FlowVariant flows[] = {{"flow64_32x16", Flow::launch, Flow::blocks}};
+const HeatVariant heats[] = {{"heat64_32x16", Heat::launch, Heat::prepare}};
+const KernelSet ks = {"fp64", sizeof(double), sizeof(double), sizeof(double), 1, flows, 1, heats, diag,
+                      launch_init<P>, launch_import<P>, launch_export<P>};
 }  // namespace
 const KernelSet *kernels_fp64() { return &ks; }
 }  // namespace lbmgb

@@ -56,12 +56,27 @@ struct StepBuffers {
     double *scratch;         // reduction scratch for init (>= 1024 doubles)
 };
 
+// One launch shape of the flow or heat kernel.  Every variant of a kernel
+// does the same per-site arithmetic; only tiling and occupancy differ.
+struct FlowVariant {
+    const char *name;
+    cudaError_t (*launch)(const DevParams &, const StepBuffers &, cudaStream_t);
+    int (*blocks)(const DevParams &);   // blocks of one launch (= per-block partials)
+};
+struct HeatVariant {
+    const char *name;
+    cudaError_t (*launch)(const DevParams &, const StepBuffers &, cudaStream_t);
+    cudaError_t (*prepare)();           // per-device kernel attributes
+};
+
 struct KernelSet {
     const char *name;
     size_t f_elem, T_elem, m_elem;      // storage bytes per population, T, moment
-    cudaError_t (*lbm)(const DevParams &, const StepBuffers &, cudaStream_t);
-    cudaError_t (*fd)(const DevParams &, const StepBuffers &, cudaStream_t);
-    cudaError_t (*diag)(const DevParams &, const StepBuffers &, cudaStream_t);
+    int n_flow;
+    const FlowVariant *flow;
+    int n_heat;
+    const HeatVariant *heat;
+    cudaError_t (*diag)(const DevParams &, const StepBuffers &, int nblk, cudaStream_t);
     // Initial state (Sec. 3.1).  phase 0: initial densities into rho and
     // their sum into scratch[0]; phase 1 (after the host has fixed rho_mean
     // and rho_shift): populations into f_out, T_sat into T_out.
@@ -72,8 +87,6 @@ struct KernelSet {
     // storage -> float64 device arrays (any pointer may be NULL).
     cudaError_t (*export_fields)(const DevParams &, const StepBuffers &, double *rho, double *ux,
                                  double *uy, double *T, double *f, cudaStream_t);
-    int (*blocks)(const DevParams &);   // number of flow-kernel blocks (partials)
-    cudaError_t (*prepare)();           // per-device kernel attributes
 };
 
 const KernelSet *kernels_fp64();

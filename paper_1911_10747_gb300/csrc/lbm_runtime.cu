@@ -3,6 +3,7 @@
 // diagnostics kernel), CUDA-graph replay, state import/export and read-back.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -41,7 +42,8 @@ struct lbm_run {
     unsigned *err = nullptr;
     long long *dstep = nullptr;
     int series_cap = 4096;
-    int nblk = 0;
+    int nblk = 0;                   // blocks of the selected flow variant
+    int fv = 0, hv = 0;             // selected flow / heat variants
     cudaGraphExec_t graph = nullptr;
     bool timing = false;
     std::vector<EventPair> ev[3];
@@ -241,15 +243,18 @@ int lbm_create(const lbm_domain_t *domain, const lbm_heater_t *heater, const lbm
         if (e != cudaSuccess) { cuda_fail(h, e, "cudaStreamCreate"); return bad(LBM_E_CUDA); }
         h->own_stream = true;
     }
-    if ((e = h->ks->prepare()) != cudaSuccess) { cuda_fail(h, e, "kernel attributes"); return bad(LBM_E_CUDA); }
+    for (int v = 0; v < h->ks->n_heat; v++)
+        if ((e = h->ks->heat[v].prepare()) != cudaSuccess) { cuda_fail(h, e, "kernel attributes"); return bad(LBM_E_CUDA); }
     const DevParams &p = h->p;
     const size_t nfl = (size_t)p.nx * p.nf, ntl = (size_t)p.nx * p.nt;
-    h->nblk = h->ks->blocks(p);
+    int max_blocks = 0;
+    for (int v = 0; v < h->ks->n_flow; v++) max_blocks = std::max(max_blocks, h->ks->flow[v].blocks(p));
+    h->nblk = h->ks->flow[0].blocks(p);
     struct A { void **ptr; size_t bytes; } allocs[] = {
         {&h->f[0], 9 * nfl * h->ks->f_elem}, {&h->f[1], 9 * nfl * h->ks->f_elem},
         {&h->T[0], ntl * h->ks->T_elem}, {&h->T[1], ntl * h->ks->T_elem},
         {&h->rho, nfl * h->ks->m_elem}, {&h->ux, nfl * h->ks->m_elem}, {&h->uy, nfl * h->ks->m_elem},
-        {(void **)&h->cw, (size_t)p.nx * sizeof(double)}, {(void **)&h->part, 2 * (size_t)h->nblk * sizeof(double)},
+        {(void **)&h->cw, (size_t)p.nx * sizeof(double)}, {(void **)&h->part, 2 * (size_t)max_blocks * sizeof(double)},
         {(void **)&h->series, (size_t)h->series_cap * SERIES_WIDTH * sizeof(double)},
         {(void **)&h->q_top, (size_t)p.nx * sizeof(double)}, {(void **)&h->last, SERIES_WIDTH * sizeof(double)},
         {(void **)&h->scratch, 1024 * sizeof(double)}, {(void **)&h->err, sizeof(unsigned)},
@@ -310,10 +315,15 @@ int lbm_destroy(lbm_handle h) {
     return LBM_OK;
 }
 
+static cudaError_t launch_kernel(lbm_run *h, int k, const StepBuffers &b) {
+    if (k == 0) return h->ks->flow[h->fv].launch(h->p, b, h->stream);
+    if (k == 1) return h->ks->heat[h->hv].launch(h->p, b, h->stream);
+    return h->ks->diag(h->p, b, h->nblk, h->stream);
+}
+
 static int launch_step(lbm_run *h, bool timed) {
     StepBuffers b = buffers(h, h->parity);
     cudaError_t e;
-    cudaError_t (*fn[3])(const DevParams &, const StepBuffers &, cudaStream_t) = {h->ks->lbm, h->ks->fd, h->ks->diag};
     for (int k = 0; k < 3; k++) {
         EventPair ep;
         if (timed) {
@@ -321,7 +331,7 @@ static int launch_step(lbm_run *h, bool timed) {
             CK(h, cudaEventCreate(&ep.b));
             CK(h, cudaEventRecord(ep.a, h->stream));
         }
-        if ((e = fn[k](h->p, b, h->stream)) != cudaSuccess) return cuda_fail(h, e, k == 0 ? "flow kernel" : (k == 1 ? "heat kernel" : "diagnostics kernel"));
+        if ((e = launch_kernel(h, k, b)) != cudaSuccess) return cuda_fail(h, e, k == 0 ? "flow kernel" : (k == 1 ? "heat kernel" : "diagnostics kernel"));
         if (timed) {
             CK(h, cudaEventRecord(ep.b, h->stream));
             h->ev[k].push_back(ep);
@@ -527,5 +537,77 @@ int lbm_kernel_times(lbm_handle h, double *avg_ms, int64_t *launches) {
 }
 
 int lbm_kernels_per_step(lbm_handle h) { return h ? 3 : 0; }
+
+int lbm_variants(lbm_handle h, int kind, int *count, int *selected) {
+    if (!h || (kind != 0 && kind != 1)) return h ? fail(h, LBM_E_INVAL, "kind must be 0 (flow) or 1 (heat)") : LBM_E_INVAL;
+    if (count) *count = kind == 0 ? h->ks->n_flow : h->ks->n_heat;
+    if (selected) *selected = kind == 0 ? h->fv : h->hv;
+    return LBM_OK;
+}
+
+const char *lbm_variant_name(lbm_handle h, int kind, int index) {
+    if (!h) return "";
+    if (kind == 0 && index >= 0 && index < h->ks->n_flow) return h->ks->flow[index].name;
+    if (kind == 1 && index >= 0 && index < h->ks->n_heat) return h->ks->heat[index].name;
+    return "";
+}
+
+int lbm_select_variants(lbm_handle h, int flow, int heat) {
+    if (!h) return LBM_E_INVAL;
+    if (flow < 0 || flow >= h->ks->n_flow || heat < 0 || heat >= h->ks->n_heat)
+        return fail(h, LBM_E_INVAL, "variant index out of range");
+    CK(h, cudaSetDevice(h->device));
+    CK(h, cudaStreamSynchronize(h->stream));
+    if (h->graph) { cudaGraphExecDestroy(h->graph); h->graph = nullptr; }
+    h->fv = flow;
+    h->hv = heat;
+    h->nblk = h->ks->flow[flow].blocks(h->p);
+    return LBM_OK;
+}
+
+// Time every flow and heat variant on the current state (outputs go to the
+// buffers the next step overwrites; the diagnostics kernel and the step
+// counter are not touched), keep the fastest pair.
+int lbm_autotune(lbm_handle h, int iters, double *best_ms) {
+    if (!h) return LBM_E_INVAL;
+    if (iters < 1) return fail(h, LBM_E_INVAL, "iters must be >= 1");
+    CK(h, cudaSetDevice(h->device));
+    CK(h, cudaStreamSynchronize(h->stream));
+    StepBuffers b = buffers(h, h->parity);
+    cudaEvent_t a, z;
+    CK(h, cudaEventCreate(&a));
+    CK(h, cudaEventCreate(&z));
+    double best[2] = {1e300, 1e300};
+    int pick[2] = {h->fv, h->hv};
+    const int saved[2] = {h->fv, h->hv};
+    for (int kind = 0; kind < 2; kind++) {
+        const int nv = kind == 0 ? h->ks->n_flow : h->ks->n_heat;
+        for (int v = 0; v < nv; v++) {
+            if (kind == 0) h->fv = v; else h->hv = v;
+            cudaError_t e = launch_kernel(h, kind, b);  // warm-up
+            if (e == cudaSuccess) e = cudaEventRecord(a, h->stream);
+            for (int it = 0; it < iters && e == cudaSuccess; it++) e = launch_kernel(h, kind, b);
+            if (e == cudaSuccess) e = cudaEventRecord(z, h->stream);
+            if (e == cudaSuccess) e = cudaEventSynchronize(z);
+            float ms = 0;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, z);
+            if (e != cudaSuccess) {
+                h->fv = saved[0]; h->hv = saved[1];
+                cudaEventDestroy(a); cudaEventDestroy(z);
+                return cuda_fail(h, e, "autotune launch");
+            }
+            if (ms / iters < best[kind]) { best[kind] = ms / iters; pick[kind] = v; }
+        }
+        if (kind == 0) h->fv = pick[0];  // heat variants read the moments of the chosen flow
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(z);
+    h->fv = saved[0];
+    h->hv = saved[1];
+    if (best_ms) { best_ms[0] = best[0]; best_ms[1] = best[1]; }
+    int rc = lbm_select_variants(h, pick[0], pick[1]);
+    if (rc != LBM_OK) return rc;
+    return check_err_word(h);
+}
 
 }  // extern "C"

@@ -28,7 +28,8 @@ LBM_FIELD_RHO, LBM_FIELD_UX, LBM_FIELD_UY, LBM_FIELD_T, LBM_FIELD_F = 1, 2, 4, 8
 #: every entry point declared in include/lbm.h
 EXPORTS = ("lbm_create", "lbm_destroy", "lbm_step", "lbm_sync", "lbm_step_count", "lbm_fields",
            "lbm_set_state", "lbm_wall_heat_flux", "lbm_vapour_fraction", "lbm_mass", "lbm_series",
-           "lbm_set_timing", "lbm_kernel_times", "lbm_kernels_per_step", "lbm_last_error",
+           "lbm_set_timing", "lbm_kernel_times", "lbm_kernels_per_step", "lbm_variants",
+           "lbm_variant_name", "lbm_select_variants", "lbm_autotune", "lbm_last_error",
            "lbm_status_string")
 
 
@@ -106,6 +107,11 @@ def load(path: str = LIB_PATH):
     L.lbm_set_timing.argtypes = [C.c_void_p, C.c_int]
     L.lbm_kernel_times.argtypes = [C.c_void_p, _D, C.POINTER(C.c_int64)]
     L.lbm_kernels_per_step.argtypes = [C.c_void_p]
+    L.lbm_variants.argtypes = [C.c_void_p, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+    L.lbm_variant_name.argtypes = [C.c_void_p, C.c_int, C.c_int]
+    L.lbm_variant_name.restype = C.c_char_p
+    L.lbm_select_variants.argtypes = [C.c_void_p, C.c_int, C.c_int]
+    L.lbm_autotune.argtypes = [C.c_void_p, C.c_int, _D]
     L.lbm_last_error.argtypes = [C.c_void_p]
     L.lbm_last_error.restype = C.c_char_p
     L.lbm_status_string.argtypes = [C.c_int]
@@ -283,3 +289,24 @@ class Run:
 
     def kernels_per_step(self) -> int:
         return int(load().lbm_kernels_per_step(self._h))
+
+    def variants(self) -> dict:
+        """{'flow': [names], 'heat': [names], 'selected': (flow, heat)}"""
+        L = load()
+        out = {}
+        sel = []
+        for kind, key in ((0, "flow"), (1, "heat")):
+            n, cur = C.c_int(), C.c_int()
+            _check(L.lbm_variants(self._h, kind, C.byref(n), C.byref(cur)), self._h, "lbm_variants")
+            out[key] = [L.lbm_variant_name(self._h, kind, i).decode() for i in range(n.value)]
+            sel.append(cur.value)
+        out["selected"] = tuple(sel)
+        return out
+
+    def select_variants(self, flow: int, heat: int):
+        _check(load().lbm_select_variants(self._h, int(flow), int(heat)), self._h, "lbm_select_variants")
+
+    def autotune(self, iters: int = 5):
+        ms = (C.c_double * 2)()
+        _check(load().lbm_autotune(self._h, int(iters), ms), self._h, "lbm_autotune")
+        return list(ms)

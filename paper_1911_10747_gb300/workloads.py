@@ -37,6 +37,9 @@ DEFAULT_VARPI = 0.11
 #: base hydrophilic and the spots progressively less so.
 DEFAULT_CW_BASE = -1.6
 DEFAULT_CW_SPOTS = (-0.9, -0.8, -0.7)
+#: Top wall: c_w = -psi(rho_V) at T_sat (about -0.465), so the wall pulls on
+#: the fluid like saturated vapour beyond it would.
+DEFAULT_CW_TOP = -0.465
 
 
 @dataclass
@@ -56,7 +59,7 @@ class RunConfig:
     spot_half_width: int = 1
     c_w_base: float = DEFAULT_CW_BASE
     c_w_spot: tuple = ()
-    c_w_top: float = 0.0
+    c_w_top: float = DEFAULT_CW_TOP
     a: float = 2.0 / 49.0
     b: float = 2.0 / 21.0
     R: float = 1.0
@@ -124,11 +127,21 @@ def paper_scale(superheat_over_Tc: float = 0.1, bc_mode: str = "spots", seed: in
         T_b_over_Tc=0.86 + superheat_over_Tc, seed=seed, precision=precision)
 
 
+#: Gravity of the 2048-wide domain.  The paper's g = 5e-5 makes the Taylor
+#: wavelength lambda_d ~ 200 for a 400-wide domain (2 lambda_d, Sec. 3.1);
+#: keeping the domain 2 lambda_d wide at 2048 columns scales g by
+#: (400 / 2048)^2 (lambda_d ~ g^-1/2).  With the unscaled g the 1365-row
+#: vapour column is compressed past saturation by the (rho - rho_mean) g
+#: buoyancy and the run breaks down within about 1300 steps.
+G_LARGE = 5e-5 * (400.0 / 2048.0) ** 2
+
+
 def large(precision: str = "fp32", seed: int = 3) -> RunConfig:
-    """2048 x 2048 fluid over a 64-row heater, fluctuating bottom (+-1 %)."""
+    """2048 x 2048 fluid over a 64-row heater, fluctuating bottom (+-1 %),
+    gravity scaled to keep the domain two Taylor wavelengths wide."""
     return RunConfig(
         nx=2048, nf=2048, ns=64, liquid_rows=683, bc_mode="noise",
-        T_b_over_Tc=0.96, seed=seed, precision=precision)
+        T_b_over_Tc=0.96, g=G_LARGE, seed=seed, precision=precision)
 
 
 def periodic_box(nx: int, ny: int, liquid_rows: int = 0, **kw) -> RunConfig:

@@ -42,3 +42,39 @@ def test_fp32_full_size_domain_two_steps():
     errs = field_errors(g, o)
     print("fp32 full-size 2-step errors", errs)
     assert errs["rho"] < 1e-5 and errs["T"] < 1e-6, errs
+
+
+def test_fp32_variants_give_identical_fields_and_autotune_keeps_state():
+    """Every launch-shape variant does the same per-site arithmetic, so the
+    fields agree bitwise; the autotuner leaves the run's state untouched."""
+    cfg = W.small_parity(precision="fp32").replace(nx=70, nf=45, ns=5, liquid_rows=15, rho_mean=2.3,
+                                                   spot_x=(3, 40, 69), spot_half_width=2)
+    ref = lbm.Run(cfg)
+    names = ref.variants()
+    ref.step(12)
+    want = ref.fields(("rho", "ux", "uy", "T", "f"))
+    for fv in range(len(names["flow"])):
+        for hv in range(len(names["heat"])):
+            r = lbm.Run(cfg)
+            r.select_variants(fv, hv)
+            r.step(12)
+            got = r.fields(("rho", "ux", "uy", "T", "f"))
+            for k in want:
+                assert np.array_equal(got[k], want[k]), (names["flow"][fv], names["heat"][hv], k)
+    r = lbm.Run(cfg)
+    r.step(5)
+    ms = r.autotune(2)
+    assert all(m > 0 for m in ms)
+    r.step(7)
+    got = r.fields(("rho", "ux", "uy", "T", "f"))
+    for k in want:
+        assert np.array_equal(got[k], want[k]), k
+
+
+def test_fp32_outflow_ragged_top_tile():
+    cfg = W.small_parity(precision="fp32").replace(nx=70, nf=33, ns=3, liquid_rows=11, top_mode="outflow",
+                                                   rho_mean=2.3, spot_x=(3, 40, 69), spot_half_width=2)
+    g, o = run_both(cfg, 60)
+    errs = field_errors(g, o)
+    print("fp32 outflow errors", errs)
+    assert errs["rho"] < 1e-4 and errs["T"] < 1e-5, errs

@@ -132,14 +132,18 @@ def test_full_size_domain_fp64_against_oracle():
 
 
 def test_numerical_fault_is_reported():
-    """A population state whose density exceeds 1/b makes the EOS radicand
-    negative: the kernels latch it and the next sync returns LBM_E_NUMERIC."""
+    """A non-finite population (host input) makes the density and the EOS
+    radicand non-finite: the kernels latch it in the error word and the next
+    synchronising call returns LBM_E_NUMERIC; the context stays usable."""
     cfg = W.small_parity()
     g = lbm.Run(cfg)
     f = g.fields(("f",))["f"]
-    f[:, 10, 10] *= 3.0
+    f[:, 10, 10] = np.nan
     g.set_state(f, None, step=0)
     g.step(1)
     with pytest.raises(lbm.LbmError) as ei:
         g.sync()
     assert ei.value.code == lbm.LBM_E_NUMERIC
+    # a fresh run on the same device still works
+    h = lbm.Run(cfg).step(2)
+    h.sync()
