@@ -12,24 +12,83 @@
 //         C1, C2 functions of rho and div u only (Eq. 13 differentiated:
 //         (dp/dT)_rho = A(rho) + B(rho) / sqrt(T)).
 #pragma once
+#include <type_traits>
+
 #include "lbm_device.cuh"
 
 namespace lbmgb {
+
+// Every constant an FP32 kernel needs, converted and combined on the host:
+// the kernels then issue no FP64 instruction (GB300 runs FP64 at a small
+// fraction of the FP32 rate, so even one FP64 division per thread shows).
+struct FParams {
+    int nx, nf, ns, nt, flags, top_mode, bc_mode, pad0;
+    unsigned long long seed;
+    long long sine_t0, sine_t1;
+    float rho_shift, T_sat, inv_Tc, kappa, a, b, R, two_over_G, mG;
+    float tau_V, rho_V, inv_drho, dtau, rho_mean, g, varpi12, inv_tauem, sgn_over_taus;
+    float s[9], hs[9];
+    float c_w_top, vap_threshold;
+    float lambda_s, cv_chi, c_v, rho_c_s;
+    float a_kappa, kappa_over_Tc, B_coef;          // (dp/dT)_rho pieces: a kappa, kappa / Tc, (1 + kappa) / sqrt(Tc)
+    float dTb, Tb_noise, sine_amp, sine_wl;        // bottom: T_b - T_sat, T_b A, amp Tc, wavelength
+};
+
+inline FParams make_fparams(const DevParams &p) {
+    FParams q{};
+    q.nx = p.nx; q.nf = p.nf; q.ns = p.ns; q.nt = p.nt;
+    q.flags = p.flags; q.top_mode = p.top_mode; q.bc_mode = p.bc_mode;
+    q.seed = p.seed; q.sine_t0 = p.sine_t0; q.sine_t1 = p.sine_t1;
+    q.rho_shift = (float)p.rho_shift; q.T_sat = (float)p.T_sat; q.inv_Tc = (float)(1.0 / p.Tc);
+    q.kappa = (float)p.kappa; q.a = (float)p.a; q.b = (float)p.b; q.R = (float)p.R;
+    q.two_over_G = (float)(2.0 / p.G); q.mG = (float)(-p.G);
+    q.tau_V = (float)p.tau_V; q.rho_V = (float)p.rho_V; q.inv_drho = (float)(1.0 / p.drho_LV);
+    q.dtau = (float)p.dtau_LV; q.rho_mean = (float)p.rho_mean; q.g = (float)p.g;
+    q.varpi12 = (float)p.varpi12; q.inv_tauem = (float)(1.0 / p.tau_e_m);
+    q.sgn_over_taus = (float)(p.sign_eps / p.tau_s_m);
+    for (int k = 0; k < 9; k++) { q.s[k] = (float)p.s[k]; q.hs[k] = (float)p.hs[k]; }
+    q.c_w_top = (float)p.c_w_top; q.vap_threshold = (float)p.vap_threshold;
+    q.lambda_s = (float)p.lambda_s; q.cv_chi = (float)p.cv_chi; q.c_v = (float)p.c_v; q.rho_c_s = (float)p.rho_c_s;
+    q.a_kappa = (float)(p.a * p.kappa); q.kappa_over_Tc = (float)(p.kappa / p.Tc);
+    q.B_coef = (float)((1.0 + p.kappa) / sqrt(p.Tc));
+    q.dTb = (float)(p.T_b - p.T_sat); q.Tb_noise = (float)(p.T_b * p.bc_noise);
+    q.sine_amp = (float)p.sine_amp; q.sine_wl = (float)p.sine_wl;
+    return q;
+}
+
+// theta = T - T_sat of the bottom row, FP32 (same draws as the FP64 path,
+// 24-bit uniform).
+__device__ __forceinline__ float bottom_theta(const FParams &q, int x, long long n) {
+    if (q.bc_mode == BCM_NOISE) {
+        const uint64_t gam = 0x9E3779B97F4A7C15ULL;
+        uint64_t h = smix(q.seed + gam);
+        h = smix((h ^ (uint64_t)TAG_BOTTOM_NOISE) + gam);
+        h = smix((h ^ (uint64_t)n) + gam);
+        h = smix((h ^ (uint64_t)x) + gam);
+        const float U = (float)(unsigned)(h >> 40) * (1.0f / 16777216.0f);
+        return q.dTb + q.Tb_noise * (2.0f * U - 1.0f);
+    }
+    if (q.bc_mode == BCM_SINE && n > q.sine_t0 && n < q.sine_t1) {
+        const float arg = 6.28318530717958647692f * ((float)x - 0.25f * q.sine_wl) / q.sine_wl;
+        return q.dTb + q.sine_amp * sinf(arg);
+    }
+    return q.dTb;
+}
 
 __device__ __forceinline__ float frcp(float x) { return __frcp_rn(x); }
 __device__ __forceinline__ float fast_rcp(float x) { return __fdividef(1.0f, x); }
 __device__ __forceinline__ float fast_sqrt(float x) { return x * rsqrtf(x); }  // x > 0
 
 // psi(rho, T) of Eq. 12-13 in FP32 with approximate reciprocals / roots.
-__device__ __forceinline__ float psi_fast(const DevParams &p, float rho, float T, unsigned &errbits) {
-    const float t1 = fast_sqrt(T * float(1.0 / p.Tc));
-    const float t2 = 1.0f + float(p.kappa) * (1.0f - t1);
+__device__ __forceinline__ float psi_fast(const FParams &q, float rho, float T, unsigned &errbits) {
+    const float t1 = fast_sqrt(T * q.inv_Tc);
+    const float t2 = 1.0f + q.kappa * (1.0f - t1);
     const float phi = t2 * t2;
-    const float br = float(p.b) * rho;
-    const float p1 = rho * float(p.R) * T * fast_rcp(1.0f - br);
+    const float br = q.b * rho;
+    const float p1 = rho * q.R * T * fast_rcp(1.0f - br);
     const float den = 1.0f + br * (2.0f - br);
-    const float p2 = float(p.a) * phi * rho * rho * fast_rcp(den);
-    const float arg = float(2.0 / p.G) * ((p1 - p2) - rho * (1.0f / 3.0f));
+    const float p2 = q.a * phi * rho * rho * fast_rcp(den);
+    const float arg = q.two_over_G * ((p1 - p2) - rho * (1.0f / 3.0f));
     if (!(arg > 0.0f)) {
         if (!(arg == 0.0f)) errbits |= ERRW_PSI;
         return 0.0f;
@@ -46,7 +105,7 @@ __device__ __forceinline__ float psi_fast(const DevParams &p, float rho, float T
 // ============================================================================
 template <class P, int BX, int BY, int RY, int MINB>
 __global__ void __launch_bounds__(BX *BY, MINB)
-k_flow_fast(const DevParams p, const typename P::fst *__restrict__ fin, typename P::fst *__restrict__ fout,
+k_flow_fast(const FParams p, const typename P::fst *__restrict__ fin, typename P::fst *__restrict__ fout,
             const typename P::tst *__restrict__ Tin, float *__restrict__ rho_o, float *__restrict__ ux_o,
             float *__restrict__ uy_o, const double *__restrict__ cw, double *__restrict__ part,
             unsigned *__restrict__ err) {
@@ -62,8 +121,8 @@ k_flow_fast(const DevParams p, const typename P::fst *__restrict__ fin, typename
     const bool outflow = p.top_mode == TOP_OUTFLOW;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const int tid = threadIdx.y * BX + threadIdx.x;
-    const float rho0 = float(p.rho_shift);
-    const float tsat = float(p.T_sat);
+    const float rho0 = p.rho_shift;
+    const float tsat = p.T_sat;
     unsigned errbits = 0;
 
     float g[RY][9];
@@ -121,8 +180,8 @@ k_flow_fast(const DevParams p, const typename P::fst *__restrict__ fin, typename
 
     // ---- collide and push ----
     const float w1 = 1.0f / 3.0f, w2 = 1.0f / 12.0f;
-    const float mG = float(-p.G);
-    const float inv_drho = float(1.0 / p.drho_LV), dtau = float(p.dtau_LV);
+    const float mG = p.mG;
+    const float inv_drho = p.inv_drho, dtau = p.dtau;
     float mass = 0.0f, nvap = 0.0f;
     #pragma unroll
     for (int r = 0; r < RY; r++) {
@@ -134,7 +193,7 @@ k_flow_fast(const DevParams p, const typename P::fst *__restrict__ fin, typename
         const float rho = d + rho0;
         if (!(fabsf(rho) < 1e30f)) errbits |= ERRW_NONFINITE_RHO;
         mass += rho;
-        nvap += (rho < float(p.vap_threshold)) ? 1.0f : 0.0f;
+        nvap += (rho < p.vap_threshold) ? 1.0f : 0.0f;
         if (frozen) {
             #pragma unroll
             for (int i = 0; i < 9; i++) st_as(fout + i * plane + k, g[r][i]);
@@ -162,9 +221,9 @@ k_flow_fast(const DevParams p, const typename P::fst *__restrict__ fin, typename
             Fax = -psi * (w2 * (cp - cm));
             Fay = psi * (w1 * c0 + w2 * (cm + cp));
         }
-        if (top && !outflow) Fay += -psi * ((w1 + 2.0f * w2) * float(p.c_w_top));
+        if (top && !outflow) Fay += -psi * ((w1 + 2.0f * w2) * p.c_w_top);
         const float Fx = Fmx + Fax;
-        const float Fy = (Fmy + Fay) - (rho - float(p.rho_mean)) * float(p.g);
+        const float Fy = (Fmy + Fay) - (rho - p.rho_mean) * p.g;
 
         const float *f = g[r];
         // moments of g (Eq. 6 with the rho0 shift of m0..m2 folded into q0..q2)
@@ -182,23 +241,23 @@ k_flow_fast(const DevParams p, const typename P::fst *__restrict__ fin, typename
         const float m8 = (f[5] + f[7]) - (f[6] + f[8]);
         const float irho = fast_rcp(rho);
         const float ux = (m3 + 0.5f * Fx) * irho, uy = (m5 + 0.5f * Fy) * irho;
-        const float tau = float(p.tau_V) + (rho - float(p.rho_V)) * inv_drho * dtau;
+        const float tau = p.tau_V + (rho - p.rho_V) * inv_drho * dtau;
         const float s78 = fast_rcp(tau);
         const float ru2 = rho * (ux * ux + uy * uy);
         const float q1 = -2.0f * d + 3.0f * ru2, q2 = d - 3.0f * ru2;
         const float q3 = rho * ux, q5 = rho * uy;
         const float q7 = rho * (ux * ux - uy * uy), q8 = rho * (ux * uy);
         const float uF = ux * Fx + uy * Fy;
-        const float eps = (psi > 0.0f) ? float(p.varpi12) * (Fmx * Fmx + Fmy * Fmy) * fast_rcp(psi * psi) : 0.0f;
-        const float S1 = 6.0f * uF + eps * float(1.0 / p.tau_e_m);
-        const float S2 = -6.0f * uF + eps * float(p.sign_eps / p.tau_s_m);
+        const float eps = (psi > 0.0f) ? p.varpi12 * (Fmx * Fmx + Fmy * Fmy) * fast_rcp(psi * psi) : 0.0f;
+        const float S1 = 6.0f * uF + eps * p.inv_tauem;
+        const float S2 = -6.0f * uF + eps * p.sgn_over_taus;
         // Eq. 7 (m0 unchanged; q4 = -q3, q6 = -q5)
-        const float z1 = m1 - float(p.s[1]) * (m1 - q1) + float(p.hs[1]) * S1;
-        const float z2 = m2 - float(p.s[2]) * (m2 - q2) + float(p.hs[2]) * S2;
-        const float z3 = m3 - float(p.s[3]) * (m3 - q3) + float(p.hs[3]) * Fx;
-        const float z4 = m4 - float(p.s[4]) * (m4 + q3) - float(p.hs[4]) * Fx;
-        const float z5 = m5 - float(p.s[5]) * (m5 - q5) + float(p.hs[5]) * Fy;
-        const float z6 = m6 - float(p.s[6]) * (m6 + q5) - float(p.hs[6]) * Fy;
+        const float z1 = m1 - p.s[1] * (m1 - q1) + p.hs[1] * S1;
+        const float z2 = m2 - p.s[2] * (m2 - q2) + p.hs[2] * S2;
+        const float z3 = m3 - p.s[3] * (m3 - q3) + p.hs[3] * Fx;
+        const float z4 = m4 - p.s[4] * (m4 + q3) - p.hs[4] * Fx;
+        const float z5 = m5 - p.s[5] * (m5 - q5) + p.hs[5] * Fy;
+        const float z6 = m6 - p.s[6] * (m6 + q5) - p.hs[6] * Fy;
         const float h78 = 1.0f - 0.5f * s78;
         const float z7 = m7 - s78 * (m7 - q7) + h78 * (2.0f * (ux * Fx - uy * Fy));
         const float z8 = m8 - s78 * (m8 - q8) + h78 * (ux * Fy + uy * Fx);
@@ -287,7 +346,7 @@ struct HeatFastLayout {
 
 template <class P, int TX, int TY, int BXH, int BYH>
 __global__ void __launch_bounds__(BXH *BYH)
-k_heat_fast(const DevParams p, const typename P::tst *__restrict__ Tin, typename P::tst *__restrict__ Tout,
+k_heat_fast(const FParams p, const typename P::tst *__restrict__ Tin, typename P::tst *__restrict__ Tout,
             const float *__restrict__ rho_i, const float *__restrict__ ux_i, const float *__restrict__ uy_i,
             const long long *__restrict__ stepp, unsigned *__restrict__ err) {
     using L = HeatFastLayout<TX, TY>;
@@ -313,37 +372,39 @@ k_heat_fast(const DevParams p, const typename P::tst *__restrict__ Tin, typename
     const long long n = *stepp;
     unsigned errbits = 0;
 
-    // ---- load ----
-    for (int hy = ty; hy < SH; hy += BYH) {
+    constexpr int NTH = BXH * BYH;
+    const int tid = ty * BXH + tx;
+    // ---- load (flattened: constant divisor SW) ----
+    for (int c = tid; c < NC; c += NTH) {
+        const int hy = c / SW, hx = c - (c / SW) * SW;
         int row = r0 + hy - H;
         unsigned char kd;
         if (py) { row = wrapi(row, nt); kd = 2; }
         else if (row < 0 || row > nt) kd = 0;
         else if (row == 0 || row == nt) kd = 3;
         else kd = (row < ns) ? 1 : 2;
-        for (int hx = tx; hx < SW; hx += BXH) {
-            const int c = hy * SW + hx;
+        {
             const int x = wrapi(x0 + hx - H, nx);
             float T = 0.0f, lam = 0.0f, ux = 0.0f, uy = 0.0f, rcv = 1.0f, rho = 0.0f;
             if (kd == 1) {
                 T = Tin[(size_t)row * nx + x];
-                lam = float(p.lambda_s);
-                rcv = float(p.rho_c_s);
+                lam = p.lambda_s;
+                rcv = p.rho_c_s;
             } else if (kd == 2) {
                 const size_t kf = (size_t)(row - ns) * nx + x;
                 T = Tin[(size_t)row * nx + x];
                 rho = rho_i[kf];
                 ux = ux_i[kf];
                 uy = uy_i[kf];
-                lam = float(p.cv_chi) * rho;
-                rcv = rho * float(p.c_v);
+                lam = p.cv_chi * rho;
+                rcv = rho * p.c_v;
             } else if (kd == 3) {
                 if (row == 0) {
-                    T = float(bottom_temperature(p, x, n) - p.T_sat);
-                    lam = float(p.lambda_s);
+                    T = bottom_theta(p, x, n);
+                    lam = p.lambda_s;
                 } else {
                     T = 0.0f;
-                    lam = float(p.cv_chi) * rho_i[(size_t)(nf - 1) * nx + x];
+                    lam = p.cv_chi * rho_i[(size_t)(nf - 1) * nx + x];
                 }
             }
             sTn[c] = T; sB[c] = T;
@@ -356,10 +417,9 @@ k_heat_fast(const DevParams p, const typename P::tst *__restrict__ Tin, typename
     // are rewritten; neighbours are read from sA = lambda and sax/say) ----
     // k_a = 6 w_a lambda_face / (rho c), lambda_face = harmonic mean
     const float w1 = 1.0f / 9.0f, w2 = 1.0f / 36.0f;
-    const float sqTc = float(sqrt(p.Tc));
-    for (int hy = ty; hy < SH; hy += BYH) {
-        for (int hx = tx; hx < SW; hx += BXH) {
-            const int c = hy * SW + hx;
+    for (int c = tid; c < NC; c += NTH) {
+        const int hy = c / SW, hx = c - (c / SW) * SW;
+        {
             const unsigned char kd = kind[c];
             float kk[8] = {0, 0, 0, 0, 0, 0, 0, 0};
             float ks = 0.0f, c1 = 0.0f, c2 = 0.0f;
@@ -384,11 +444,11 @@ k_heat_fast(const DevParams p, const typename P::tst *__restrict__ Tin, typename
                     const float divu = -(dx + dy);  // 3 (sum w e.u) with the -3 folded out
                     // (dp/dT)_rho = A + B / sqrt(T) (Eq. 13), rho-only A, B
                     const float rho = sRho[c];
-                    const float br = float(p.b) * rho;
+                    const float br = p.b * rho;
                     const float iden = fast_rcp(1.0f + br * (2.0f - br));
-                    const float pa = float(p.a * p.kappa) * rho * rho * iden;
-                    const float A = rho * float(p.R) * fast_rcp(1.0f - br) - pa * float(p.kappa / p.Tc);
-                    const float B = pa * float((1.0 + p.kappa)) * (1.0f / sqTc);
+                    const float pa = p.a_kappa * rho * rho * iden;
+                    const float A = rho * p.R * fast_rcp(1.0f - br) - pa * p.kappa_over_Tc;
+                    const float B = pa * p.B_coef;
                     const float g0 = -divu * fast_rcp(sRcv[c]);
                     c1 = g0 * A;   // times T
                     c2 = g0 * B;   // times sqrt(T)
@@ -402,63 +462,63 @@ k_heat_fast(const DevParams p, const typename P::tst *__restrict__ Tin, typename
         }
     }
     __syncthreads();
-    for (int hy = ty; hy < SH; hy += BYH)
-        for (int hx = tx; hx < SW; hx += BXH) sA[hy * SW + hx] = sTn[hy * SW + hx];
+    for (int c = tid; c < NC; c += NTH) sA[c] = sTn[c];
     __syncthreads();
 
-    // ---- four RK stages on shrinking regions ----
-    const float tsat = float(p.T_sat);
-    if (!iso) {
-        #pragma unroll 1
-        for (int st = 0; st < 4; st++) {
-            const int m = 1 + st;
-            const float *Tk = (st == 0) ? sTn : ((st == 2) ? sB : sA);
-            float *To = (st == 1) ? sB : sA;
-            for (int hy = m + ty; hy < SH - m; hy += BYH) {
-                for (int hx = m + tx; hx < SW - m; hx += BXH) {
-                    const int c = hy * SW + hx;
-                    const unsigned char kd = kind[c];
-                    if (kd != 1 && kd != 2) continue;
-                    const float T0 = Tk[c];
-                    const float T1 = Tk[c + 1], T2 = Tk[c + SW], T3 = Tk[c - 1], T4 = Tk[c - SW];
-                    const float T5 = Tk[c + SW + 1], T6 = Tk[c + SW - 1], T7 = Tk[c - SW - 1], T8 = Tk[c - SW + 1];
-                    float h = sk[c] * T1 + sk[NC + c] * T2 + sk[2 * NC + c] * T3 + sk[3 * NC + c] * T4 +
-                              sk[4 * NC + c] * T5 + sk[5 * NC + c] * T6 + sk[6 * NC + c] * T7 +
-                              sk[7 * NC + c] * T8 - sks[c] * T0;
-                    if (kd == 2) {
-                        const float a = T5 - T7, b = T8 - T6;
-                        const float gx = w1 * (T1 - T3) + w2 * (a + b);
-                        const float gy = w1 * (T2 - T4) + w2 * (a - b);
-                        const float Ta = fmaxf(T0 + tsat, 1e-30f);
-                        h += sax[c] * gx + say[c] * gy + sc1[c] * Ta + sc2[c] * fast_sqrt(Ta);
-                    }
-                    const bool in_tile = hx >= H && hx < H + TX && hy >= H && hy < H + TY;
-                    const int ai = (hy - H) * TX + (hx - H);
-                    const float Tn = sTn[c];
-                    if (st == 0) {
-                        if (in_tile) sAcc[ai] = h;
-                        To[c] = Tn + 0.5f * h;
-                    } else if (st == 1) {
-                        if (in_tile) sAcc[ai] += 2.0f * h;
-                        To[c] = Tn + 0.5f * h;
-                    } else if (st == 2) {
-                        if (in_tile) sAcc[ai] += 2.0f * h;
-                        To[c] = Tn + h;
-                    } else {
-                        sAcc[ai] += h;
-                    }
-                }
+    // ---- four RK stages on shrinking regions (region width a compile-time
+    // constant per stage, cells dealt out densely) ----
+    const float tsat = p.T_sat;
+    auto stage = [&](auto mtag, const float *Tk, float *To) {
+        constexpr int m = decltype(mtag)::value;
+        constexpr int st = m - 1;
+        constexpr int RW = SW - 2 * m, RH = SH - 2 * m;
+        for (int q = tid; q < RW * RH; q += NTH) {
+            const int hy = m + q / RW, hx = m + (q - (q / RW) * RW);
+            const int c = hy * SW + hx;
+            const unsigned char kd = kind[c];
+            if (kd != 1 && kd != 2) continue;
+            const float T0 = Tk[c];
+            const float T1 = Tk[c + 1], T2 = Tk[c + SW], T3 = Tk[c - 1], T4 = Tk[c - SW];
+            const float T5 = Tk[c + SW + 1], T6 = Tk[c + SW - 1], T7 = Tk[c - SW - 1], T8 = Tk[c - SW + 1];
+            float h = sk[c] * T1 + sk[NC + c] * T2 + sk[2 * NC + c] * T3 + sk[3 * NC + c] * T4 +
+                      sk[4 * NC + c] * T5 + sk[5 * NC + c] * T6 + sk[6 * NC + c] * T7 +
+                      sk[7 * NC + c] * T8 - sks[c] * T0;
+            if (kd == 2) {
+                const float a = T5 - T7, b = T8 - T6;
+                const float gx = w1 * (T1 - T3) + w2 * (a + b);
+                const float gy = w1 * (T2 - T4) + w2 * (a - b);
+                const float Ta = fmaxf(T0 + tsat, 1e-30f);
+                h += sax[c] * gx + say[c] * gy + sc1[c] * Ta + sc2[c] * fast_sqrt(Ta);
             }
-            __syncthreads();
+            const bool in_tile = hx >= H && hx < H + TX && hy >= H && hy < H + TY;
+            const int ai = (hy - H) * TX + (hx - H);
+            const float Tn = sTn[c];
+            if constexpr (st == 0) {
+                if (in_tile) sAcc[ai] = h;
+                To[c] = Tn + 0.5f * h;
+            } else if constexpr (st == 1) {
+                if (in_tile) sAcc[ai] += 2.0f * h;
+                To[c] = Tn + 0.5f * h;
+            } else if constexpr (st == 2) {
+                if (in_tile) sAcc[ai] += 2.0f * h;
+                To[c] = Tn + h;
+            } else {
+                sAcc[ai] += h;
+            }
         }
+        __syncthreads();
+    };
+    if (!iso) {
+        stage(std::integral_constant<int, 1>{}, sTn, sA);
+        stage(std::integral_constant<int, 2>{}, sA, sB);
+        stage(std::integral_constant<int, 3>{}, sB, sA);
+        stage(std::integral_constant<int, 4>{}, sA, nullptr);
     }
     // ---- write ----
-    for (int yy = ty; yy < TY; yy += BYH) {
-        const int row = r0 + yy;
-        if (row >= nt) break;
-        for (int xx = tx; xx < TX; xx += BXH) {
-            const int x = x0 + xx;
-            if (x >= nx) break;
+    for (int a = tid; a < TX * TY; a += NTH) {
+        const int yy = a / TX, xx = a - (a / TX) * TX;
+        const int row = r0 + yy, x = x0 + xx;
+        if (row < nt && x < nx) {
             const int c = (yy + H) * SW + (xx + H);
             const unsigned char kd = kind[c];
             float v = sTn[c];
@@ -473,7 +533,7 @@ k_heat_fast(const DevParams p, const typename P::tst *__restrict__ Tin, typename
 // ---- diagnostics for the FP32 path: per-column flux in FP32, FP64 sums ----
 template <class P, int NT>
 __global__ void __launch_bounds__(NT)
-k_diag_fast(const DevParams p, const float *__restrict__ T, const float *__restrict__ rho,
+k_diag_fast(const FParams p, const float *__restrict__ T, const float *__restrict__ rho,
             const double *__restrict__ part, int nblk, double *__restrict__ q_top, double *__restrict__ series,
             int cap, double *__restrict__ last, long long *__restrict__ stepp) {
     __shared__ double sh[2][NT / 32];
@@ -487,7 +547,7 @@ k_diag_fast(const DevParams p, const float *__restrict__ T, const float *__restr
     block_sum2<NT>(mass, nvap, sh);
     __syncthreads();
     double qb = 0.0, qt = 0.0;
-    const float lams = float(p.lambda_s), cvchi = float(p.cv_chi);
+    const float lams = p.lambda_s, cvchi = p.cv_chi;
     if (!py && ns >= 3) {
         for (int x = threadIdx.x; x < nx; x += NT) {
             // theta differences: T_sat cancels in the gradients
@@ -522,7 +582,7 @@ struct FlowFastShape {
     static int blocks(const DevParams &p) { dim3 g = grid(p); return (int)(g.x * g.y); }
     static cudaError_t launch(const DevParams &p, const StepBuffers &b, cudaStream_t s) {
         k_flow_fast<P, BX, BY, RY, MINB><<<grid(p), dim3(BX, BY), 0, s>>>(
-            p, (const typename P::fst *)b.f_in, (typename P::fst *)b.f_out, (const typename P::tst *)b.T_in,
+            make_fparams(p), (const typename P::fst *)b.f_in, (typename P::fst *)b.f_out, (const typename P::tst *)b.T_in,
             (float *)b.rho, (float *)b.ux, (float *)b.uy, b.cw, b.part, b.err);
         return cudaGetLastError();
     }
@@ -538,7 +598,7 @@ struct HeatFastShape {
     static cudaError_t launch(const DevParams &p, const StepBuffers &b, cudaStream_t s) {
         dim3 g((p.nx + TX - 1) / TX, (p.nt + TY - 1) / TY);
         k_heat_fast<P, TX, TY, BXH, BYH><<<g, dim3(BXH, BYH), smem, s>>>(
-            p, (const typename P::tst *)b.T_in, (typename P::tst *)b.T_out, (const float *)b.rho,
+            make_fparams(p), (const typename P::tst *)b.T_in, (typename P::tst *)b.T_out, (const float *)b.rho,
             (const float *)b.ux, (const float *)b.uy, b.step, b.err);
         return cudaGetLastError();
     }
@@ -546,7 +606,7 @@ struct HeatFastShape {
 
 template <class P, int NT>
 cudaError_t launch_diag_fast(const DevParams &p, const StepBuffers &b, int nblk, cudaStream_t s) {
-    k_diag_fast<P, NT><<<1, NT, 0, s>>>(p, (const float *)b.T_out, (const float *)b.rho, b.part, nblk, b.q_top,
+    k_diag_fast<P, NT><<<1, NT, 0, s>>>(make_fparams(p), (const float *)b.T_out, (const float *)b.rho, b.part, nblk, b.q_top,
                                         b.series, b.series_cap, b.last, b.step);
     return cudaGetLastError();
 }

