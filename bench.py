@@ -35,6 +35,13 @@ METRIC = "MLUPS (fluid-site updates per second), one GB300"
 # read + written, temperature read)
 ALG_STEP_BYTES = {"fp32": 80, "fp64": 160, "fp16": 44}
 ALG_FLOW_BYTES = {"fp32": 76, "fp64": 152, "fp16": 40}
+# arithmetic of the heat kernel per temperature site and step: four RK
+# stages of ~46 flops (9-point conduction with link weights, Eq. 27 gradient,
+# advection, the C1 T + C2 sqrt(T) source, stage update) plus ~90 flops of
+# per-step coefficients (harmonic means, div u, EOS factors)
+HEAT_FLOPS = 274
+# FP32 peak from unit counts and clock: 152 SMs x 128 FP32 lanes x 2 flops x clock
+FP32_LANES = 152 * 128
 PROFILE = os.path.join(ROOT, "profiles", "flow_kernel_2048x2048_fp32.md")
 
 
@@ -47,10 +54,23 @@ def peaks():
         return 6800.0, "fallback"
 
 
+KERNEL_SOURCES = ("lbm_device.cuh", "lbm_fast.cuh")
+
+
+def max_sm_mhz() -> float:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["sm_max_mhz"])
+    except Exception:
+        return 2070.0
+
+
 def kernel_source_hash() -> str:
+    """Hash of the kernel sources; an ncu summary taken on other sources is stale."""
     h = hashlib.sha256()
-    with open(os.path.join(ROOT, "paper_1911_10747_gb300", "csrc", "lbm_device.cuh"), "rb") as fh:
-        h.update(fh.read())
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1911_10747_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
     return h.hexdigest()[:16]
 
 
@@ -189,7 +209,10 @@ def run_ours(args):
         if ws > 1:
             torch.distributed.barrier()
 
-    # warm-up (also builds the two-step graph)
+    # launch-shape autotuning (does not advance the run), then warm-up (also
+    # builds the two-step graph)
+    tuned_ms = run.autotune(5)
+    variants = run.variants()
     run.step(max(args.warmup, 3))
     run.sync()
     # ---- timed region: K steps, CUDA events on the run's stream ----
@@ -218,10 +241,18 @@ def run_ours(args):
     run.set_timing(False)
     hbm, peak_kind = peaks()
     flow_bytes = ALG_FLOW_BYTES[args.precision] * sites
-    achieved = flow_bytes / (kms[0] / 1e3) / 1e9
-    traffic = ncu_traffic() if args.precision == "fp32" else None
+    flow_achieved = flow_bytes / (kms[0] / 1e3) / 1e9
+    flow_roof = {"bound": "hbm", "achieved": flow_achieved, "peak": hbm, "unit": "GB/s",
+                 "frac": flow_achieved / hbm, "kernel": "k_flow", "bytes_per_site": ALG_FLOW_BYTES[args.precision],
+                 "traffic": ncu_traffic() if args.precision == "fp32" else None, "peak_source": peak_kind}
+    fp32_peak = FP32_LANES * 2 * max_sm_mhz() * 1e6 / 1e12
+    heat_achieved = HEAT_FLOPS * cfg.temperature_sites / (kms[1] / 1e3) / 1e12
+    heat_roof = {"bound": "alu", "achieved": heat_achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                 "frac": heat_achieved / fp32_peak, "kernel": "k_heat", "flops_per_site": HEAT_FLOPS,
+                 "traffic": None, "peak_source": "152 SMs x 128 FP32 lanes x 2 x max SM clock"}
     step_ms = ms_max / args.steps
     step_achieved = ALG_STEP_BYTES[args.precision] * sites / (step_ms / 1e3) / 1e9
+    dominant = flow_roof if kms[0] >= kms[1] else heat_roof
 
     # ---- end to end through the C ABI with pinned host buffers ----
     e2e = None
@@ -287,12 +318,13 @@ def run_ours(args):
                        "nx": cfg.nx, "ny_fluid": cfg.nf, "ny_solid": cfg.ns,
                        "l2": "inputs larger than L2 (populations alone 2 x 151 MB in FP32)",
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single run"},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                         "frac": achieved / hbm, "traffic": traffic, "kernel": "k_flow",
-                         "peak_source": peak_kind,
-                         "step": {"achieved": step_achieved, "frac": step_achieved / hbm,
-                                  "bytes_per_site": ALG_STEP_BYTES[args.precision]}},
+            "roofline": dict(dominant, step={"bound": "hbm", "achieved": step_achieved, "peak": hbm,
+                                             "frac": step_achieved / hbm,
+                                             "bytes_per_site": ALG_STEP_BYTES[args.precision]}),
+            "kernel_rooflines": {"flow": flow_roof, "heat": heat_roof},
             "kernel_ms": {"flow": kms[0], "heat": kms[1], "diag": kms[2], "launches_timed": nl},
+            "variants": {"flow": variants["flow"][variants["selected"][0]],
+                         "heat": variants["heat"][variants["selected"][1]]},
             "gpu_launches": kps * args.steps,
             "clocks": clk.summary(),
             "e2e": e2e,
