@@ -207,6 +207,39 @@ int lbm_select_variants(lbm_handle h, int flow, int heat);
  * receives the winning average milliseconds per launch.  Synchronises. */
 int lbm_autotune(lbm_handle h, int iters, double *best_ms);
 
+/* Diagnostics of one state without allocating device memory.  The paper has
+ * no counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc or cudaFree -- a host program whose device memory is owned by
+ * another allocator (for instance a framework's caching allocator holding
+ * the whole GPU), or a loop that must not risk the implicit device
+ * synchronisation of those calls.
+ *
+ * Inputs (device pointers, float64, row-major as in lbm_fields): rho
+ * [ny_fluid][nx] and T [ny_solid + ny_fluid][nx].  Output: out, a device
+ * pointer to 4 doubles receiving the same values as one row of lbm_series:
+ * mean heater-bottom flux (Eq. 36 with lambda_s, 0 if ny_solid < 3), mean
+ * heater-surface face flux (harmonic-mean conductance, cv_chi * rho in the
+ * fluid), vapour fraction (rho < (rho_L + rho_V) / 2) and mass.  Work is
+ * queued on `stream` (a cudaStream_t; NULL = legacy default stream) and the
+ * call returns without waiting.
+ *
+ * Scratch: per-block partial sums go to a file-scope device array of
+ * 16384 x 4 doubles (512 KiB) that every GPU loading the library keeps until
+ * the process exits; inputs larger than 16,777,216 fluid sites (16384 blocks
+ * of 1024 sites) are rejected with LBM_E_INVAL and a message.  No
+ * cudaMalloc, cudaFree or allocating library routine is called.  The first
+ * call on a device looks up the array's device address (cudaGetSymbolAddress,
+ * with that device current); make that first call before any stream capture.
+ * All calls share the array and leave their partials in it (each call writes
+ * every slot it reads, so nothing needs clearing): calls that overlap on the
+ * GPU race, so serialise them (one stream, or events).
+ * Errors: LBM_E_INVAL (NULL pointer, bad size, over capacity), LBM_E_CUDA (no
+ * current device, symbol lookup or launch failed); the message is returned
+ * by lbm_last_error(NULL). */
+int lbm_diagnostics_static(const double *rho, const double *T, int32_t nx, int32_t ny_fluid,
+                           int32_t ny_solid, double lambda_s, double cv_chi, double rho_L,
+                           double rho_V, double *out, void *stream);
+
 /* Message of the last error on h (or of the last failed lbm_create when h is
  * NULL).  Valid until the next call on the same handle. */
 const char *lbm_last_error(lbm_handle h);

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 namespace lbmgb {
 
 enum { FLAG_PERIODIC_Y = 1, FLAG_ISOTHERMAL = 2, FLAG_FROZEN_FLOW = 4 };
@@ -88,6 +90,9 @@ struct KernelSet {
     cudaError_t (*export_fields)(const DevParams &, const StepBuffers &, double *rho, double *ux,
                                  double *uy, double *T, double *f, cudaStream_t);
 };
+
+// Message returned by lbm_last_error(NULL) (thread-local).
+void set_global_error(const std::string &msg);
 
 const KernelSet *kernels_fp64();
 const KernelSet *kernels_fp32();

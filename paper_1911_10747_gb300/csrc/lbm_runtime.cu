@@ -52,6 +52,8 @@ struct lbm_run {
     std::string msg;
 };
 
+void lbmgb::set_global_error(const std::string &msg) { g_create_error = msg; }
+
 static int fail(lbm_run *h, int code, const std::string &m) {
     if (h) h->msg = m; else g_create_error = m;
     return code;

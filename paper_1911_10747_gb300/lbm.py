@@ -29,7 +29,8 @@ LBM_FIELD_RHO, LBM_FIELD_UX, LBM_FIELD_UY, LBM_FIELD_T, LBM_FIELD_F = 1, 2, 4, 8
 EXPORTS = ("lbm_create", "lbm_destroy", "lbm_step", "lbm_sync", "lbm_step_count", "lbm_fields",
            "lbm_set_state", "lbm_wall_heat_flux", "lbm_vapour_fraction", "lbm_mass", "lbm_series",
            "lbm_set_timing", "lbm_kernel_times", "lbm_kernels_per_step", "lbm_variants",
-           "lbm_variant_name", "lbm_select_variants", "lbm_autotune", "lbm_last_error",
+           "lbm_variant_name", "lbm_select_variants", "lbm_autotune", "lbm_diagnostics_static",
+           "lbm_last_error",
            "lbm_status_string")
 
 
@@ -112,6 +113,9 @@ def load(path: str = LIB_PATH):
     L.lbm_variant_name.restype = C.c_char_p
     L.lbm_select_variants.argtypes = [C.c_void_p, C.c_int, C.c_int]
     L.lbm_autotune.argtypes = [C.c_void_p, C.c_int, _D]
+    L.lbm_diagnostics_static.argtypes = [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_int32,
+                                         C.c_double, C.c_double, C.c_double, C.c_double, C.c_void_p,
+                                         C.c_void_p]
     L.lbm_last_error.argtypes = [C.c_void_p]
     L.lbm_last_error.restype = C.c_char_p
     L.lbm_status_string.argtypes = [C.c_int]
@@ -310,3 +314,12 @@ class Run:
         ms = (C.c_double * 2)()
         _check(load().lbm_autotune(self._h, int(iters), ms), self._h, "lbm_autotune")
         return list(ms)
+
+
+def diagnostics_static(rho_ptr: int, T_ptr: int, cfg, out_ptr: int, stream=None):
+    """Allocation-free diagnostics of a state held in float64 device arrays
+    (see lbm_diagnostics_static in include/lbm.h); out_ptr receives 4 doubles."""
+    rc = load().lbm_diagnostics_static(rho_ptr, T_ptr, cfg.nx, cfg.nf, cfg.ns, cfg.lambda_s, cfg.cv_chi,
+                                       cfg.rho_L, cfg.rho_V, out_ptr, stream)
+    _check(rc, None, "lbm_diagnostics_static")
+
