@@ -330,6 +330,260 @@ k_flow_fast(const FParams p, const typename P::fst *__restrict__ fin, typename P
     if (errbits) atomicOr(err, errbits);
 }
 
+template <class P, int BX, int BY, int RY, int MINB>
+__global__ void __launch_bounds__(BX *BY, MINB)
+k_flow_pers(const FParams p, int tiles_x, int ntiles, const typename P::fst *__restrict__ fin, typename P::fst *__restrict__ fout,
+            const typename P::tst *__restrict__ Tin, float *__restrict__ rho_o, float *__restrict__ ux_o,
+            float *__restrict__ uy_o, const double *__restrict__ cw, double *__restrict__ part,
+            unsigned *__restrict__ err) {
+    using S = typename P::fst;
+    constexpr int TX = BX, TY = BY * RY, SW = TX + 2, SH = TY + 2, NT = BX * BY;
+    __shared__ float s_psi[SH * SW];
+    __shared__ float s_red[2][NT / 32];
+
+    const int nx = p.nx, nf = p.nf;
+    const size_t plane = (size_t)nf * nx;
+    const bool py = (p.flags & FLAG_PERIODIC_Y) != 0;
+    const bool frozen = (p.flags & FLAG_FROZEN_FLOW) != 0;
+    const bool outflow = p.top_mode == TOP_OUTFLOW;
+    const int tid = threadIdx.y * BX + threadIdx.x;
+    const float rho0 = p.rho_shift;
+    const float tsat = p.T_sat;
+    unsigned errbits = 0;
+
+    float g[RY][9];
+    float dd[RY];
+    float gT[RY];
+    // populations and temperature of the next tile, loaded during this tile
+    float pg[RY][9];
+    float pTv[RY];
+    auto fetch = [&](int tile) {
+        const int x0 = (tile % tiles_x) * TX, y0 = (tile / tiles_x) * TY;
+        #pragma unroll
+        for (int r = 0; r < RY; r++) {
+            const int lx = threadIdx.x, ly = threadIdx.y + r * BY;
+            const int x = (x0 + lx < nx) ? x0 + lx : wrapi(x0 + lx, nx);
+            int y = y0 + ly;
+            const bool has = py || y < nf;
+            if (py) y = wrapi(y, nf);
+            if (has) {
+                const size_t k = (size_t)y * nx + x;
+                #pragma unroll
+                for (int i = 0; i < 9; i++) pg[r][i] = ld_as<float>(fin + i * plane + k);
+                pTv[r] = ld_as<float>(Tin + (size_t)(p.ns + y) * nx + x);
+            } else {
+                #pragma unroll
+                for (int i = 0; i < 9; i++) pg[r][i] = 0.0f;
+                pTv[r] = 0.0f;
+            }
+        }
+    };
+    float mass = 0.0f, nvap = 0.0f;
+    if ((int)blockIdx.x < ntiles) fetch(blockIdx.x);
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int x0 = (tile % tiles_x) * TX, y0 = (tile / tiles_x) * TY;
+    #pragma unroll
+    for (int r = 0; r < RY; r++) {
+        #pragma unroll
+        for (int i = 0; i < 9; i++) g[r][i] = pg[r][i];
+        gT[r] = pTv[r];
+    }
+    if (tile + (int)gridDim.x < ntiles) fetch(tile + gridDim.x);
+
+    // ---- own sites: density, psi ----
+    #pragma unroll
+    for (int r = 0; r < RY; r++) {
+        const int lx = threadIdx.x, ly = threadIdx.y + r * BY;
+        const int y = y0 + ly;
+        const bool has = py || y < nf;
+        float psi = 0.0f;
+        dd[r] = 0.0f;
+        if (has) {
+            const float d = ((g[r][0] + g[r][1]) + (g[r][2] + g[r][3])) + ((g[r][4] + g[r][5]) + (g[r][6] + g[r][7])) + g[r][8];
+            dd[r] = d;
+            if (!frozen) psi = psi_fast(p, d + rho0, gT[r] + tsat, errbits);
+        }
+        s_psi[(ly + 1) * SW + lx + 1] = psi;
+    }
+    // ---- halo ring ----
+    if (!frozen) {
+        for (int k = tid; k < 2 * SW + 2 * TY; k += NT) {
+            int hx, hy;
+            if (k < SW) { hx = k; hy = 0; }
+            else if (k < 2 * SW) { hx = k - SW; hy = SH - 1; }
+            else if (k < 2 * SW + TY) { hx = 0; hy = 1 + (k - 2 * SW); }
+            else { hx = SW - 1; hy = 1 + (k - 2 * SW - TY); }
+            const int x = wrapi(x0 + hx - 1, nx);
+            int y = y0 + hy - 1;
+            if (py) y = wrapi(y, nf);
+            float psi = 0.0f;
+            if (y >= 0 && y < nf) {
+                const size_t kk = (size_t)y * nx + x;
+                float v[9];
+                #pragma unroll
+                for (int i = 0; i < 9; i++) v[i] = ld_as<float>(fin + i * plane + kk);
+                const float d = ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7])) + v[8];
+                const float T = ld_as<float>(Tin + (size_t)(p.ns + y) * nx + x) + tsat;
+                psi = psi_fast(p, d + rho0, T, errbits);
+            }
+            s_psi[hy * SW + hx] = psi;
+        }
+    }
+    __syncthreads();
+
+    // ---- collide and push ----
+    const float w1 = 1.0f / 3.0f, w2 = 1.0f / 12.0f;
+    const float mG = p.mG;
+    const float inv_drho = p.inv_drho, dtau = p.dtau;
+    #pragma unroll
+    for (int r = 0; r < RY; r++) {
+        const int lx = threadIdx.x, ly = threadIdx.y + r * BY;
+        const int x = x0 + lx, y = y0 + ly;
+        if (x >= nx || y >= nf) continue;
+        const size_t k = (size_t)y * nx + x;
+        const float d = dd[r];
+        const float rho = d + rho0;
+        if (!(fabsf(rho) < 1e30f)) errbits |= ERRW_NONFINITE_RHO;
+        mass += rho;
+        nvap += (rho < p.vap_threshold) ? 1.0f : 0.0f;
+        if (frozen) {
+            #pragma unroll
+            for (int i = 0; i < 9; i++) st_as(fout + i * plane + k, g[r][i]);
+            rho_o[k] = rho;
+            ux_o[k] = 0.0f;
+            uy_o[k] = 0.0f;
+            continue;
+        }
+        const float *sp = s_psi + (ly + 1) * SW + (lx + 1);
+        const float psi = sp[0];
+        const float pE = sp[1], pW = sp[-1], pN = sp[SW], pS = sp[-SW];
+        float pNE = sp[SW + 1], pNW = sp[SW - 1];
+        const float pSW = sp[-SW - 1], pSE = sp[-SW + 1];
+        const bool bot = !py && y == 0, top = !py && y == nf - 1;
+        float pNx = pN;
+        if (top && outflow) { pNx = psi; pNE = pE; pNW = pW; }  // open top: zero normal gradient
+        const float a = pNE - pSW, b = pSE - pNW;
+        const float pre = mG * psi;
+        const float Fmx = pre * (w1 * (pE - pW) + w2 * (a + b));
+        const float Fmy = pre * (w1 * (pNx - pS) + w2 * (a - b));
+        const int xm = wrap1(x - 1, nx), xp = wrap1(x + 1, nx);
+        float Fax = 0.0f, Fay = 0.0f;
+        if (bot) {  // Eq. 14 with the heater sites below (i = 4, 7, 8)
+            const float cm = float(cw[xm]), c0 = float(cw[x]), cp = float(cw[xp]);
+            Fax = -psi * (w2 * (cp - cm));
+            Fay = psi * (w1 * c0 + w2 * (cm + cp));
+        }
+        if (top && !outflow) Fay += -psi * ((w1 + 2.0f * w2) * p.c_w_top);
+        const float Fx = Fmx + Fax;
+        const float Fy = (Fmy + Fay) - (rho - p.rho_mean) * p.g;
+
+        const float *f = g[r];
+        // moments of g (Eq. 6 with the rho0 shift of m0..m2 folded into q0..q2)
+        const float s14 = (f[1] + f[2]) + (f[3] + f[4]);
+        const float s58 = (f[5] + f[6]) + (f[7] + f[8]);
+        const float m1 = -4.0f * f[0] - s14 + 2.0f * s58;
+        const float m2 = 4.0f * f[0] - 2.0f * s14 + s58;
+        const float f13 = f[1] - f[3], f24 = f[2] - f[4];
+        const float f57 = f[5] - f[7], f86 = f[8] - f[6];
+        const float m3 = f13 + (f57 + f86);
+        const float m4 = -2.0f * f13 + (f57 + f86);
+        const float m5 = f24 + (f57 - f86);
+        const float m6 = -2.0f * f24 + (f57 - f86);
+        const float m7 = (f[1] + f[3]) - (f[2] + f[4]);
+        const float m8 = (f[5] + f[7]) - (f[6] + f[8]);
+        const float irho = fast_rcp(rho);
+        const float ux = (m3 + 0.5f * Fx) * irho, uy = (m5 + 0.5f * Fy) * irho;
+        const float tau = p.tau_V + (rho - p.rho_V) * inv_drho * dtau;
+        const float s78 = fast_rcp(tau);
+        const float ru2 = rho * (ux * ux + uy * uy);
+        const float q1 = -2.0f * d + 3.0f * ru2, q2 = d - 3.0f * ru2;
+        const float q3 = rho * ux, q5 = rho * uy;
+        const float q7 = rho * (ux * ux - uy * uy), q8 = rho * (ux * uy);
+        const float uF = ux * Fx + uy * Fy;
+        const float eps = (psi > 0.0f) ? p.varpi12 * (Fmx * Fmx + Fmy * Fmy) * fast_rcp(psi * psi) : 0.0f;
+        const float S1 = 6.0f * uF + eps * p.inv_tauem;
+        const float S2 = -6.0f * uF + eps * p.sgn_over_taus;
+        // Eq. 7 (m0 unchanged; q4 = -q3, q6 = -q5)
+        const float z1 = m1 - p.s[1] * (m1 - q1) + p.hs[1] * S1;
+        const float z2 = m2 - p.s[2] * (m2 - q2) + p.hs[2] * S2;
+        const float z3 = m3 - p.s[3] * (m3 - q3) + p.hs[3] * Fx;
+        const float z4 = m4 - p.s[4] * (m4 + q3) - p.hs[4] * Fx;
+        const float z5 = m5 - p.s[5] * (m5 - q5) + p.hs[5] * Fy;
+        const float z6 = m6 - p.s[6] * (m6 + q5) - p.hs[6] * Fy;
+        const float h78 = 1.0f - 0.5f * s78;
+        const float z7 = m7 - s78 * (m7 - q7) + h78 * (2.0f * (ux * Fx - uy * Fy));
+        const float z8 = m8 - s78 * (m8 - q8) + h78 * (ux * Fy + uy * Fx);
+        const float e0 = d * (1.0f / 9.0f), e1 = z1 * (1.0f / 36.0f), e2 = z2 * (1.0f / 36.0f);
+        const float e3 = z3 * (1.0f / 6.0f), e4 = z4 * (1.0f / 12.0f), e5 = z5 * (1.0f / 6.0f);
+        const float e6 = z6 * (1.0f / 12.0f), e7 = z7 * 0.25f, e8 = z8 * 0.25f;
+        const float A0 = e0 - e1 - 2.0f * e2;       // axis-direction common part
+        const float B0 = e0 + 2.0f * e1 + e2;       // diagonal common part
+        const float fo0 = e0 - 4.0f * e1 + 4.0f * e2;
+        const float fo1 = A0 + (e3 - 2.0f * e4) + e7;
+        const float fo3 = A0 - (e3 - 2.0f * e4) + e7;
+        const float fo2 = A0 + (e5 - 2.0f * e6) - e7;
+        const float fo4 = A0 - (e5 - 2.0f * e6) - e7;
+        const float cxx = e3 + e4, cyy = e5 + e6;
+        const float fo5 = B0 + cxx + cyy + e8;
+        const float fo6 = B0 - cxx + cyy - e8;
+        const float fo7 = B0 - cxx - cyy + e8;
+        const float fo8 = B0 + cxx - cyy - e8;
+        rho_o[k] = rho;
+        ux_o[k] = ux;
+        uy_o[k] = uy;
+        // Eq. 8, push; halfway bounce-back at the heater and the top wall
+        S *o = fout;
+        const size_t ro = (size_t)y * nx;
+        st_as(o + ro + x, fo0);
+        st_as(o + plane + ro + xp, fo1);
+        st_as(o + 3 * plane + ro + xm, fo3);
+        const size_t ru = (size_t)(py && y == nf - 1 ? 0 : y + 1) * nx;
+        const size_t rd = (size_t)(py && y == 0 ? nf - 1 : y - 1) * nx;
+        if (!top) {
+            st_as(o + 2 * plane + ru + x, fo2);
+            st_as(o + 5 * plane + ru + xp, fo5);
+            st_as(o + 6 * plane + ru + xm, fo6);
+        } else if (!outflow) {
+            st_as(o + 4 * plane + ro + x, fo2);
+            st_as(o + 7 * plane + ro + x, fo5);
+            st_as(o + 8 * plane + ro + x, fo6);
+        }
+        if (!bot) {
+            st_as(o + 4 * plane + rd + x, fo4);
+            st_as(o + 7 * plane + rd + xm, fo7);
+            st_as(o + 8 * plane + rd + xp, fo8);
+        } else {
+            st_as(o + 2 * plane + ro + x, fo4);
+            st_as(o + 5 * plane + ro + x, fo7);
+            st_as(o + 6 * plane + ro + x, fo8);
+        }
+        if (top && outflow) {
+            st_as(o + 4 * plane + ro + x, fo4);
+            st_as(o + 7 * plane + ro + xm, fo7);
+            st_as(o + 8 * plane + ro + xp, fo8);
+        }
+    }
+    __syncthreads();  // s_psi is rewritten by the next tile
+    }
+    // per-block mass and vapour count: FP32 inside the block, FP64 across blocks
+    #pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        mass += __shfl_down_sync(0xffffffffu, mass, o);
+        nvap += __shfl_down_sync(0xffffffffu, nvap, o);
+    }
+    if ((tid & 31) == 0) { s_red[0][tid >> 5] = mass; s_red[1][tid >> 5] = nvap; }
+    __syncthreads();
+    if (tid == 0) {
+        double m = 0.0, v = 0.0;
+        #pragma unroll
+        for (int w = 0; w < NT / 32; w++) { m += (double)s_red[0][w]; v += (double)s_red[1][w]; }
+        const int bi = blockIdx.y * gridDim.x + blockIdx.x;
+        part[2 * bi] = m;
+        part[2 * bi + 1] = v;
+    }
+    if (errbits) atomicOr(err, errbits);
+}
+
 // ============================================================================
 // Heat kernel, FP32.  Output tile TX x TY, 4-cell halo.  Shared arrays per
 // cell: three temperature buffers, eight link coefficients k_a, their sum,
@@ -578,6 +832,7 @@ k_diag_fast(const FParams p, const float *__restrict__ T, const float *__restric
 
 template <class P, int BX, int BY, int RY, int MINB>
 struct FlowFastShape {
+    static cudaError_t prepare() { return cudaSuccess; }
     static dim3 grid(const DevParams &p) { return dim3((p.nx + BX - 1) / BX, (p.nf + BY * RY - 1) / (BY * RY)); }
     static int blocks(const DevParams &p) { dim3 g = grid(p); return (int)(g.x * g.y); }
     static cudaError_t launch(const DevParams &p, const StepBuffers &b, cudaStream_t s) {
@@ -587,6 +842,30 @@ struct FlowFastShape {
         return cudaGetLastError();
     }
 };
+
+template <class P, int BX, int BY, int RY, int MINB>
+struct FlowPersShape {
+    static int grid_blocks;
+    static cudaError_t prepare() {
+        int dev = 0, sms = 0, per = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_flow_pers<P, BX, BY, RY, MINB>, BX * BY, 0);
+        if (e != cudaSuccess) return e;
+        grid_blocks = sms * (per > 0 ? per : 1);
+        return cudaSuccess;
+    }
+    static int tiles(const DevParams &p) { return ((p.nx + BX - 1) / BX) * ((p.nf + BY * RY - 1) / (BY * RY)); }
+    static int blocks(const DevParams &p) { const int t = tiles(p); return t < grid_blocks ? t : grid_blocks; }
+    static cudaError_t launch(const DevParams &p, const StepBuffers &b, cudaStream_t s) {
+        k_flow_pers<P, BX, BY, RY, MINB><<<blocks(p), dim3(BX, BY), 0, s>>>(
+            make_fparams(p), (p.nx + BX - 1) / BX, tiles(p), (const typename P::fst *)b.f_in, (typename P::fst *)b.f_out,
+            (const typename P::tst *)b.T_in, (float *)b.rho, (float *)b.ux, (float *)b.uy, b.cw, b.part, b.err);
+        return cudaGetLastError();
+    }
+};
+template <class P, int BX, int BY, int RY, int MINB>
+int FlowPersShape<P, BX, BY, RY, MINB>::grid_blocks = 152;
 
 template <class P, int TX, int TY, int BXH, int BYH>
 struct HeatFastShape {
@@ -610,5 +889,405 @@ cudaError_t launch_diag_fast(const DevParams &p, const StepBuffers &b, int nblk,
                                         b.series, b.series_cap, b.last, b.step);
     return cudaGetLastError();
 }
+
+}  // namespace lbmgb
+
+namespace lbmgb {
+
+// ============================================================================
+// Heat kernel, FP32, register-resident variant.  A block covers 32 columns x
+// SH = NWARP * CPT rows of cells (4-cell halo on every side, so 24 x (SH - 8)
+// outputs).  Lane = column, warp w owns rows w, w + NWARP, ...  Each thread
+// keeps its cells' per-step coefficients (8 link weights and their sum,
+// -3u, C1, C2), T^n and the RK accumulator in registers for all four
+// stages; a stage exchanges only the stage temperature: the row above and
+// below through shared memory, the left and right columns by warp shuffle.
+// Same arithmetic as k_heat_fast.
+// ============================================================================
+template <class P, int NWARP, int CPT>
+__global__ void __launch_bounds__(NWARP * 32, (NWARP * 32 <= 512) ? 2 : 1)
+k_heat_reg(const FParams p, const typename P::tst *__restrict__ Tin, typename P::tst *__restrict__ Tout,
+           const float *__restrict__ rho_i, const float *__restrict__ ux_i, const float *__restrict__ uy_i,
+           const long long *__restrict__ stepp, unsigned *__restrict__ err) {
+    constexpr int H = 4, SH = NWARP * CPT, TXO = 32 - 2 * H, TYO = SH - 2 * H;
+    __shared__ float sT[2][SH][32];
+    __shared__ float sLam[SH][32], sUx[SH][32], sUy[SH][32];
+    const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5;
+    const int nx = p.nx, nt = p.nt, ns = p.ns, nf = p.nf;
+    const bool py = (p.flags & FLAG_PERIODIC_Y) != 0;
+    const bool iso = (p.flags & FLAG_ISOTHERMAL) != 0;
+    const int x0 = blockIdx.x * TXO, r0 = blockIdx.y * TYO;
+    const int x = wrapi(x0 + lane - H, nx);
+    const long long n = *stepp;
+    unsigned errbits = 0;
+
+    float Tn[CPT], acc[CPT], kk[CPT][8], ks[CPT], ax[CPT], ay[CPT], c1[CPT], c2[CPT], rcv[CPT], rho[CPT];
+    int kd[CPT];  // 0 outside, 1 solid, 2 fluid, 3 fixed (bottom Dirichlet row / top ghost)
+
+    // ---- load ----
+    #pragma unroll
+    for (int c = 0; c < CPT; c++) {
+        const int hy = wy + c * NWARP;
+        int row = r0 + hy - H;
+        int k;
+        if (py) { row = wrapi(row, nt); k = 2; }
+        else if (row < 0 || row > nt) k = 0;
+        else if (row == 0 || row == nt) k = 3;
+        else k = (row < ns) ? 1 : 2;
+        float T = 0.0f, lam = 0.0f, ux = 0.0f, uy = 0.0f, rc = 1.0f, r = 0.0f;
+        if (k == 1) {
+            T = Tin[(size_t)row * nx + x];
+            lam = p.lambda_s;
+            rc = p.rho_c_s;
+        } else if (k == 2) {
+            const size_t kf = (size_t)(row - ns) * nx + x;
+            T = Tin[(size_t)row * nx + x];
+            r = rho_i[kf];
+            ux = ux_i[kf];
+            uy = uy_i[kf];
+            lam = p.cv_chi * r;
+            rc = r * p.c_v;
+        } else if (k == 3) {
+            if (row == 0) {
+                T = bottom_theta(p, x, n);
+                lam = p.lambda_s;
+            } else {
+                lam = p.cv_chi * rho_i[(size_t)(nf - 1) * nx + x];
+            }
+        }
+        kd[c] = k;
+        Tn[c] = T;
+        rcv[c] = rc;
+        rho[c] = r;
+        sT[0][hy][lane] = T;
+        sT[1][hy][lane] = T;
+        sLam[hy][lane] = lam;
+        sUx[hy][lane] = ux;
+        sUy[hy][lane] = uy;
+    }
+    __syncthreads();
+    // ---- per-step coefficients ----
+    const float w1 = 1.0f / 9.0f, w2 = 1.0f / 36.0f;
+    #pragma unroll
+    for (int c = 0; c < CPT; c++) {
+        const int hy = wy + c * NWARP;
+        #pragma unroll
+        for (int a = 0; a < 8; a++) kk[c][a] = 0.0f;
+        ks[c] = 0.0f; ax[c] = 0.0f; ay[c] = 0.0f; c1[c] = 0.0f; c2[c] = 0.0f;
+        acc[c] = 0.0f;
+        const bool inner = hy >= 1 && hy < SH - 1 && lane >= 1 && lane < 31;
+        if (inner && (kd[c] == 1 || kd[c] == 2)) {
+            const float l0 = sLam[hy][lane];
+            const float inv6 = 6.0f * fast_rcp(rcv[c]);
+            const float la[8] = {sLam[hy][lane + 1], sLam[hy + 1][lane], sLam[hy][lane - 1], sLam[hy - 1][lane],
+                                 sLam[hy + 1][lane + 1], sLam[hy + 1][lane - 1], sLam[hy - 1][lane - 1],
+                                 sLam[hy - 1][lane + 1]};
+            #pragma unroll
+            for (int a = 0; a < 8; a++) {
+                const float hm = 2.0f * l0 * la[a] * fast_rcp(l0 + la[a]);
+                kk[c][a] = (a < 4 ? w1 : w2) * hm * inv6;
+                ks[c] += kk[c][a];
+            }
+            if (kd[c] == 2) {
+                ax[c] = -3.0f * sUx[hy][lane];
+                ay[c] = -3.0f * sUy[hy][lane];
+                const float dx = w1 * (sUx[hy][lane + 1] - sUx[hy][lane - 1]) +
+                                 w2 * ((sUx[hy + 1][lane + 1] - sUx[hy - 1][lane - 1]) +
+                                       (sUx[hy - 1][lane + 1] - sUx[hy + 1][lane - 1]));
+                const float dy = w1 * (sUy[hy + 1][lane] - sUy[hy - 1][lane]) +
+                                 w2 * ((sUy[hy + 1][lane + 1] - sUy[hy - 1][lane - 1]) -
+                                       (sUy[hy - 1][lane + 1] - sUy[hy + 1][lane - 1]));
+                const float divu = 3.0f * (dx + dy);
+                const float br = p.b * rho[c];
+                const float iden = fast_rcp(1.0f + br * (2.0f - br));
+                const float pa = p.a_kappa * rho[c] * rho[c] * iden;
+                const float A = rho[c] * p.R * fast_rcp(1.0f - br) - pa * p.kappa_over_Tc;
+                const float B = pa * p.B_coef;
+                const float g0 = -divu * fast_rcp(rcv[c]);
+                c1[c] = g0 * A;
+                c2[c] = g0 * B;
+            }
+        }
+    }
+    // ---- four RK stages ----
+    if (!iso) {
+        #pragma unroll
+        for (int st = 0; st < 4; st++) {
+            const int m = st + 1;
+            const int rb = st & 1, wb = rb ^ 1;
+            #pragma unroll
+            for (int c = 0; c < CPT; c++) {
+                const int hy = wy + c * NWARP;
+                const float T0 = sT[rb][hy][lane];
+                const float Tu = (hy + 1 < SH) ? sT[rb][hy + 1][lane] : 0.0f;
+                const float Td = (hy >= 1) ? sT[rb][hy - 1][lane] : 0.0f;
+                const float T1 = __shfl_down_sync(0xffffffffu, T0, 1);
+                const float T3 = __shfl_up_sync(0xffffffffu, T0, 1);
+                const float T5 = __shfl_down_sync(0xffffffffu, Tu, 1);
+                const float T6 = __shfl_up_sync(0xffffffffu, Tu, 1);
+                const float T8 = __shfl_down_sync(0xffffffffu, Td, 1);
+                const float T7 = __shfl_up_sync(0xffffffffu, Td, 1);
+                const bool act = hy >= m && hy < SH - m && lane >= m && lane < 32 - m && (kd[c] == 1 || kd[c] == 2);
+                if (act) {
+                    float h = kk[c][0] * T1 + kk[c][1] * Tu + kk[c][2] * T3 + kk[c][3] * Td + kk[c][4] * T5 +
+                              kk[c][5] * T6 + kk[c][6] * T7 + kk[c][7] * T8 - ks[c] * T0;
+                    if (kd[c] == 2) {
+                        const float a = T5 - T7, b = T8 - T6;
+                        const float gx = w1 * (T1 - T3) + w2 * (a + b);
+                        const float gy = w1 * (Tu - Td) + w2 * (a - b);
+                        const float Ta = fmaxf(T0 + p.T_sat, 1e-30f);
+                        h += ax[c] * gx + ay[c] * gy + c1[c] * Ta + c2[c] * fast_sqrt(Ta);
+                    }
+                    if (st == 0) { acc[c] = h; sT[wb][hy][lane] = Tn[c] + 0.5f * h; }
+                    else if (st == 1) { acc[c] += 2.0f * h; sT[wb][hy][lane] = Tn[c] + 0.5f * h; }
+                    else if (st == 2) { acc[c] += 2.0f * h; sT[wb][hy][lane] = Tn[c] + h; }
+                    else { acc[c] += h; }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    // ---- write the tile ----
+    #pragma unroll
+    for (int c = 0; c < CPT; c++) {
+        const int hy = wy + c * NWARP;
+        const int row = r0 + hy - H, xo = x0 + lane - H;
+        if (lane >= H && lane < 32 - H && hy >= H && hy < SH - H && row < nt && xo < nx) {
+            float v = Tn[c];
+            if ((kd[c] == 1 || kd[c] == 2) && !iso) v = Tn[c] + acc[c] * (1.0f / 6.0f);
+            if (!(fabsf(v) < 1e30f)) errbits |= ERRW_NONFINITE_T;
+            Tout[(size_t)row * nx + xo] = v;
+        }
+    }
+    if (errbits) atomicOr(err, errbits);
+}
+
+template <class P, int NWARP, int CPT>
+__global__ void __launch_bounds__(NWARP * 32, (NWARP * 32 <= 512) ? 2 : 1)
+k_heat_pers(const FParams p, int tiles_x, int ntiles, const typename P::tst *__restrict__ Tin, typename P::tst *__restrict__ Tout,
+           const float *__restrict__ rho_i, const float *__restrict__ ux_i, const float *__restrict__ uy_i,
+           const long long *__restrict__ stepp, unsigned *__restrict__ err) {
+    constexpr int H = 4, SH = NWARP * CPT, TXO = 32 - 2 * H, TYO = SH - 2 * H;
+    __shared__ float sT[2][SH][32];
+    __shared__ float sLam[SH][32], sUx[SH][32], sUy[SH][32];
+    const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5;
+    const int nx = p.nx, nt = p.nt, ns = p.ns, nf = p.nf;
+    const bool py = (p.flags & FLAG_PERIODIC_Y) != 0;
+    const bool iso = (p.flags & FLAG_ISOTHERMAL) != 0;
+    const long long n = *stepp;
+    unsigned errbits = 0;
+
+    float Tn[CPT], acc[CPT], kk[CPT][8], ks[CPT], ax[CPT], ay[CPT], c1[CPT], c2[CPT], rcv[CPT], rho[CPT];
+    int kd[CPT];  // 0 outside, 1 solid, 2 fluid, 3 fixed (bottom Dirichlet row / top ghost)
+    // raw inputs of the next tile, loaded while the current one is computed
+    float pT[CPT], pr[CPT], pux[CPT], puy[CPT];
+
+    auto classify = [&](int tile, int c, int &row, int &x) {
+        const int x0 = (tile % tiles_x) * TXO, r0 = (tile / tiles_x) * TYO;
+        const int hy = wy + c * NWARP;
+        x = wrapi(x0 + lane - H, nx);
+        row = r0 + hy - H;
+        int k;
+        if (py) { row = wrapi(row, nt); k = 2; }
+        else if (row < 0 || row > nt) k = 0;
+        else if (row == 0 || row == nt) k = 3;
+        else k = (row < ns) ? 1 : 2;
+        return k;
+    };
+    auto fetch = [&](int tile) {
+        #pragma unroll
+        for (int c = 0; c < CPT; c++) {
+            int row, x;
+            const int k = classify(tile, c, row, x);
+            pT[c] = 0.0f; pr[c] = 0.0f; pux[c] = 0.0f; puy[c] = 0.0f;
+            if (k == 1 || k == 2) pT[c] = Tin[(size_t)row * nx + x];
+            if (k == 2) {
+                const size_t kf = (size_t)(row - ns) * nx + x;
+                pr[c] = rho_i[kf]; pux[c] = ux_i[kf]; puy[c] = uy_i[kf];
+            } else if (k == 3 && row == nt) {
+                pr[c] = rho_i[(size_t)(nf - 1) * nx + x];
+            }
+        }
+    };
+    if (blockIdx.x < ntiles) fetch(blockIdx.x);
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int x0 = (tile % tiles_x) * TXO, r0 = (tile / tiles_x) * TYO;
+    const int x = wrapi(x0 + lane - H, nx);
+
+    // ---- load (from the prefetched registers) ----
+    #pragma unroll
+    for (int c = 0; c < CPT; c++) {
+        const int hy = wy + c * NWARP;
+        int row, xx;
+        const int k = classify(tile, c, row, xx);
+        float T = 0.0f, lam = 0.0f, ux = 0.0f, uy = 0.0f, rc = 1.0f, r = 0.0f;
+        if (k == 1) {
+            T = pT[c];
+            lam = p.lambda_s;
+            rc = p.rho_c_s;
+        } else if (k == 2) {
+            T = pT[c];
+            r = pr[c];
+            ux = pux[c];
+            uy = puy[c];
+            lam = p.cv_chi * r;
+            rc = r * p.c_v;
+        } else if (k == 3) {
+            if (row == 0) {
+                T = bottom_theta(p, x, n);
+                lam = p.lambda_s;
+            } else {
+                lam = p.cv_chi * pr[c];
+            }
+        }
+        kd[c] = k;
+        Tn[c] = T;
+        rcv[c] = rc;
+        rho[c] = r;
+        sT[0][hy][lane] = T;
+        sT[1][hy][lane] = T;
+        sLam[hy][lane] = lam;
+        sUx[hy][lane] = ux;
+        sUy[hy][lane] = uy;
+    }
+    // issue the next tile's loads now; they complete during this tile's stages
+    if (tile + (int)gridDim.x < ntiles) fetch(tile + gridDim.x);
+    __syncthreads();
+    // ---- per-step coefficients ----
+    const float w1 = 1.0f / 9.0f, w2 = 1.0f / 36.0f;
+    #pragma unroll
+    for (int c = 0; c < CPT; c++) {
+        const int hy = wy + c * NWARP;
+        #pragma unroll
+        for (int a = 0; a < 8; a++) kk[c][a] = 0.0f;
+        ks[c] = 0.0f; ax[c] = 0.0f; ay[c] = 0.0f; c1[c] = 0.0f; c2[c] = 0.0f;
+        acc[c] = 0.0f;
+        const bool inner = hy >= 1 && hy < SH - 1 && lane >= 1 && lane < 31;
+        if (inner && (kd[c] == 1 || kd[c] == 2)) {
+            const float l0 = sLam[hy][lane];
+            const float inv6 = 6.0f * fast_rcp(rcv[c]);
+            const float la[8] = {sLam[hy][lane + 1], sLam[hy + 1][lane], sLam[hy][lane - 1], sLam[hy - 1][lane],
+                                 sLam[hy + 1][lane + 1], sLam[hy + 1][lane - 1], sLam[hy - 1][lane - 1],
+                                 sLam[hy - 1][lane + 1]};
+            #pragma unroll
+            for (int a = 0; a < 8; a++) {
+                const float hm = 2.0f * l0 * la[a] * fast_rcp(l0 + la[a]);
+                kk[c][a] = (a < 4 ? w1 : w2) * hm * inv6;
+                ks[c] += kk[c][a];
+            }
+            if (kd[c] == 2) {
+                ax[c] = -3.0f * sUx[hy][lane];
+                ay[c] = -3.0f * sUy[hy][lane];
+                const float dx = w1 * (sUx[hy][lane + 1] - sUx[hy][lane - 1]) +
+                                 w2 * ((sUx[hy + 1][lane + 1] - sUx[hy - 1][lane - 1]) +
+                                       (sUx[hy - 1][lane + 1] - sUx[hy + 1][lane - 1]));
+                const float dy = w1 * (sUy[hy + 1][lane] - sUy[hy - 1][lane]) +
+                                 w2 * ((sUy[hy + 1][lane + 1] - sUy[hy - 1][lane - 1]) -
+                                       (sUy[hy - 1][lane + 1] - sUy[hy + 1][lane - 1]));
+                const float divu = 3.0f * (dx + dy);
+                const float br = p.b * rho[c];
+                const float iden = fast_rcp(1.0f + br * (2.0f - br));
+                const float pa = p.a_kappa * rho[c] * rho[c] * iden;
+                const float A = rho[c] * p.R * fast_rcp(1.0f - br) - pa * p.kappa_over_Tc;
+                const float B = pa * p.B_coef;
+                const float g0 = -divu * fast_rcp(rcv[c]);
+                c1[c] = g0 * A;
+                c2[c] = g0 * B;
+            }
+        }
+    }
+    // ---- four RK stages ----
+    if (!iso) {
+        #pragma unroll
+        for (int st = 0; st < 4; st++) {
+            const int m = st + 1;
+            const int rb = st & 1, wb = rb ^ 1;
+            #pragma unroll
+            for (int c = 0; c < CPT; c++) {
+                const int hy = wy + c * NWARP;
+                const float T0 = sT[rb][hy][lane];
+                const float Tu = (hy + 1 < SH) ? sT[rb][hy + 1][lane] : 0.0f;
+                const float Td = (hy >= 1) ? sT[rb][hy - 1][lane] : 0.0f;
+                const float T1 = __shfl_down_sync(0xffffffffu, T0, 1);
+                const float T3 = __shfl_up_sync(0xffffffffu, T0, 1);
+                const float T5 = __shfl_down_sync(0xffffffffu, Tu, 1);
+                const float T6 = __shfl_up_sync(0xffffffffu, Tu, 1);
+                const float T8 = __shfl_down_sync(0xffffffffu, Td, 1);
+                const float T7 = __shfl_up_sync(0xffffffffu, Td, 1);
+                const bool act = hy >= m && hy < SH - m && lane >= m && lane < 32 - m && (kd[c] == 1 || kd[c] == 2);
+                if (act) {
+                    float h = kk[c][0] * T1 + kk[c][1] * Tu + kk[c][2] * T3 + kk[c][3] * Td + kk[c][4] * T5 +
+                              kk[c][5] * T6 + kk[c][6] * T7 + kk[c][7] * T8 - ks[c] * T0;
+                    if (kd[c] == 2) {
+                        const float a = T5 - T7, b = T8 - T6;
+                        const float gx = w1 * (T1 - T3) + w2 * (a + b);
+                        const float gy = w1 * (Tu - Td) + w2 * (a - b);
+                        const float Ta = fmaxf(T0 + p.T_sat, 1e-30f);
+                        h += ax[c] * gx + ay[c] * gy + c1[c] * Ta + c2[c] * fast_sqrt(Ta);
+                    }
+                    if (st == 0) { acc[c] = h; sT[wb][hy][lane] = Tn[c] + 0.5f * h; }
+                    else if (st == 1) { acc[c] += 2.0f * h; sT[wb][hy][lane] = Tn[c] + 0.5f * h; }
+                    else if (st == 2) { acc[c] += 2.0f * h; sT[wb][hy][lane] = Tn[c] + h; }
+                    else { acc[c] += h; }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    // ---- write the tile ----
+    #pragma unroll
+    for (int c = 0; c < CPT; c++) {
+        const int hy = wy + c * NWARP;
+        const int row = r0 + hy - H, xo = x0 + lane - H;
+        if (lane >= H && lane < 32 - H && hy >= H && hy < SH - H && row < nt && xo < nx) {
+            float v = Tn[c];
+            if ((kd[c] == 1 || kd[c] == 2) && !iso) v = Tn[c] + acc[c] * (1.0f / 6.0f);
+            if (!(fabsf(v) < 1e30f)) errbits |= ERRW_NONFINITE_T;
+            Tout[(size_t)row * nx + xo] = v;
+        }
+    }
+    __syncthreads();  // shared tiles are rewritten by the next iteration
+    }
+    if (errbits) atomicOr(err, errbits);
+}
+
+template <class P, int NWARP, int CPT>
+struct HeatPersShape {
+    static int grid_blocks;
+    static cudaError_t prepare() {
+        int dev = 0, sms = 0, per = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_heat_pers<P, NWARP, CPT>, NWARP * 32, 0);
+        if (e != cudaSuccess) return e;
+        grid_blocks = sms * (per > 0 ? per : 1);
+        return cudaSuccess;
+    }
+    static cudaError_t launch(const DevParams &p, const StepBuffers &b, cudaStream_t s) {
+        constexpr int TXO = 24, TYO = NWARP * CPT - 8;
+        const int tx = (p.nx + TXO - 1) / TXO, ty = (p.nt + TYO - 1) / TYO;
+        const int ntiles = tx * ty;
+        const int g = ntiles < grid_blocks ? ntiles : grid_blocks;
+        k_heat_pers<P, NWARP, CPT><<<g, NWARP * 32, 0, s>>>(
+            make_fparams(p), tx, ntiles, (const typename P::tst *)b.T_in, (typename P::tst *)b.T_out,
+            (const float *)b.rho, (const float *)b.ux, (const float *)b.uy, b.step, b.err);
+        return cudaGetLastError();
+    }
+};
+template <class P, int NWARP, int CPT>
+int HeatPersShape<P, NWARP, CPT>::grid_blocks = 152;
+
+template <class P, int NWARP, int CPT>
+struct HeatRegShape {
+    static cudaError_t prepare() { return cudaSuccess; }
+    static cudaError_t launch(const DevParams &p, const StepBuffers &b, cudaStream_t s) {
+        constexpr int TXO = 24, TYO = NWARP * CPT - 8;
+        dim3 g((p.nx + TXO - 1) / TXO, (p.nt + TYO - 1) / TYO);
+        k_heat_reg<P, NWARP, CPT><<<g, NWARP * 32, 0, s>>>(
+            make_fparams(p), (const typename P::tst *)b.T_in, (typename P::tst *)b.T_out, (const float *)b.rho,
+            (const float *)b.ux, (const float *)b.uy, b.step, b.err);
+        return cudaGetLastError();
+    }
+};
 
 }  // namespace lbmgb

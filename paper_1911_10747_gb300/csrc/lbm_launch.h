@@ -64,6 +64,7 @@ struct FlowVariant {
     const char *name;
     cudaError_t (*launch)(const DevParams &, const StepBuffers &, cudaStream_t);
     int (*blocks)(const DevParams &);   // blocks of one launch (= per-block partials)
+    cudaError_t (*prepare)();           // per-device set-up (persistent grid size)
 };
 struct HeatVariant {
     const char *name;

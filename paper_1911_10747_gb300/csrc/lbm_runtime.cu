@@ -247,6 +247,8 @@ int lbm_create(const lbm_domain_t *domain, const lbm_heater_t *heater, const lbm
     }
     for (int v = 0; v < h->ks->n_heat; v++)
         if ((e = h->ks->heat[v].prepare()) != cudaSuccess) { cuda_fail(h, e, "kernel attributes"); return bad(LBM_E_CUDA); }
+    for (int v = 0; v < h->ks->n_flow; v++)
+        if ((e = h->ks->flow[v].prepare()) != cudaSuccess) { cuda_fail(h, e, "kernel attributes"); return bad(LBM_E_CUDA); }
     const DevParams &p = h->p;
     const size_t nfl = (size_t)p.nx * p.nf, ntl = (size_t)p.nx * p.nt;
     int max_blocks = 0;
