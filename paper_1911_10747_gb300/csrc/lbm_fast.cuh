@@ -1291,3 +1291,292 @@ struct HeatRegShape {
 };
 
 }  // namespace lbmgb
+
+namespace lbmgb {
+
+// ============================================================================
+// Heat kernel, FP32, wide persistent variant.  A block covers BW columns x
+// SH = BY * CPT rows of cells (4-cell halo, so (BW - 8) x (SH - 8) outputs);
+// thread (tx, ty) owns column tx, rows ty + c BY.  Per-step coefficients,
+// T^n, the current stage temperature and the RK accumulator stay in
+// registers; neighbours' stage temperatures are read from shared memory.
+// A warp covers 32 columns of one row, so rows outside a stage's region are
+// skipped by whole warps.  The next tile's raw inputs are fetched into
+// registers while the current tile is computed.  Same arithmetic as
+// k_heat_fast / k_heat_reg.
+// ============================================================================
+template <class P, int BW, int BY, int CPT, int MINB>
+__global__ void __launch_bounds__(BW * BY, MINB)
+k_heat_wide(const FParams p, int tiles_x, int ntiles, const typename P::tst *__restrict__ Tin,
+            typename P::tst *__restrict__ Tout, const float *__restrict__ rho_i, const float *__restrict__ ux_i,
+            const float *__restrict__ uy_i, const long long *__restrict__ stepp, unsigned *__restrict__ err) {
+    constexpr int H = 4, SH = BY * CPT, TXO = BW - 2 * H, TYO = SH - 2 * H;
+    static_assert(BW % 32 == 0, "a warp must cover whole columns of one row");
+    __shared__ float sT[2][SH][BW];
+    __shared__ float sLam[SH][BW], sUx[SH][BW], sUy[SH][BW];
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int nx = p.nx, nt = p.nt, ns = p.ns, nf = p.nf;
+    const bool py = (p.flags & FLAG_PERIODIC_Y) != 0;
+    const bool iso = (p.flags & FLAG_ISOTHERMAL) != 0;
+    const long long n = *stepp;
+    unsigned errbits = 0;
+
+    float Tn[CPT], Tc[CPT], acc[CPT], kk[CPT][8], ks[CPT], ax[CPT], ay[CPT], c1[CPT], c2[CPT];
+    int kd[CPT];
+    float pT[CPT], pr[CPT], pux[CPT], puy[CPT];
+
+    auto classify = [&](int tile, int c, int &row, int &x) {
+        const int x0 = (tile % tiles_x) * TXO, r0 = (tile / tiles_x) * TYO;
+        x = wrapi(x0 + tx - H, nx);
+        row = r0 + ty + c * BY - H;
+        int k;
+        if (py) { row = wrapi(row, nt); k = 2; }
+        else if (row < 0 || row > nt) k = 0;
+        else if (row == 0 || row == nt) k = 3;
+        else k = (row < ns) ? 1 : 2;
+        return k;
+    };
+    auto fetch = [&](int tile) {
+        #pragma unroll
+        for (int c = 0; c < CPT; c++) {
+            int row, x;
+            const int k = classify(tile, c, row, x);
+            pT[c] = 0.0f; pr[c] = 0.0f; pux[c] = 0.0f; puy[c] = 0.0f;
+            if (k == 1 || k == 2) pT[c] = Tin[(size_t)row * nx + x];
+            if (k == 2) {
+                const size_t kf = (size_t)(row - ns) * nx + x;
+                pr[c] = rho_i[kf]; pux[c] = ux_i[kf]; puy[c] = uy_i[kf];
+            } else if (k == 3 && row == nt) {
+                pr[c] = rho_i[(size_t)(nf - 1) * nx + x];
+            }
+        }
+    };
+    const float w1 = 1.0f / 9.0f, w2 = 1.0f / 36.0f;
+    if ((int)blockIdx.x < ntiles) fetch(blockIdx.x);
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int x0 = (tile % tiles_x) * TXO, r0 = (tile / tiles_x) * TYO;
+        float rcv[CPT], rho[CPT];
+        // ---- load from the prefetched registers ----
+        #pragma unroll
+        for (int c = 0; c < CPT; c++) {
+            const int hy = ty + c * BY;
+            int row, x;
+            const int k = classify(tile, c, row, x);
+            float T = 0.0f, lam = 0.0f, ux = 0.0f, uy = 0.0f, rc = 1.0f, r = 0.0f;
+            if (k == 1) {
+                T = pT[c]; lam = p.lambda_s; rc = p.rho_c_s;
+            } else if (k == 2) {
+                T = pT[c]; r = pr[c]; ux = pux[c]; uy = puy[c];
+                lam = p.cv_chi * r; rc = r * p.c_v;
+            } else if (k == 3) {
+                if (row == 0) { T = bottom_theta(p, x, n); lam = p.lambda_s; }
+                else lam = p.cv_chi * pr[c];
+            }
+            kd[c] = k; Tn[c] = T; Tc[c] = T; rcv[c] = rc; rho[c] = r;
+            sT[0][hy][tx] = T;
+            sLam[hy][tx] = lam; sUx[hy][tx] = ux; sUy[hy][tx] = uy;
+        }
+        if (tile + (int)gridDim.x < ntiles) fetch(tile + gridDim.x);
+        __syncthreads();
+        // ---- per-step coefficients ----
+        #pragma unroll
+        for (int c = 0; c < CPT; c++) {
+            const int hy = ty + c * BY;
+            #pragma unroll
+            for (int a = 0; a < 8; a++) kk[c][a] = 0.0f;
+            ks[c] = 0.0f; ax[c] = 0.0f; ay[c] = 0.0f; c1[c] = 0.0f; c2[c] = 0.0f; acc[c] = 0.0f;
+            const bool inner = hy >= 1 && hy < SH - 1 && tx >= 1 && tx < BW - 1;
+            if (inner && (kd[c] == 1 || kd[c] == 2)) {
+                const float l0 = sLam[hy][tx];
+                const float inv6 = 6.0f * fast_rcp(rcv[c]);
+                const float la[8] = {sLam[hy][tx + 1], sLam[hy + 1][tx], sLam[hy][tx - 1], sLam[hy - 1][tx],
+                                     sLam[hy + 1][tx + 1], sLam[hy + 1][tx - 1], sLam[hy - 1][tx - 1], sLam[hy - 1][tx + 1]};
+                #pragma unroll
+                for (int a = 0; a < 8; a++) {
+                    const float hm = 2.0f * l0 * la[a] * fast_rcp(l0 + la[a]);
+                    kk[c][a] = (a < 4 ? w1 : w2) * hm * inv6;
+                    ks[c] += kk[c][a];
+                }
+                if (kd[c] == 2) {
+                    ax[c] = -3.0f * sUx[hy][tx];
+                    ay[c] = -3.0f * sUy[hy][tx];
+                    const float dx = w1 * (sUx[hy][tx + 1] - sUx[hy][tx - 1]) +
+                                     w2 * ((sUx[hy + 1][tx + 1] - sUx[hy - 1][tx - 1]) + (sUx[hy - 1][tx + 1] - sUx[hy + 1][tx - 1]));
+                    const float dy = w1 * (sUy[hy + 1][tx] - sUy[hy - 1][tx]) +
+                                     w2 * ((sUy[hy + 1][tx + 1] - sUy[hy - 1][tx - 1]) - (sUy[hy - 1][tx + 1] - sUy[hy + 1][tx - 1]));
+                    const float divu = 3.0f * (dx + dy);
+                    const float br = p.b * rho[c];
+                    const float iden = fast_rcp(1.0f + br * (2.0f - br));
+                    const float pa = p.a_kappa * rho[c] * rho[c] * iden;
+                    const float A = rho[c] * p.R * fast_rcp(1.0f - br) - pa * p.kappa_over_Tc;
+                    const float B = pa * p.B_coef;
+                    const float g0 = -divu * fast_rcp(rcv[c]);
+                    c1[c] = g0 * A;
+                    c2[c] = g0 * B;
+                }
+            }
+        }
+        // ---- four RK stages; stage s reads sT[s & 1], writes sT[(s + 1) & 1] ----
+        if (!iso) {
+            #pragma unroll
+            for (int st = 0; st < 4; st++) {
+                const int m = st + 1;
+                const int rb = st & 1, wb = rb ^ 1;
+                if (st > 0) __syncthreads();  // the previous stage's writes are visible
+                #pragma unroll
+                for (int c = 0; c < CPT; c++) {
+                    const int hy = ty + c * BY;
+                    if (hy < m || hy >= SH - m) continue;  // whole warp
+                    const bool act = tx >= m && tx < BW - m && (kd[c] == 1 || kd[c] == 2);
+                    if (!act) continue;
+                    const float T0 = Tc[c];
+                    const float T1 = sT[rb][hy][tx + 1], T3 = sT[rb][hy][tx - 1];
+                    const float Tu = sT[rb][hy + 1][tx], Td = sT[rb][hy - 1][tx];
+                    const float T5 = sT[rb][hy + 1][tx + 1], T6 = sT[rb][hy + 1][tx - 1];
+                    const float T7 = sT[rb][hy - 1][tx - 1], T8 = sT[rb][hy - 1][tx + 1];
+                    float h = kk[c][0] * T1 + kk[c][1] * Tu + kk[c][2] * T3 + kk[c][3] * Td + kk[c][4] * T5 +
+                              kk[c][5] * T6 + kk[c][6] * T7 + kk[c][7] * T8 - ks[c] * T0;
+                    if (kd[c] == 2) {
+                        const float a = T5 - T7, b = T8 - T6;
+                        const float gx = w1 * (T1 - T3) + w2 * (a + b);
+                        const float gy = w1 * (Tu - Td) + w2 * (a - b);
+                        const float Ta = fmaxf(T0 + p.T_sat, 1e-30f);
+                        h += ax[c] * gx + ay[c] * gy + c1[c] * Ta + c2[c] * fast_sqrt(Ta);
+                    }
+                    float Tnext;
+                    if (st == 0) { acc[c] = h; Tnext = Tn[c] + 0.5f * h; }
+                    else if (st == 1) { acc[c] += 2.0f * h; Tnext = Tn[c] + 0.5f * h; }
+                    else if (st == 2) { acc[c] += 2.0f * h; Tnext = Tn[c] + h; }
+                    else { acc[c] += h; Tnext = Tn[c]; }
+                    if (st < 3) { Tc[c] = Tnext; sT[wb][hy][tx] = Tnext; }
+                }
+                // cells outside this stage's region keep their value in the
+                // other buffer too (fixed cells, or values no longer read)
+                if (st == 0) {
+                    #pragma unroll
+                    for (int c = 0; c < CPT; c++) {
+                        const int hy = ty + c * BY;
+                        const bool act = hy >= 1 && hy < SH - 1 && tx >= 1 && tx < BW - 1 && (kd[c] == 1 || kd[c] == 2);
+                        if (!act) sT[1][hy][tx] = Tn[c];
+                    }
+                }
+            }
+        }
+        // ---- write the tile ----
+        #pragma unroll
+        for (int c = 0; c < CPT; c++) {
+            const int hy = ty + c * BY;
+            const int row = r0 + hy - H, xo = x0 + tx - H;
+            if (tx >= H && tx < BW - H && hy >= H && hy < SH - H && row < nt && xo < nx) {
+                float v = Tn[c];
+                if ((kd[c] == 1 || kd[c] == 2) && !iso) v = Tn[c] + acc[c] * (1.0f / 6.0f);
+                if (!(fabsf(v) < 1e30f)) errbits |= ERRW_NONFINITE_T;
+                Tout[(size_t)row * nx + xo] = v;
+            }
+        }
+        __syncthreads();  // shared tiles are rewritten by the next tile
+    }
+    if (errbits) atomicOr(err, errbits);
+}
+
+template <class P, int BW, int BY, int CPT, int MINB>
+struct HeatWideShape {
+    static int grid_blocks;
+    static cudaError_t prepare() {
+        int dev = 0, sms = 0, per = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_heat_wide<P, BW, BY, CPT, MINB>, BW * BY, 0);
+        if (e != cudaSuccess) return e;
+        grid_blocks = sms * (per > 0 ? per : 1);
+        return cudaSuccess;
+    }
+    static cudaError_t launch(const DevParams &p, const StepBuffers &b, cudaStream_t s) {
+        constexpr int TXO = BW - 8, TYO = BY * CPT - 8;
+        const int tx = (p.nx + TXO - 1) / TXO, ty = (p.nt + TYO - 1) / TYO;
+        const int ntiles = tx * ty;
+        const int g = ntiles < grid_blocks ? ntiles : grid_blocks;
+        k_heat_wide<P, BW, BY, CPT, MINB><<<g, dim3(BW, BY), 0, s>>>(
+            make_fparams(p), tx, ntiles, (const typename P::tst *)b.T_in, (typename P::tst *)b.T_out,
+            (const float *)b.rho, (const float *)b.ux, (const float *)b.uy, b.step, b.err);
+        return cudaGetLastError();
+    }
+};
+template <class P, int BW, int BY, int CPT, int MINB>
+int HeatWideShape<P, BW, BY, CPT, MINB>::grid_blocks = 152;
+
+}  // namespace lbmgb
+
+namespace lbmgb {
+
+// Diagnostics kernel, FP32 path, single pass: every global load is issued
+// before the first reduction, then one block-wide reduction of four sums.
+template <class P, int NT>
+__global__ void __launch_bounds__(NT)
+k_diag_flat(const FParams p, const float *__restrict__ T, const float *__restrict__ rho,
+            const double *__restrict__ part, int nblk, double *__restrict__ q_top, double *__restrict__ series,
+            int cap, double *__restrict__ last, long long *__restrict__ stepp, double inv_nx, double inv_nfl) {
+    __shared__ double sh[4][NT / 32];
+    const int nx = p.nx, ns = p.ns, t = threadIdx.x;
+    const bool flux = !(p.flags & FLAG_PERIODIC_Y) && ns >= 3;
+    double v[4] = {0.0, 0.0, 0.0, 0.0};  // mass, vapour count, bottom flux, surface flux
+    for (int b = t; b < nblk; b += NT) {
+        v[0] += part[2 * b];
+        v[1] += part[2 * b + 1];
+    }
+    if (flux) {
+        const float lams = p.lambda_s, cvchi = p.cv_chi;
+        for (int x = t; x < nx; x += NT) {
+            const float t0 = T[x], t1 = T[nx + x], t2 = T[2 * nx + x];
+            const float tu = T[(size_t)ns * nx + x], td = T[(size_t)(ns - 1) * nx + x];
+            const float lf1 = cvchi * rho[x];
+            // Eq. 36 (theta differences: T_sat cancels) and the face flux
+            const float qb = -lams * (0.5f * ((4.0f * t1 - t2) - 3.0f * t0));
+            const float lf = 2.0f * lams * lf1 * fast_rcp(lams + lf1);
+            const float q = -lf * (tu - td);
+            q_top[x] = (double)q;
+            v[2] += (double)qb;
+            v[3] += (double)q;
+        }
+    }
+    #pragma unroll
+    for (int k = 0; k < 4; k++) {
+        #pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+    }
+    if ((t & 31) == 0) {
+        #pragma unroll
+        for (int k = 0; k < 4; k++) sh[k][t >> 5] = v[k];
+    }
+    __syncthreads();
+    if (t < 32) {
+        #pragma unroll
+        for (int k = 0; k < 4; k++) {
+            double s = (t < NT / 32) ? sh[k][t] : 0.0;
+            #pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+            v[k] = s;
+        }
+        if (t == 0) {
+            const long long n = *stepp;
+            const double out[SERIES_WIDTH] = {v[2] * inv_nx, v[3] * inv_nx, v[1] * inv_nfl, v[0]};
+            const long long slot = n % cap;
+            #pragma unroll
+            for (int k = 0; k < SERIES_WIDTH; k++) {
+                series[slot * SERIES_WIDTH + k] = out[k];
+                last[k] = out[k];
+            }
+            *stepp = n + 1;
+        }
+    }
+}
+
+template <class P, int NT>
+cudaError_t launch_diag_flat(const DevParams &p, const StepBuffers &b, int nblk, cudaStream_t s) {
+    k_diag_flat<P, NT><<<1, NT, 0, s>>>(make_fparams(p), (const float *)b.T_out, (const float *)b.rho, b.part, nblk,
+                                        b.q_top, b.series, b.series_cap, b.last, b.step, 1.0 / (double)p.nx,
+                                        1.0 / ((double)p.nx * (double)p.nf));
+    return cudaGetLastError();
+}
+
+}  // namespace lbmgb

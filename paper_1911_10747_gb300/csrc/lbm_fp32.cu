@@ -7,7 +7,7 @@ namespace lbmgb {
 namespace {
 template <class P>
 cudaError_t diag(const DevParams &p, const StepBuffers &b, int nblk, cudaStream_t s) {
-    return launch_diag_fast<P, 512>(p, b, nblk, s);
+    return launch_diag_flat<P, 1024>(p, b, nblk, s);
 }
 #define FLOWV(P, BX, BY, RY, MB)                                                                  \
     {"flow_" #BX "x" #BY "x" #RY "_b" #MB, FlowFastShape<P, BX, BY, RY, MB>::launch,                \
@@ -15,6 +15,8 @@ cudaError_t diag(const DevParams &p, const StepBuffers &b, int nblk, cudaStream_
 #define FLOWP(P, BX, BY, RY, MB)                                                                  \
     {"flowpers_" #BX "x" #BY "x" #RY "_b" #MB, FlowPersShape<P, BX, BY, RY, MB>::launch,            \
      FlowPersShape<P, BX, BY, RY, MB>::blocks, FlowPersShape<P, BX, BY, RY, MB>::prepare}
+#define HEATW(P, BW, BY, CPT, MB) \
+    {"heatwide_" #BW "x" #BY "x" #CPT, HeatWideShape<P, BW, BY, CPT, MB>::launch, HeatWideShape<P, BW, BY, CPT, MB>::prepare}
 #define HEATP(P, NW, CPT) \
     {"heatpers_24x" #NW "x" #CPT, HeatPersShape<P, NW, CPT>::launch, HeatPersShape<P, NW, CPT>::prepare}
 #define HEATR(P, NW, CPT) \
@@ -28,13 +30,14 @@ const FlowVariant flows32[] = {
     FLOWV(PolicyF32, 64, 4, 2, 3), FLOWV(PolicyF32, 32, 8, 1, 4), FLOWV(PolicyF32, 64, 8, 2, 2),
 };
 const HeatVariant heats32[] = {
+    HEATW(PolicyF32, 64, 16, 2, 1), HEATW(PolicyF32, 64, 8, 4, 1), HEATW(PolicyF32, 32, 16, 2, 2),
     HEATP(PolicyF32, 16, 2), HEATP(PolicyF32, 8, 4),
     HEATR(PolicyF32, 16, 2), HEATR(PolicyF32, 8, 4), HEATR(PolicyF32, 32, 2),
     HEATV(PolicyF32, 32, 16, 32, 8), HEATV(PolicyF32, 32, 32, 32, 16), HEATV(PolicyF32, 64, 16, 64, 4),
     HEATV(PolicyF32, 64, 32, 32, 16),
 };
 const FlowVariant flows16[] = {FLOWP(PolicyF16, 32, 8, 2, 2), FLOWV(PolicyF16, 32, 8, 2, 3)};
-const HeatVariant heats16[] = {HEATP(PolicyF16, 16, 2), HEATR(PolicyF16, 16, 2), HEATR(PolicyF16, 8, 4), HEATV(PolicyF16, 32, 32, 32, 16)};
+const HeatVariant heats16[] = {HEATW(PolicyF16, 64, 16, 2, 1), HEATP(PolicyF16, 16, 2), HEATR(PolicyF16, 16, 2), HEATR(PolicyF16, 8, 4), HEATV(PolicyF16, 32, 32, 32, 16)};
 
 const KernelSet ks32 = {"fp32", sizeof(float), sizeof(float), sizeof(float),
                         (int)(sizeof(flows32) / sizeof(flows32[0])), flows32,
