@@ -357,8 +357,33 @@ k_flow_pers(const FParams p, int tiles_x, int ntiles, const typename P::fst *__r
     // populations and temperature of the next tile, loaded during this tile
     float pg[RY][9];
     float pTv[RY];
+    // one halo-ring site per thread (threads 0 .. ring-1): its density and T
+    constexpr int RING = 2 * SW + 2 * TY;
+    static_assert(RING <= NT, "one ring site per thread");
+    float rg[9], rT = 0.0f;
+    bool rvalid = false;
+    auto ring_site = [&](int k, int x0, int y0, int &hx, int &hy, int &x, int &y) {
+        if (k < SW) { hx = k; hy = 0; }
+        else if (k < 2 * SW) { hx = k - SW; hy = SH - 1; }
+        else if (k < 2 * SW + TY) { hx = 0; hy = 1 + (k - 2 * SW); }
+        else { hx = SW - 1; hy = 1 + (k - 2 * SW - TY); }
+        x = wrapi(x0 + hx - 1, nx);
+        y = y0 + hy - 1;
+        if (py) y = wrapi(y, nf);
+        return py || (y >= 0 && y < nf);
+    };
     auto fetch = [&](int tile) {
         const int x0 = (tile % tiles_x) * TX, y0 = (tile / tiles_x) * TY;
+        if (tid < RING && !frozen) {
+            int hx, hy, x, y;
+            rvalid = ring_site(tid, x0, y0, hx, hy, x, y);
+            if (rvalid) {
+                const size_t kk = (size_t)y * nx + x;
+                #pragma unroll
+                for (int i = 0; i < 9; i++) rg[i] = ld_as<float>(fin + i * plane + kk);
+                rT = ld_as<float>(Tin + (size_t)(p.ns + y) * nx + x);
+            }
+        }
         #pragma unroll
         for (int r = 0; r < RY; r++) {
             const int lx = threadIdx.x, ly = threadIdx.y + r * BY;
@@ -388,7 +413,6 @@ k_flow_pers(const FParams p, int tiles_x, int ntiles, const typename P::fst *__r
         for (int i = 0; i < 9; i++) g[r][i] = pg[r][i];
         gT[r] = pTv[r];
     }
-    if (tile + (int)gridDim.x < ntiles) fetch(tile + gridDim.x);
 
     // ---- own sites: density, psi ----
     #pragma unroll
@@ -405,30 +429,19 @@ k_flow_pers(const FParams p, int tiles_x, int ntiles, const typename P::fst *__r
         }
         s_psi[(ly + 1) * SW + lx + 1] = psi;
     }
-    // ---- halo ring ----
-    if (!frozen) {
-        for (int k = tid; k < 2 * SW + 2 * TY; k += NT) {
-            int hx, hy;
-            if (k < SW) { hx = k; hy = 0; }
-            else if (k < 2 * SW) { hx = k - SW; hy = SH - 1; }
-            else if (k < 2 * SW + TY) { hx = 0; hy = 1 + (k - 2 * SW); }
-            else { hx = SW - 1; hy = 1 + (k - 2 * SW - TY); }
-            const int x = wrapi(x0 + hx - 1, nx);
-            int y = y0 + hy - 1;
-            if (py) y = wrapi(y, nf);
-            float psi = 0.0f;
-            if (y >= 0 && y < nf) {
-                const size_t kk = (size_t)y * nx + x;
-                float v[9];
-                #pragma unroll
-                for (int i = 0; i < 9; i++) v[i] = ld_as<float>(fin + i * plane + kk);
-                const float d = ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7])) + v[8];
-                const float T = ld_as<float>(Tin + (size_t)(p.ns + y) * nx + x) + tsat;
-                psi = psi_fast(p, d + rho0, T, errbits);
-            }
-            s_psi[hy * SW + hx] = psi;
+    // ---- halo ring, from the prefetched registers ----
+    if (!frozen && tid < RING) {
+        int hx, hy, x, y;
+        ring_site(tid, x0, y0, hx, hy, x, y);
+        float psi = 0.0f;
+        if (rvalid) {
+            const float d = ((rg[0] + rg[1]) + (rg[2] + rg[3])) + ((rg[4] + rg[5]) + (rg[6] + rg[7])) + rg[8];
+            psi = psi_fast(p, d + rho0, rT + tsat, errbits);
         }
+        s_psi[hy * SW + hx] = psi;
     }
+    // the next tile's loads (own sites and ring) fly during this tile's collisions
+    if (tile + (int)gridDim.x < ntiles) fetch(tile + gridDim.x);
     __syncthreads();
 
     // ---- collide and push ----
