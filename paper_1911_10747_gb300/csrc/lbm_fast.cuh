@@ -354,6 +354,7 @@ k_flow_pers(const FParams p, int tiles_x, int ntiles, const typename P::fst *__r
     float g[RY][9];
     float dd[RY];
     float gT[RY];
+    const bool wide = nx >= TX + 1;  // then tile columns +-1 wrap with one compare
     // populations and temperature of the next tile, loaded during this tile
     float pg[RY][9];
     float pTv[RY];
@@ -367,7 +368,7 @@ k_flow_pers(const FParams p, int tiles_x, int ntiles, const typename P::fst *__r
         else if (k < 2 * SW) { hx = k - SW; hy = SH - 1; }
         else if (k < 2 * SW + TY) { hx = 0; hy = 1 + (k - 2 * SW); }
         else { hx = SW - 1; hy = 1 + (k - 2 * SW - TY); }
-        x = wrapi(x0 + hx - 1, nx);
+        x = wide ? wrap1(x0 + hx - 1, nx) : wrapi(x0 + hx - 1, nx);
         y = y0 + hy - 1;
         if (py) y = wrapi(y, nf);
         return py || (y >= 0 && y < nf);
@@ -387,7 +388,7 @@ k_flow_pers(const FParams p, int tiles_x, int ntiles, const typename P::fst *__r
         #pragma unroll
         for (int r = 0; r < RY; r++) {
             const int lx = threadIdx.x, ly = threadIdx.y + r * BY;
-            const int x = (x0 + lx < nx) ? x0 + lx : wrapi(x0 + lx, nx);
+            const int x = wide ? wrap1(x0 + lx, nx) : wrapi(x0 + lx, nx);
             int y = y0 + ly;
             const bool has = py || y < nf;
             if (py) y = wrapi(y, nf);
@@ -1337,10 +1338,12 @@ k_heat_wide(const FParams p, int tiles_x, int ntiles, const typename P::tst *__r
     float Tn[CPT], Tc[CPT], acc[CPT], kk[CPT][8], ks[CPT], ax[CPT], ay[CPT], c1[CPT], c2[CPT];
     int kd[CPT];
     float pT[CPT], pr[CPT], pux[CPT], puy[CPT];
+    int pkd[CPT], prow[CPT], px[CPT];  // kind, row and column of the prefetched cells
 
+    const bool wide = nx >= BW;  // then x0 + tx - H lies in [-H, 2 nx): one compare wraps it
     auto classify = [&](int tile, int c, int &row, int &x) {
         const int x0 = (tile % tiles_x) * TXO, r0 = (tile / tiles_x) * TYO;
-        x = wrapi(x0 + tx - H, nx);
+        x = wide ? wrap1(x0 + tx - H, nx) : wrapi(x0 + tx - H, nx);
         row = r0 + ty + c * BY - H;
         int k;
         if (py) { row = wrapi(row, nt); k = 2; }
@@ -1354,6 +1357,7 @@ k_heat_wide(const FParams p, int tiles_x, int ntiles, const typename P::tst *__r
         for (int c = 0; c < CPT; c++) {
             int row, x;
             const int k = classify(tile, c, row, x);
+            pkd[c] = k; prow[c] = row; px[c] = x;
             pT[c] = 0.0f; pr[c] = 0.0f; pux[c] = 0.0f; puy[c] = 0.0f;
             if (k == 1 || k == 2) pT[c] = Tin[(size_t)row * nx + x];
             if (k == 2) {
@@ -1373,8 +1377,7 @@ k_heat_wide(const FParams p, int tiles_x, int ntiles, const typename P::tst *__r
         #pragma unroll
         for (int c = 0; c < CPT; c++) {
             const int hy = ty + c * BY;
-            int row, x;
-            const int k = classify(tile, c, row, x);
+            const int row = prow[c], x = px[c], k = pkd[c];
             float T = 0.0f, lam = 0.0f, ux = 0.0f, uy = 0.0f, rc = 1.0f, r = 0.0f;
             if (k == 1) {
                 T = pT[c]; lam = p.lambda_s; rc = p.rho_c_s;
@@ -1387,7 +1390,9 @@ k_heat_wide(const FParams p, int tiles_x, int ntiles, const typename P::tst *__r
             }
             kd[c] = k; Tn[c] = T; Tc[c] = T; rcv[c] = rc; rho[c] = r;
             sT[0][hy][tx] = T;
-            sLam[hy][tx] = lam; sUx[hy][tx] = ux; sUy[hy][tx] = uy;
+            // 1/lambda: the harmonic mean of a link is 2 / (1/l0 + 1/la)
+            sLam[hy][tx] = (lam > 0.0f) ? fast_rcp(lam) : 1e30f;
+            sUx[hy][tx] = ux; sUy[hy][tx] = uy;
         }
         if (tile + (int)gridDim.x < ntiles) fetch(tile + gridDim.x);
         __syncthreads();
@@ -1400,14 +1405,15 @@ k_heat_wide(const FParams p, int tiles_x, int ntiles, const typename P::tst *__r
             ks[c] = 0.0f; ax[c] = 0.0f; ay[c] = 0.0f; c1[c] = 0.0f; c2[c] = 0.0f; acc[c] = 0.0f;
             const bool inner = hy >= 1 && hy < SH - 1 && tx >= 1 && tx < BW - 1;
             if (inner && (kd[c] == 1 || kd[c] == 2)) {
-                const float l0 = sLam[hy][tx];
-                const float inv6 = 6.0f * fast_rcp(rcv[c]);
-                const float la[8] = {sLam[hy][tx + 1], sLam[hy + 1][tx], sLam[hy][tx - 1], sLam[hy - 1][tx],
+                const float r0l = sLam[hy][tx];
+                const float inv12 = 12.0f * fast_rcp(rcv[c]);
+                const float ra[8] = {sLam[hy][tx + 1], sLam[hy + 1][tx], sLam[hy][tx - 1], sLam[hy - 1][tx],
                                      sLam[hy + 1][tx + 1], sLam[hy + 1][tx - 1], sLam[hy - 1][tx - 1], sLam[hy - 1][tx + 1]};
+                const float c_ax = w1 * inv12, c_dg = w2 * inv12;
                 #pragma unroll
                 for (int a = 0; a < 8; a++) {
-                    const float hm = 2.0f * l0 * la[a] * fast_rcp(l0 + la[a]);
-                    kk[c][a] = (a < 4 ? w1 : w2) * hm * inv6;
+                    // 6 w_a lambda_face / (rho c) with lambda_face = 2 / (1/l0 + 1/la)
+                    kk[c][a] = (a < 4 ? c_ax : c_dg) * fast_rcp(r0l + ra[a]);
                     ks[c] += kk[c][a];
                 }
                 if (kd[c] == 2) {
