@@ -180,6 +180,48 @@ def run_reference(args):
     return 0
 
 
+def measure_sweep(lbm, W, torch, dev, steps):
+    """Runs/hour of the 48-run boiling-curve sweep (widths 128-512, 20,000
+    steps per run): batched FP32 through one concurrent graph vs the same
+    runs stepped one after another in FP64.  Both are timed on `steps` steps
+    and scaled to 20,000."""
+    full = 20000
+    cfgs = W.sweep(48)
+    sites = sum(c.fluid_sites for c in cfgs)
+    runs = [lbm.Run(c) for c in cfgs]
+    batch = lbm.Batch(runs)
+    batch.step(4)
+    batch.sync()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    batch.step(steps)
+    batch.sync()
+    dt_b = time.perf_counter() - t0
+    batch.close()
+    for r in runs:
+        r.close()
+    # sequential FP64 (each run alone; a few runs are sampled and scaled)
+    sample = cfgs[::6]
+    t_seq = 0.0
+    for c in sample:
+        r = lbm.Run(c.replace(precision="fp64"))
+        r.step(2)
+        r.sync()
+        t0 = time.perf_counter()
+        r.step(steps)
+        r.sync()
+        t_seq += time.perf_counter() - t0
+        r.close()
+    t_seq *= len(cfgs) / len(sample)
+    hours_b = dt_b * full / steps / 3600.0
+    hours_s = t_seq * full / steps / 3600.0
+    return {"runs": len(cfgs), "fluid_sites": sites, "steps_per_run": full, "timed_steps": steps,
+            "batched_fp32_runs_per_hour": len(cfgs) / hours_b,
+            "sequential_fp64_runs_per_hour": len(cfgs) / hours_s,
+            "batched_fp32_mlups": sites * steps / dt_b / 1e6,
+            "note": "sequential FP64 timed on every 6th run and scaled to 48"}
+
+
 def run_ours(args):
     import torch
 
@@ -300,6 +342,12 @@ def run_ours(args):
     else:
         run.close()
 
+    # ---- boiling-curve sweep: 48 runs batched (FP32, one concurrent graph)
+    # versus the same runs one after another in FP64 ----
+    sweep = None
+    if not args.no_sweep:
+        sweep = measure_sweep(lbm, W, torch, dev, args.sweep_steps)
+
     # ---- CPU baseline: the oracle on a bounded sample (rank 0, N = 1) ----
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
@@ -330,6 +378,7 @@ def run_ours(args):
             "e2e": e2e,
             "cpu_baseline": cpu,
             "fp64": fp64,
+            "sweep": sweep,
         }
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -347,6 +396,8 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-sweep", action="store_true")
+    ap.add_argument("--sweep-steps", type=int, default=200)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

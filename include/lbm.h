@@ -62,6 +62,7 @@ enum lbm_field_mask {
 };
 
 typedef struct lbm_run *lbm_handle;
+typedef struct lbm_batch_s *lbm_batch;
 
 /* Fluid domain and flow model (Sec. 2.1, 3.1). */
 typedef struct {
@@ -206,6 +207,24 @@ int lbm_select_variants(lbm_handle h, int flow, int heat);
  * only buffers that the next step overwrites).  best_ms (nullable, [2])
  * receives the winning average milliseconds per launch.  Synchronises. */
 int lbm_autotune(lbm_handle h, int iters, double *best_ms);
+
+/* Batches of independent runs (the boiling-curve sweep, served requests).
+ * A batch groups n >= 1 existing runs of one device (it does not own them;
+ * destroy the batch before its runs).  lbm_batch_step advances every run by
+ * n steps: pairs of steps are replayed from one captured CUDA graph whose
+ * branches, one per run on that run's own stream, run concurrently on the
+ * device, so small runs share the GPU instead of queueing behind each other.
+ * The graph is re-captured when a run's launch shape changes
+ * (lbm_select_variants, lbm_autotune).  Runs with per-kernel timing enabled
+ * are rejected (LBM_E_STATE).  Work of a run issued through its own handle
+ * before or after a batch step is ordered with it.  lbm_batch_sync waits and
+ * reports the first latched fault; messages via lbm_batch_last_error
+ * (NULL batch: the last failed lbm_batch_create). */
+int lbm_batch_create(const lbm_handle *runs, int32_t n, lbm_batch *out);
+int lbm_batch_step(lbm_batch b, int64_t n);
+int lbm_batch_sync(lbm_batch b);
+int lbm_batch_destroy(lbm_batch b);
+const char *lbm_batch_last_error(lbm_batch b);
 
 /* Diagnostics of one state without allocating device memory.  The paper has
  * no counterpart: this entry point exists for callers that cannot call

@@ -44,6 +44,7 @@ struct lbm_run {
     int series_cap = 4096;
     int nblk = 0;                   // blocks of the selected flow variant
     int fv = 0, hv = 0;             // selected flow / heat variants
+    int version = 0;                // bumped when captured launch parameters change
     cudaGraphExec_t graph = nullptr;
     bool timing = false;
     std::vector<EventPair> ev[3];
@@ -542,6 +543,172 @@ int lbm_kernel_times(lbm_handle h, double *avg_ms, int64_t *launches) {
 
 int lbm_kernels_per_step(lbm_handle h) { return h ? 3 : 0; }
 
+}  // extern "C"
+
+// ---- batches of runs ---------------------------------------------------------
+struct lbm_batch_s {
+    std::vector<lbm_run *> runs;
+    std::vector<int> versions;
+    std::vector<int> parities;      // each run's buffer parity when the graph was captured
+    std::vector<cudaEvent_t> join;
+    cudaEvent_t fork = nullptr;
+    cudaStream_t stream = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    int device = 0;
+    std::string msg;
+};
+
+static int bfail(lbm_batch_s *b, int code, const std::string &m) {
+    if (b) b->msg = m; else g_create_error = m;
+    return code;
+}
+
+static void batch_free(lbm_batch_s *b) {
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    for (auto e : b->join) cudaEventDestroy(e);
+    if (b->fork) cudaEventDestroy(b->fork);
+    if (b->stream) cudaStreamDestroy(b->stream);
+}
+
+// Capture two steps of every run: the batch stream forks to each run's
+// stream, each run queues its own kernels, the branches join back.
+static int batch_build_graph(lbm_batch_s *b) {
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return bfail(b, LBM_E_CUDA, std::string("batch capture: ") + cudaGetErrorString(e));
+    int rc = LBM_OK;
+    if ((e = cudaEventRecord(b->fork, b->stream)) != cudaSuccess) rc = LBM_E_CUDA;
+    for (size_t i = 0; i < b->runs.size() && rc == LBM_OK; i++) {
+        lbm_run *h = b->runs[i];
+        if ((e = cudaStreamWaitEvent(h->stream, b->fork, 0)) != cudaSuccess) { rc = LBM_E_CUDA; break; }
+        if ((rc = launch_step(h, false)) != LBM_OK || (rc = launch_step(h, false)) != LBM_OK) {
+            b->msg = h->msg;
+            break;
+        }
+        if ((e = cudaEventRecord(b->join[i], h->stream)) != cudaSuccess ||
+            (e = cudaStreamWaitEvent(b->stream, b->join[i], 0)) != cudaSuccess) { rc = LBM_E_CUDA; break; }
+    }
+    cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
+    if (rc != LBM_OK || e2 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        if (rc == LBM_E_CUDA) return bfail(b, rc, std::string("batch capture: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
+        return rc != LBM_OK ? rc : bfail(b, LBM_E_CUDA, std::string("batch capture: ") + cudaGetErrorString(e2));
+    }
+    e = cudaGraphInstantiate(&b->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) { b->graph = nullptr; return bfail(b, LBM_E_CUDA, std::string("batch graph: ") + cudaGetErrorString(e)); }
+    for (size_t i = 0; i < b->runs.size(); i++) {
+        b->versions[i] = b->runs[i]->version;
+        b->parities[i] = b->runs[i]->parity;
+    }
+    return LBM_OK;
+}
+
+extern "C" {
+
+int lbm_batch_create(const lbm_handle *runs, int32_t n, lbm_batch *out) {
+    if (!out) return bfail(nullptr, LBM_E_INVAL, "out is NULL");
+    *out = nullptr;
+    if (!runs || n < 1) return bfail(nullptr, LBM_E_INVAL, "a batch needs at least one run");
+    lbm_batch_s *b = new (std::nothrow) lbm_batch_s();
+    if (!b) return bfail(nullptr, LBM_E_NOMEM, "host allocation failed");
+    b->device = runs[0] ? runs[0]->device : 0;
+    for (int i = 0; i < n; i++) {
+        if (!runs[i]) { delete b; return bfail(nullptr, LBM_E_INVAL, "NULL run in batch"); }
+        if (runs[i]->device != b->device) { delete b; return bfail(nullptr, LBM_E_INVAL, "runs of a batch must share a device"); }
+        for (int j = 0; j < i; j++)
+            if (runs[j] == runs[i]) { delete b; return bfail(nullptr, LBM_E_INVAL, "a run appears twice in the batch"); }
+        b->runs.push_back(runs[i]);
+        b->versions.push_back(-1);
+        b->parities.push_back(-1);
+    }
+    cudaError_t e = cudaSetDevice(b->device);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+    for (int i = 0; i < n && e == cudaSuccess; i++) {
+        cudaEvent_t ev = nullptr;
+        e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        b->join.push_back(ev);
+    }
+    if (e != cudaSuccess) {
+        std::string m = std::string("batch set-up: ") + cudaGetErrorString(e);
+        batch_free(b);
+        delete b;
+        return bfail(nullptr, LBM_E_CUDA, m);
+    }
+    *out = b;
+    return LBM_OK;
+}
+
+int lbm_batch_destroy(lbm_batch b) {
+    if (!b) return LBM_OK;
+    cudaSetDevice(b->device);
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    batch_free(b);
+    delete b;
+    return LBM_OK;
+}
+
+int lbm_batch_step(lbm_batch b, int64_t n) {
+    if (!b) return LBM_E_INVAL;
+    if (n < 0) return bfail(b, LBM_E_INVAL, "negative step count");
+    cudaError_t e = cudaSetDevice(b->device);
+    if (e != cudaSuccess) return bfail(b, LBM_E_CUDA, cudaGetErrorString(e));
+    for (auto h : b->runs)
+        if (h->timing) return bfail(b, LBM_E_STATE, "a run of the batch has per-kernel timing enabled");
+    int rc;
+    while (n >= 2) {
+        // a captured graph bakes in every run's buffer parity and launch shape
+        bool stale = !b->graph;
+        for (size_t i = 0; i < b->runs.size(); i++)
+            stale = stale || b->versions[i] != b->runs[i]->version || b->parities[i] != b->runs[i]->parity;
+        if (stale) {
+            if (b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; }
+            // order the capture after everything already queued on the runs' streams
+            for (size_t i = 0; i < b->runs.size(); i++) {
+                if ((e = cudaEventRecord(b->join[i], b->runs[i]->stream)) != cudaSuccess ||
+                    (e = cudaStreamWaitEvent(b->stream, b->join[i], 0)) != cudaSuccess)
+                    return bfail(b, LBM_E_CUDA, cudaGetErrorString(e));
+            }
+            if ((rc = batch_build_graph(b)) != LBM_OK) return rc;
+        }
+        // the graph starts after the runs' queued work and the runs' streams
+        // wait for the graph before any later work of their own
+        for (size_t i = 0; i < b->runs.size(); i++) {
+            if ((e = cudaEventRecord(b->join[i], b->runs[i]->stream)) != cudaSuccess ||
+                (e = cudaStreamWaitEvent(b->stream, b->join[i], 0)) != cudaSuccess)
+                return bfail(b, LBM_E_CUDA, cudaGetErrorString(e));
+        }
+        if ((e = cudaGraphLaunch(b->graph, b->stream)) != cudaSuccess) return bfail(b, LBM_E_CUDA, cudaGetErrorString(e));
+        if ((e = cudaEventRecord(b->fork, b->stream)) != cudaSuccess) return bfail(b, LBM_E_CUDA, cudaGetErrorString(e));
+        for (auto h : b->runs) {
+            if ((e = cudaStreamWaitEvent(h->stream, b->fork, 0)) != cudaSuccess) return bfail(b, LBM_E_CUDA, cudaGetErrorString(e));
+            h->steps += 2;
+        }
+        n -= 2;
+    }
+    if (n == 1) {
+        // odd remainder: one step of every run on its own stream
+        for (auto h : b->runs)
+            if ((rc = lbm_step(h, 1)) != LBM_OK) return bfail(b, rc, h->msg);
+    }
+    return LBM_OK;
+}
+
+int lbm_batch_sync(lbm_batch b) {
+    if (!b) return LBM_E_INVAL;
+    cudaError_t e = cudaSetDevice(b->device);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return bfail(b, LBM_E_CUDA, cudaGetErrorString(e));
+    for (auto h : b->runs) {
+        int rc = lbm_sync(h);
+        if (rc != LBM_OK) return bfail(b, rc, h->msg);
+    }
+    return LBM_OK;
+}
+
+const char *lbm_batch_last_error(lbm_batch b) { return b ? b->msg.c_str() : g_create_error.c_str(); }
+
 int lbm_variants(lbm_handle h, int kind, int *count, int *selected) {
     if (!h || (kind != 0 && kind != 1)) return h ? fail(h, LBM_E_INVAL, "kind must be 0 (flow) or 1 (heat)") : LBM_E_INVAL;
     if (count) *count = kind == 0 ? h->ks->n_flow : h->ks->n_heat;
@@ -565,6 +732,7 @@ int lbm_select_variants(lbm_handle h, int flow, int heat) {
     if (h->graph) { cudaGraphExecDestroy(h->graph); h->graph = nullptr; }
     h->fv = flow;
     h->hv = heat;
+    h->version++;
     h->nblk = h->ks->flow[flow].blocks(h->p);
     return LBM_OK;
 }

@@ -30,6 +30,8 @@ EXPORTS = ("lbm_create", "lbm_destroy", "lbm_step", "lbm_sync", "lbm_step_count"
            "lbm_set_state", "lbm_wall_heat_flux", "lbm_vapour_fraction", "lbm_mass", "lbm_series",
            "lbm_set_timing", "lbm_kernel_times", "lbm_kernels_per_step", "lbm_variants",
            "lbm_variant_name", "lbm_select_variants", "lbm_autotune", "lbm_diagnostics_static",
+           "lbm_batch_create", "lbm_batch_step", "lbm_batch_sync", "lbm_batch_destroy",
+           "lbm_batch_last_error",
            "lbm_last_error",
            "lbm_status_string")
 
@@ -113,6 +115,12 @@ def load(path: str = LIB_PATH):
     L.lbm_variant_name.restype = C.c_char_p
     L.lbm_select_variants.argtypes = [C.c_void_p, C.c_int, C.c_int]
     L.lbm_autotune.argtypes = [C.c_void_p, C.c_int, _D]
+    L.lbm_batch_create.argtypes = [C.POINTER(C.c_void_p), C.c_int32, C.POINTER(C.c_void_p)]
+    L.lbm_batch_step.argtypes = [C.c_void_p, C.c_int64]
+    L.lbm_batch_sync.argtypes = [C.c_void_p]
+    L.lbm_batch_destroy.argtypes = [C.c_void_p]
+    L.lbm_batch_last_error.argtypes = [C.c_void_p]
+    L.lbm_batch_last_error.restype = C.c_char_p
     L.lbm_diagnostics_static.argtypes = [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_int32,
                                          C.c_double, C.c_double, C.c_double, C.c_double, C.c_void_p,
                                          C.c_void_p]
@@ -322,4 +330,41 @@ def diagnostics_static(rho_ptr: int, T_ptr: int, cfg, out_ptr: int, stream=None)
     rc = load().lbm_diagnostics_static(rho_ptr, T_ptr, cfg.nx, cfg.nf, cfg.ns, cfg.lambda_s, cfg.cv_chi,
                                        cfg.rho_L, cfg.rho_V, out_ptr, stream)
     _check(rc, None, "lbm_diagnostics_static")
+
+
+class Batch:
+    """Steps several runs together through one concurrent CUDA graph
+    (lbm_batch_* in include/lbm.h).  Keeps references to its runs."""
+
+    def __init__(self, runs):
+        L = load()
+        self.runs = list(runs)
+        arr = (C.c_void_p * len(self.runs))(*[r.handle for r in self.runs])
+        b = C.c_void_p()
+        rc = L.lbm_batch_create(arr, len(self.runs), C.byref(b))
+        if rc != LBM_OK:
+            raise LbmError(rc, "lbm_batch_create", L.lbm_batch_last_error(None).decode())
+        self._b = b
+
+    def _check(self, rc, where):
+        if rc != LBM_OK:
+            raise LbmError(rc, where, load().lbm_batch_last_error(self._b).decode())
+
+    def step(self, n: int = 1):
+        self._check(load().lbm_batch_step(self._b, int(n)), "lbm_batch_step")
+        return self
+
+    def sync(self):
+        self._check(load().lbm_batch_sync(self._b), "lbm_batch_sync")
+
+    def close(self):
+        if getattr(self, "_b", None):
+            load().lbm_batch_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 

@@ -117,6 +117,12 @@ def small_parity(seed: int = 1, precision: str = "fp64") -> RunConfig:
         T_b_over_Tc=0.96, lambda_s=3.25, rho_c_s=39.0, seed=seed, precision=precision)
 
 
+#: Gravity of the 400 x 600 domain: twice as tall as the paper's 400 x 300,
+#: so the buoyancy head (rho_mean - rho_V) g H of the vapour column is kept
+#: by halving g (at g = 5e-5 the run breaks down within 2000 steps).
+G_PAPER_TALL = 2.5e-5
+
+
 def paper_scale(superheat_over_Tc: float = 0.1, bc_mode: str = "spots", seed: int = 2,
                 precision: str = "fp64") -> RunConfig:
     """400 x 600 fluid over a 30-row heater (lambda_S = 16.25, rho_S = 3 rho_L)."""
@@ -124,7 +130,7 @@ def paper_scale(superheat_over_Tc: float = 0.1, bc_mode: str = "spots", seed: in
     return RunConfig(
         nx=400, nf=600, ns=30, liquid_rows=200, bc_mode=bc_mode, spot_x=spots,
         spot_half_width=5, c_w_spot=DEFAULT_CW_SPOTS if spots else (),
-        T_b_over_Tc=0.86 + superheat_over_Tc, seed=seed, precision=precision)
+        T_b_over_Tc=0.86 + superheat_over_Tc, g=G_PAPER_TALL, seed=seed, precision=precision)
 
 
 #: Gravity of the 2048-wide domain.  The paper's g = 5e-5 makes the Taylor
@@ -150,3 +156,26 @@ def periodic_box(nx: int, ny: int, liquid_rows: int = 0, **kw) -> RunConfig:
                 g=0.0, init_noise=0.0, bc_mode="spots")
     base.update(kw)
     return RunConfig(**base)
+
+
+def sweep(n_runs: int = 48, seed: int = 4, precision: str = "fp32") -> list:
+    """Boiling-curve sweep: widths drawn from {128, 256, 384, 512}, height
+    1.5 x width, heater 16-32 rows, superheat uniform in 0.02-0.3 Tc, bottom
+    mode 50/50 spots / noise.  Gravity follows the domain width as in
+    ``large`` (two Taylor wavelengths across)."""
+    import random
+    rng = random.Random(seed)
+    runs = []
+    for i in range(n_runs):
+        w = rng.choice((128, 256, 384, 512))
+        h = (3 * w) // 2
+        ns = rng.randint(16, 32)
+        dT = rng.uniform(0.02, 0.3)
+        mode = "spots" if rng.random() < 0.5 else "noise"
+        spots = scaled_spots(w) if mode == "spots" else ()
+        runs.append(RunConfig(
+            nx=w, nf=h, ns=ns, liquid_rows=h // 3, bc_mode=mode, spot_x=spots,
+            spot_half_width=max(1, w // 80), c_w_spot=DEFAULT_CW_SPOTS if spots else (),
+            T_b_over_Tc=0.86 + dT, g=5e-5 * (400.0 / w) ** 2 if w > 400 else 5e-5,
+            seed=100 + i, precision=precision))
+    return runs
