@@ -222,6 +222,66 @@ def measure_sweep(lbm, W, torch, dev, steps):
             "note": "sequential FP64 timed on every 6th run and scaled to 48"}
 
 
+def measure_serving(lbm, W, n_requests, step_scale, load=0.8):
+    """Served requests (Poisson arrivals at `load` x the measured capacity,
+    150 GB device-memory budget): p50 / p99 time-to-result and aggregate
+    MLUPS.  Step counts are the workload's times step_scale."""
+    import random
+    reqs = W.serving_requests(n_requests, step_scale=step_scale)
+    # capacity: measured site-update rate of each precision on a mid-size run
+    rate = {}
+    for prec in ("fp32", "fp64"):
+        c = W.serving_requests(1)[0][0].replace(nx=512, nf=768, ns=32, liquid_rows=256, precision=prec)
+        r = lbm.Run(c)
+        r.step(4)
+        r.sync()
+        t0 = time.perf_counter()
+        r.step(100)
+        r.sync()
+        rate[prec] = c.fluid_sites * 100 / (time.perf_counter() - t0)
+        r.close()
+    mean_service = sum(c.fluid_sites * n / rate[c.precision] for c, n in reqs) / len(reqs)
+    lam = load / mean_service
+    rng = random.Random(55)
+    arrivals, t = [], 0.0
+    for _ in reqs:
+        t += rng.expovariate(lam)
+        arrivals.append(t)
+    srv = lbm.Server(hbm_budget_bytes=150 * 10**9, max_active=64, chunk_steps=200)
+    ids = [None] * len(reqs)
+    nxt = 0
+    t0 = time.perf_counter()
+    done = 0
+    while done < len(reqs):
+        now = time.perf_counter() - t0
+        while nxt < len(reqs) and arrivals[nxt] <= now:
+            ids[nxt] = srv.submit(reqs[nxt][0], reqs[nxt][1])
+            nxt += 1
+        q, a, _ = srv.counts()
+        if a == 0 and q == 0:
+            if nxt < len(reqs):
+                time.sleep(max(0.0, arrivals[nxt] - (time.perf_counter() - t0)))
+            continue
+        done += srv.tick()
+    makespan = time.perf_counter() - t0
+    ttr, work = [], 0.0
+    for i, (c, n) in zip(ids, reqs):
+        st, (ts, t1, t2) = srv.status(i)
+        if st == 2:
+            ttr.append(t2 - ts)
+            work += c.fluid_sites * n
+    srv.close()
+    ttr.sort()
+
+    def pct(p):
+        return ttr[min(len(ttr) - 1, int(round(p / 100.0 * (len(ttr) - 1))))] if ttr else None
+
+    return {"requests": len(reqs), "completed": len(ttr), "step_scale": step_scale, "offered_load": load,
+            "arrival_rate_per_s": lam, "p50_s": pct(50), "p99_s": pct(99), "makespan_s": makespan,
+            "aggregate_mlups": work / makespan / 1e6, "budget_bytes": 150 * 10**9,
+            "capacity_mlups": {k: v / 1e6 for k, v in rate.items()}}
+
+
 def run_ours(args):
     import torch
 
@@ -348,6 +408,10 @@ def run_ours(args):
     if not args.no_sweep:
         sweep = measure_sweep(lbm, W, torch, dev, args.sweep_steps)
 
+    serve = None
+    if args.serve:
+        serve = measure_serving(lbm, W, args.serve_requests, args.serve_step_scale)
+
     # ---- CPU baseline: the oracle on a bounded sample (rank 0, N = 1) ----
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
@@ -379,6 +443,7 @@ def run_ours(args):
             "cpu_baseline": cpu,
             "fp64": fp64,
             "sweep": sweep,
+            "serve": serve,
         }
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -398,6 +463,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--sweep-steps", type=int, default=200)
+    ap.add_argument("--serve", action="store_true", help="also measure the request loop")
+    ap.add_argument("--serve-requests", type=int, default=200)
+    ap.add_argument("--serve-step-scale", type=float, default=0.02)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

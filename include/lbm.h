@@ -226,6 +226,37 @@ int lbm_batch_sync(lbm_batch b);
 int lbm_batch_destroy(lbm_batch b);
 const char *lbm_batch_last_error(lbm_batch b);
 
+/* Device memory (bytes, upper estimate) a run of this configuration holds. */
+int lbm_device_bytes(const lbm_domain_t *domain, const lbm_heater_t *heater, const lbm_opts_t *opts,
+                     uint64_t *bytes);
+
+/* Request loop with continuous batching (serving).  A server owns the runs
+ * it creates.  lbm_server_submit queues a request (the five configuration
+ * structs, copied; a step count; keep_fields = 1 to keep rho and T of the
+ * final state) and returns its id.  Each lbm_server_tick admits queued
+ * requests in arrival order while at most max_active runs are active and
+ * their lbm_device_bytes sum stays within hbm_budget_bytes, advances every
+ * active run by min(chunk_steps, the smallest remaining step count) through
+ * one concurrent batch graph, waits for it, and retires finished runs (their
+ * device memory is freed before the next admission).  A run whose kernels
+ * latch a numerical fault is retired as failed alone.  lbm_server_status:
+ * state 0 queued, 1 running, 2 done, 3 failed, and the submit / start /
+ * finish times in seconds since the server was created.
+ * lbm_server_result copies the final diagnostics (4 values, as one row of
+ * lbm_series) and the kept fields.  Not thread-safe. */
+typedef struct lbm_server_s *lbm_server;
+int lbm_server_create(uint64_t hbm_budget_bytes, int32_t max_active, int32_t chunk_steps, int32_t device,
+                      lbm_server *out);
+int lbm_server_submit(lbm_server s, const lbm_domain_t *domain, const lbm_heater_t *heater,
+                      const lbm_eos_t *eos, const lbm_bc_t *bc, const lbm_opts_t *opts, int64_t steps,
+                      int32_t keep_fields, int64_t *id);
+int lbm_server_tick(lbm_server s, int32_t *finished);
+int lbm_server_status(lbm_server s, int64_t id, int32_t *state, double *times /* [3] */);
+int lbm_server_result(lbm_server s, int64_t id, double *diag4, double *rho, double *T);
+int lbm_server_counts(lbm_server s, int32_t *queued, int32_t *active, uint64_t *bytes_in_use);
+int lbm_server_destroy(lbm_server s);
+const char *lbm_server_last_error(lbm_server s);
+
 /* Diagnostics of one state without allocating device memory.  The paper has
  * no counterpart: this entry point exists for callers that cannot call
  * cudaMalloc or cudaFree -- a host program whose device memory is owned by

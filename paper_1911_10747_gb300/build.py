@@ -5,6 +5,7 @@ Three translation units compiled in parallel by nvcc, then linked:
   csrc/lbm_fp32.cu     FP32 / FP16-storage kernels
   csrc/lbm_runtime.cu  host runtime and the C ABI of include/lbm.h
   csrc/lbm_static_diag.cu  the allocation-free diagnostics entry point
+  csrc/lbm_server.cu   continuous-batching request loop (host code)
 Host code is compiled with -ffp-contract=off so the FP64 constants derived
 on the host round the same way on x86-64 and AArch64.
 """
@@ -22,7 +23,7 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "liblbm_gb300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 UNITS = {"lbm_fp64.cu": ["-fmad=false"], "lbm_fp32.cu": [], "lbm_runtime.cu": [],
-         "lbm_static_diag.cu": ["-fmad=false"]}
+         "lbm_static_diag.cu": ["-fmad=false"], "lbm_server.cu": []}
 
 
 def nvcc() -> str:

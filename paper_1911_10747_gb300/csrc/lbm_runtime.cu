@@ -709,6 +709,23 @@ int lbm_batch_sync(lbm_batch b) {
 
 const char *lbm_batch_last_error(lbm_batch b) { return b ? b->msg.c_str() : g_create_error.c_str(); }
 
+int lbm_device_bytes(const lbm_domain_t *domain, const lbm_heater_t *heater, const lbm_opts_t *opts, uint64_t *bytes) {
+    if (!domain || !heater || !opts || !bytes) return fail(nullptr, LBM_E_INVAL, "NULL argument");
+    const KernelSet *ks = opts->precision == LBM_FP64 ? kernels_fp64()
+                          : opts->precision == LBM_FP32 ? kernels_fp32()
+                          : opts->precision == LBM_FP16 ? kernels_fp16() : nullptr;
+    if (!ks) return fail(nullptr, LBM_E_INVAL, "opts.precision invalid");
+    if (domain->nx < 1 || domain->ny_fluid < 1 || heater->ny_solid < 0) return fail(nullptr, LBM_E_INVAL, "bad sizes");
+    const uint64_t nfl = (uint64_t)domain->nx * domain->ny_fluid;
+    const uint64_t ntl = (uint64_t)domain->nx * (domain->ny_fluid + heater->ny_solid);
+    const uint64_t cap = opts->series_capacity > 0 ? (uint64_t)opts->series_capacity : 4096;
+    // populations x2, temperature x2, moments x3, per-column arrays, per-block
+    // partials (at most one block per 32 sites), series ring, small words
+    *bytes = 2 * 9 * nfl * ks->f_elem + 2 * ntl * ks->T_elem + 3 * nfl * ks->m_elem + 2 * 8 * (uint64_t)domain->nx +
+             2 * 8 * (nfl / 32 + 1) + cap * SERIES_WIDTH * 8 + 1024 * 8 + 4096;
+    return LBM_OK;
+}
+
 int lbm_variants(lbm_handle h, int kind, int *count, int *selected) {
     if (!h || (kind != 0 && kind != 1)) return h ? fail(h, LBM_E_INVAL, "kind must be 0 (flow) or 1 (heat)") : LBM_E_INVAL;
     if (count) *count = kind == 0 ? h->ks->n_flow : h->ks->n_heat;

@@ -31,7 +31,9 @@ EXPORTS = ("lbm_create", "lbm_destroy", "lbm_step", "lbm_sync", "lbm_step_count"
            "lbm_set_timing", "lbm_kernel_times", "lbm_kernels_per_step", "lbm_variants",
            "lbm_variant_name", "lbm_select_variants", "lbm_autotune", "lbm_diagnostics_static",
            "lbm_batch_create", "lbm_batch_step", "lbm_batch_sync", "lbm_batch_destroy",
-           "lbm_batch_last_error",
+           "lbm_batch_last_error", "lbm_device_bytes", "lbm_server_create", "lbm_server_submit",
+           "lbm_server_tick", "lbm_server_status", "lbm_server_result", "lbm_server_counts",
+           "lbm_server_destroy", "lbm_server_last_error",
            "lbm_last_error",
            "lbm_status_string")
 
@@ -121,6 +123,20 @@ def load(path: str = LIB_PATH):
     L.lbm_batch_destroy.argtypes = [C.c_void_p]
     L.lbm_batch_last_error.argtypes = [C.c_void_p]
     L.lbm_batch_last_error.restype = C.c_char_p
+    L.lbm_device_bytes.argtypes = [C.POINTER(lbm_domain_t), C.POINTER(lbm_heater_t), C.POINTER(lbm_opts_t),
+                                   C.POINTER(C.c_uint64)]
+    L.lbm_server_create.argtypes = [C.c_uint64, C.c_int32, C.c_int32, C.c_int32, C.POINTER(C.c_void_p)]
+    L.lbm_server_submit.argtypes = [C.c_void_p, C.POINTER(lbm_domain_t), C.POINTER(lbm_heater_t),
+                                    C.POINTER(lbm_eos_t), C.POINTER(lbm_bc_t), C.POINTER(lbm_opts_t),
+                                    C.c_int64, C.c_int32, C.POINTER(C.c_int64)]
+    L.lbm_server_tick.argtypes = [C.c_void_p, C.POINTER(C.c_int32)]
+    L.lbm_server_status.argtypes = [C.c_void_p, C.c_int64, C.POINTER(C.c_int32), _D]
+    L.lbm_server_result.argtypes = [C.c_void_p, C.c_int64, _D, _D, _D]
+    L.lbm_server_counts.argtypes = [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                    C.POINTER(C.c_uint64)]
+    L.lbm_server_destroy.argtypes = [C.c_void_p]
+    L.lbm_server_last_error.argtypes = [C.c_void_p]
+    L.lbm_server_last_error.restype = C.c_char_p
     L.lbm_diagnostics_static.argtypes = [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_int32,
                                          C.c_double, C.c_double, C.c_double, C.c_double, C.c_void_p,
                                          C.c_void_p]
@@ -361,6 +377,76 @@ class Batch:
         if getattr(self, "_b", None):
             load().lbm_batch_destroy(self._b)
             self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def device_bytes(cfg) -> int:
+    d, ht, _, _, op = structs_from_config(cfg)
+    out = C.c_uint64()
+    _check(load().lbm_device_bytes(C.byref(d), C.byref(ht), C.byref(op), C.byref(out)), None, "lbm_device_bytes")
+    return int(out.value)
+
+
+class Server:
+    """Continuous-batching request loop (lbm_server_* in include/lbm.h)."""
+
+    def __init__(self, hbm_budget_bytes: int, max_active: int = 64, chunk_steps: int = 200, device: int = 0):
+        L = load()
+        s = C.c_void_p()
+        rc = L.lbm_server_create(int(hbm_budget_bytes), int(max_active), int(chunk_steps), int(device), C.byref(s))
+        if rc != LBM_OK:
+            raise LbmError(rc, "lbm_server_create", L.lbm_last_error(None).decode())
+        self._s = s
+        self._cfg = {}
+
+    def _check(self, rc, where):
+        if rc != LBM_OK:
+            raise LbmError(rc, where, load().lbm_server_last_error(self._s).decode())
+
+    def submit(self, cfg, steps: int, keep_fields: bool = False) -> int:
+        d, ht, eo, bc, op = structs_from_config(cfg)
+        rid = C.c_int64()
+        self._check(load().lbm_server_submit(self._s, C.byref(d), C.byref(ht), C.byref(eo), C.byref(bc),
+                                             C.byref(op), int(steps), 1 if keep_fields else 0, C.byref(rid)),
+                    "lbm_server_submit")
+        self._cfg[rid.value] = cfg
+        return int(rid.value)
+
+    def tick(self) -> int:
+        n = C.c_int32()
+        self._check(load().lbm_server_tick(self._s, C.byref(n)), "lbm_server_tick")
+        return int(n.value)
+
+    def status(self, rid: int):
+        st = C.c_int32()
+        t = (C.c_double * 3)()
+        self._check(load().lbm_server_status(self._s, int(rid), C.byref(st), t), "lbm_server_status")
+        return int(st.value), tuple(t)
+
+    def result(self, rid: int, fields: bool = False):
+        cfg = self._cfg[rid]
+        diag = np.zeros(4)
+        rho = np.empty((cfg.nf, cfg.nx)) if fields else None
+        T = np.empty((cfg.ns + cfg.nf, cfg.nx)) if fields else None
+        self._check(load().lbm_server_result(self._s, int(rid), diag.ctypes.data_as(_D),
+                                             None if rho is None else rho.ctypes.data_as(_D),
+                                             None if T is None else T.ctypes.data_as(_D)), "lbm_server_result")
+        return (diag, rho, T) if fields else diag
+
+    def counts(self):
+        q, a, b = C.c_int32(), C.c_int32(), C.c_uint64()
+        self._check(load().lbm_server_counts(self._s, C.byref(q), C.byref(a), C.byref(b)), "lbm_server_counts")
+        return int(q.value), int(a.value), int(b.value)
+
+    def close(self):
+        if getattr(self, "_s", None):
+            load().lbm_server_destroy(self._s)
+            self._s = None
 
     def __del__(self):
         try:

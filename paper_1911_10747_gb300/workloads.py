@@ -179,3 +179,30 @@ def sweep(n_runs: int = 48, seed: int = 4, precision: str = "fp32") -> list:
             T_b_over_Tc=0.86 + dT, g=5e-5 * (400.0 / w) ** 2 if w > 400 else 5e-5,
             seed=100 + i, precision=precision))
     return runs
+
+
+def serving_requests(n: int = 200, seed: int = 5, step_scale: float = 1.0) -> list:
+    """Served boiling runs: domains from {64x64, 128x192, 256x384, 512x768,
+    1024x1536} with w/16 heater rows (at least 8), steps log-uniform in
+    [1000, 50000] (times step_scale), superheat uniform in 0.02-0.3 Tc,
+    bottom mode 50/50, precision 75 % FP32 / 25 % FP64.  Returns a list of
+    (RunConfig, steps)."""
+    import math
+    import random
+    rng = random.Random(seed)
+    sizes = ((64, 64), (128, 192), (256, 384), (512, 768), (1024, 1536))
+    out = []
+    for i in range(n):
+        w, h = rng.choice(sizes)
+        ns = max(8, w // 16)
+        steps = int(round(math.exp(rng.uniform(math.log(1000), math.log(50000))) * step_scale))
+        dT = rng.uniform(0.02, 0.3)
+        mode = "spots" if rng.random() < 0.5 else "noise"
+        prec = "fp32" if rng.random() < 0.75 else "fp64"
+        spots = scaled_spots(w) if mode == "spots" else ()
+        cfg = RunConfig(nx=w, nf=h, ns=ns, liquid_rows=h // 3, bc_mode=mode, spot_x=spots,
+                        spot_half_width=max(1, w // 80), c_w_spot=DEFAULT_CW_SPOTS if spots else (),
+                        T_b_over_Tc=0.86 + dT, g=5e-5 * (400.0 / w) ** 2 if w > 400 else 5e-5,
+                        seed=1000 + i, precision=prec)
+        out.append((cfg, max(2, steps)))
+    return out
