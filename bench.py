@@ -282,6 +282,62 @@ def measure_serving(lbm, W, n_requests, step_scale, load=0.8):
             "capacity_mlups": {k: v / 1e6 for k, v in rate.items()}}
 
 
+def measure_chf(lbm, W, steps):
+    """Boiling curve on a 256 x 384 domain over 16 heater rows (constant
+    bottom with nucleate spots): time-averaged heater-bottom flux Q'' over
+    the second half of `steps` steps at 7 superheats, in FP32 and FP64 (all
+    14 runs in one batch).  CHF = max Q'' over the superheats."""
+    base = W.sweep(1)[0].replace(nx=256, nf=384, ns=16, liquid_rows=128, bc_mode="spots",
+                                 spot_x=W.scaled_spots(256), spot_half_width=3,
+                                 c_w_spot=W.DEFAULT_CW_SPOTS, g=W.stable_gravity(384, 128), seed=21)
+    dts = [0.04, 0.08, 0.12, 0.16, 0.20, 0.24, 0.28]
+    cfgs = [base.replace(T_b_over_Tc=0.86 + d, precision=p) for p in ("fp32", "fp64") for d in dts]
+    runs = [lbm.Run(c, series_capacity=steps + 8) for c in cfgs]
+    alive = list(range(len(runs)))
+    fault = [None] * len(runs)
+    t0 = time.perf_counter()
+    chunk = 1000
+    done = 0
+    while done < steps and alive:
+        k = min(chunk, steps - done)
+        b = lbm.Batch([runs[i] for i in alive])
+        try:
+            b.step(k)
+            b.sync()
+        except lbm.LbmError:
+            pass
+        b.close()
+        still = []
+        for i in alive:
+            try:
+                runs[i].sync()
+                still.append(i)
+            except lbm.LbmError:
+                fault[i] = done + k  # faulted within this chunk
+        alive = still
+        done += k
+    dt = time.perf_counter() - t0
+    q = [None] * len(runs)
+    for i in alive:
+        ser = runs[i].series(0, steps)
+        q[i] = float(ser[steps // 2:, 0].mean())
+    for r in runs:
+        r.close()
+    n = len(dts)
+    q32, q64 = q[:n], q[n:]
+    both = [j for j in range(n) if q32[j] is not None and q64[j] is not None]
+    c32 = max(q32[j] for j in both) if both else None
+    c64 = max(q64[j] for j in both) if both else None
+    return {"domain": "256x384 fluid + 16 heater rows, spots", "steps": steps, "superheats_over_Tc": dts,
+            "q_fp32": q32, "q_fp64": q64, "fault_step_fp32": fault[:n], "fault_step_fp64": fault[n:],
+            "chf_fp32": c32, "chf_fp64": c64,
+            "chf_superheat_fp32": dts[q32.index(c32)] if both else None,
+            "chf_superheat_fp64": dts[q64.index(c64)] if both else None,
+            "chf_rel_error": abs(c32 - c64) / abs(c64) if both else None,
+            "max_rel_error_curve": max(abs(q32[j] - q64[j]) / abs(q64[j]) for j in both) if both else None,
+            "seconds": dt}
+
+
 def run_ours(args):
     import torch
 
@@ -408,6 +464,9 @@ def run_ours(args):
     if not args.no_sweep:
         sweep = measure_sweep(lbm, W, torch, dev, args.sweep_steps)
 
+    chf = None
+    if args.chf:
+        chf = measure_chf(lbm, W, args.chf_steps)
     serve = None
     if args.serve:
         serve = measure_serving(lbm, W, args.serve_requests, args.serve_step_scale)
@@ -444,6 +503,7 @@ def run_ours(args):
             "fp64": fp64,
             "sweep": sweep,
             "serve": serve,
+            "chf": chf,
         }
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -463,6 +523,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--sweep-steps", type=int, default=200)
+    ap.add_argument("--chf", action="store_true", help="also measure the FP32 vs FP64 boiling curve")
+    ap.add_argument("--chf-steps", type=int, default=20000)
     ap.add_argument("--serve", action="store_true", help="also measure the request loop")
     ap.add_argument("--serve-requests", type=int, default=200)
     ap.add_argument("--serve-step-scale", type=float, default=0.02)
