@@ -158,6 +158,20 @@ def oracle_sample(cfg, steps: int):
     return cfg.fluid_sites * steps / dt / 1e6, dt
 
 
+def aggregate_over_ranks(ms: float, sites: int, steps: int, device=None):
+    """Replicas: every rank ran `steps` steps of its own run of `sites` fluid
+    sites in `ms` milliseconds.  Returns (slowest rank's ms, whole-job MLUPS
+    = all ranks' site updates / slowest time)."""
+    import torch
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    return ms_max, ws * sites * steps / (ms_max / 1e3) / 1e6
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -386,11 +400,7 @@ def run_ours(args):
     barrier()
     ms = e0.elapsed_time(e1)
     run.sync()
-    t_all = torch.tensor([ms], device=dev, dtype=torch.float64)
-    if ws > 1:
-        torch.distributed.all_reduce(t_all, op=torch.distributed.ReduceOp.MAX)
-    ms_max = float(t_all.item())
-    value = ws * sites * args.steps / (ms_max / 1e3) / 1e6
+    ms_max, value = aggregate_over_ranks(ms, sites, args.steps, dev)
 
     # ---- per-kernel durations over K more steps (events around each launch) ----
     run.set_timing(True)
