@@ -330,7 +330,7 @@ k_flow_fast(const FParams p, const typename P::fst *__restrict__ fin, typename P
     if (errbits) atomicOr(err, errbits);
 }
 
-template <class P, int BX, int BY, int RY, int MINB>
+template <class P, int BX, int BY, int RY, int MINB, bool WIDE>
 __global__ void __launch_bounds__(BX *BY, MINB)
 k_flow_pers(const FParams p, int tiles_x, int ntiles, const typename P::fst *__restrict__ fin, typename P::fst *__restrict__ fout,
             const typename P::tst *__restrict__ Tin, float *__restrict__ rho_o, float *__restrict__ ux_o,
@@ -354,7 +354,12 @@ k_flow_pers(const FParams p, int tiles_x, int ntiles, const typename P::fst *__r
     float g[RY][9];
     float dd[RY];
     float gT[RY];
-    const bool wide = nx >= TX + 1;  // then tile columns +-1 wrap with one compare
+    // WIDE (compile time): nx >= TX + 1 and, if periodic in y, nf >= TY + 2, so
+    // every wrap below is one compare instead of an integer modulo
+    auto wx = [&](int v) { return WIDE ? wrap1(v, nx) : wrapi(v, nx); };
+    auto wy = [&](int v) { return WIDE ? wrap1(v, nf) : wrapi(v, nf); };
+    // tile coordinates advance by gridDim.x tiles per iteration without a division
+    const int gdx = (int)gridDim.x % tiles_x, gdy = (int)gridDim.x / tiles_x;
     // populations and temperature of the next tile, loaded during this tile
     float pg[RY][9];
     float pTv[RY];
@@ -368,13 +373,13 @@ k_flow_pers(const FParams p, int tiles_x, int ntiles, const typename P::fst *__r
         else if (k < 2 * SW) { hx = k - SW; hy = SH - 1; }
         else if (k < 2 * SW + TY) { hx = 0; hy = 1 + (k - 2 * SW); }
         else { hx = SW - 1; hy = 1 + (k - 2 * SW - TY); }
-        x = wide ? wrap1(x0 + hx - 1, nx) : wrapi(x0 + hx - 1, nx);
+        x = wx(x0 + hx - 1);
         y = y0 + hy - 1;
-        if (py) y = wrapi(y, nf);
+        if (py) y = wy(y);
         return py || (y >= 0 && y < nf);
     };
-    auto fetch = [&](int tile) {
-        const int x0 = (tile % tiles_x) * TX, y0 = (tile / tiles_x) * TY;
+    auto fetch = [&](int txt, int tyt) {
+        const int x0 = txt * TX, y0 = tyt * TY;
         if (tid < RING && !frozen) {
             int hx, hy, x, y;
             rvalid = ring_site(tid, x0, y0, hx, hy, x, y);
@@ -388,10 +393,10 @@ k_flow_pers(const FParams p, int tiles_x, int ntiles, const typename P::fst *__r
         #pragma unroll
         for (int r = 0; r < RY; r++) {
             const int lx = threadIdx.x, ly = threadIdx.y + r * BY;
-            const int x = wide ? wrap1(x0 + lx, nx) : wrapi(x0 + lx, nx);
+            const int x = wx(x0 + lx);
             int y = y0 + ly;
             const bool has = py || y < nf;
-            if (py) y = wrapi(y, nf);
+            if (py) y = wy(y);
             if (has) {
                 const size_t k = (size_t)y * nx + x;
                 #pragma unroll
@@ -405,9 +410,12 @@ k_flow_pers(const FParams p, int tiles_x, int ntiles, const typename P::fst *__r
         }
     };
     float mass = 0.0f, nvap = 0.0f;
-    if ((int)blockIdx.x < ntiles) fetch(blockIdx.x);
+    int cxt = (int)blockIdx.x % tiles_x, cyt = (int)blockIdx.x / tiles_x;  // current tile
+    if ((int)blockIdx.x < ntiles) fetch(cxt, cyt);
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int x0 = (tile % tiles_x) * TX, y0 = (tile / tiles_x) * TY;
+    const int x0 = cxt * TX, y0 = cyt * TY;
+    int nxt = cxt + gdx, nyt = cyt + gdy;  // next tile of this block
+    if (nxt >= tiles_x) { nxt -= tiles_x; nyt += 1; }
     #pragma unroll
     for (int r = 0; r < RY; r++) {
         #pragma unroll
@@ -442,7 +450,7 @@ k_flow_pers(const FParams p, int tiles_x, int ntiles, const typename P::fst *__r
         s_psi[hy * SW + hx] = psi;
     }
     // the next tile's loads (own sites and ring) fly during this tile's collisions
-    if (tile + (int)gridDim.x < ntiles) fetch(tile + gridDim.x);
+    if (tile + (int)gridDim.x < ntiles) fetch(nxt, nyt);
     __syncthreads();
 
     // ---- collide and push ----
@@ -578,6 +586,7 @@ k_flow_pers(const FParams p, int tiles_x, int ntiles, const typename P::fst *__r
         }
     }
     __syncthreads();  // s_psi is rewritten by the next tile
+    cxt = nxt; cyt = nyt;
     }
     // per-block mass and vapour count: FP32 inside the block, FP64 across blocks
     #pragma unroll
@@ -864,7 +873,7 @@ struct FlowPersShape {
         int dev = 0, sms = 0, per = 0;
         cudaError_t e = cudaGetDevice(&dev);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_flow_pers<P, BX, BY, RY, MINB>, BX * BY, 0);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_flow_pers<P, BX, BY, RY, MINB, true>, BX * BY, 0);
         if (e != cudaSuccess) return e;
         grid_blocks = sms * (per > 0 ? per : 1);
         return cudaSuccess;
@@ -872,7 +881,9 @@ struct FlowPersShape {
     static int tiles(const DevParams &p) { return ((p.nx + BX - 1) / BX) * ((p.nf + BY * RY - 1) / (BY * RY)); }
     static int blocks(const DevParams &p) { const int t = tiles(p); return t < grid_blocks ? t : grid_blocks; }
     static cudaError_t launch(const DevParams &p, const StepBuffers &b, cudaStream_t s) {
-        k_flow_pers<P, BX, BY, RY, MINB><<<blocks(p), dim3(BX, BY), 0, s>>>(
+        const bool wide = p.nx >= BX + 1 && (!(p.flags & FLAG_PERIODIC_Y) || p.nf >= BY * RY + 2);
+        auto k = wide ? k_flow_pers<P, BX, BY, RY, MINB, true> : k_flow_pers<P, BX, BY, RY, MINB, false>;
+        k<<<blocks(p), dim3(BX, BY), 0, s>>>(
             make_fparams(p), (p.nx + BX - 1) / BX, tiles(p), (const typename P::fst *)b.f_in, (typename P::fst *)b.f_out,
             (const typename P::tst *)b.T_in, (float *)b.rho, (float *)b.ux, (float *)b.uy, b.cw, b.part, b.err);
         return cudaGetLastError();
@@ -1319,7 +1330,7 @@ namespace lbmgb {
 // registers while the current tile is computed.  Same arithmetic as
 // k_heat_fast / k_heat_reg.
 // ============================================================================
-template <class P, int BW, int BY, int CPT, int MINB>
+template <class P, int BW, int BY, int CPT, int MINB, bool WIDE>
 __global__ void __launch_bounds__(BW * BY, MINB)
 k_heat_wide(const FParams p, int tiles_x, int ntiles, const typename P::tst *__restrict__ Tin,
             typename P::tst *__restrict__ Tout, const float *__restrict__ rho_i, const float *__restrict__ ux_i,
@@ -1340,23 +1351,25 @@ k_heat_wide(const FParams p, int tiles_x, int ntiles, const typename P::tst *__r
     float pT[CPT], pr[CPT], pux[CPT], puy[CPT];
     int pkd[CPT], prow[CPT], px[CPT];  // kind, row and column of the prefetched cells
 
-    const bool wide = nx >= BW;  // then x0 + tx - H lies in [-H, 2 nx): one compare wraps it
-    auto classify = [&](int tile, int c, int &row, int &x) {
-        const int x0 = (tile % tiles_x) * TXO, r0 = (tile / tiles_x) * TYO;
-        x = wide ? wrap1(x0 + tx - H, nx) : wrapi(x0 + tx - H, nx);
+    // WIDE (compile time): nx >= BW and, if periodic in y, nt >= SH, so the
+    // wraps below are one compare instead of an integer modulo
+    const int gdx = (int)gridDim.x % tiles_x, gdy = (int)gridDim.x / tiles_x;
+    auto classify = [&](int txt, int tyt, int c, int &row, int &x) {
+        const int x0 = txt * TXO, r0 = tyt * TYO;
+        x = WIDE ? wrap1(x0 + tx - H, nx) : wrapi(x0 + tx - H, nx);
         row = r0 + ty + c * BY - H;
         int k;
-        if (py) { row = wrapi(row, nt); k = 2; }
+        if (py) { row = WIDE ? wrap1(row, nt) : wrapi(row, nt); k = 2; }
         else if (row < 0 || row > nt) k = 0;
         else if (row == 0 || row == nt) k = 3;
         else k = (row < ns) ? 1 : 2;
         return k;
     };
-    auto fetch = [&](int tile) {
+    auto fetch = [&](int txt, int tyt) {
         #pragma unroll
         for (int c = 0; c < CPT; c++) {
             int row, x;
-            const int k = classify(tile, c, row, x);
+            const int k = classify(txt, tyt, c, row, x);
             pkd[c] = k; prow[c] = row; px[c] = x;
             pT[c] = 0.0f; pr[c] = 0.0f; pux[c] = 0.0f; puy[c] = 0.0f;
             if (k == 1 || k == 2) pT[c] = Tin[(size_t)row * nx + x];
@@ -1369,9 +1382,12 @@ k_heat_wide(const FParams p, int tiles_x, int ntiles, const typename P::tst *__r
         }
     };
     const float w1 = 1.0f / 9.0f, w2 = 1.0f / 36.0f;
-    if ((int)blockIdx.x < ntiles) fetch(blockIdx.x);
+    int cxt = (int)blockIdx.x % tiles_x, cyt = (int)blockIdx.x / tiles_x;  // current tile
+    if ((int)blockIdx.x < ntiles) fetch(cxt, cyt);
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int x0 = (tile % tiles_x) * TXO, r0 = (tile / tiles_x) * TYO;
+        const int x0 = cxt * TXO, r0 = cyt * TYO;
+        int nxt = cxt + gdx, nyt = cyt + gdy;  // next tile of this block
+        if (nxt >= tiles_x) { nxt -= tiles_x; nyt += 1; }
         float rcv[CPT], rho[CPT];
         // ---- load from the prefetched registers ----
         #pragma unroll
@@ -1394,7 +1410,7 @@ k_heat_wide(const FParams p, int tiles_x, int ntiles, const typename P::tst *__r
             sLam[hy][tx] = (lam > 0.0f) ? fast_rcp(lam) : 1e30f;
             sUx[hy][tx] = ux; sUy[hy][tx] = uy;
         }
-        if (tile + (int)gridDim.x < ntiles) fetch(tile + gridDim.x);
+        if (tile + (int)gridDim.x < ntiles) fetch(nxt, nyt);
         __syncthreads();
         // ---- per-step coefficients ----
         #pragma unroll
@@ -1494,6 +1510,7 @@ k_heat_wide(const FParams p, int tiles_x, int ntiles, const typename P::tst *__r
             }
         }
         __syncthreads();  // shared tiles are rewritten by the next tile
+        cxt = nxt; cyt = nyt;
     }
     if (errbits) atomicOr(err, errbits);
 }
@@ -1505,7 +1522,7 @@ struct HeatWideShape {
         int dev = 0, sms = 0, per = 0;
         cudaError_t e = cudaGetDevice(&dev);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_heat_wide<P, BW, BY, CPT, MINB>, BW * BY, 0);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_heat_wide<P, BW, BY, CPT, MINB, true>, BW * BY, 0);
         if (e != cudaSuccess) return e;
         grid_blocks = sms * (per > 0 ? per : 1);
         return cudaSuccess;
@@ -1515,7 +1532,9 @@ struct HeatWideShape {
         const int tx = (p.nx + TXO - 1) / TXO, ty = (p.nt + TYO - 1) / TYO;
         const int ntiles = tx * ty;
         const int g = ntiles < grid_blocks ? ntiles : grid_blocks;
-        k_heat_wide<P, BW, BY, CPT, MINB><<<g, dim3(BW, BY), 0, s>>>(
+        const bool wide = p.nx >= BW && (!(p.flags & FLAG_PERIODIC_Y) || p.nt >= BY * CPT);
+        auto k = wide ? k_heat_wide<P, BW, BY, CPT, MINB, true> : k_heat_wide<P, BW, BY, CPT, MINB, false>;
+        k<<<g, dim3(BW, BY), 0, s>>>(
             make_fparams(p), tx, ntiles, (const typename P::tst *)b.T_in, (typename P::tst *)b.T_out,
             (const float *)b.rho, (const float *)b.ux, (const float *)b.uy, b.step, b.err);
         return cudaGetLastError();
