@@ -34,8 +34,15 @@ struct lbm_run {
     int64_t steps = 0;
     void *f[2] = {nullptr, nullptr};
     void *T[2] = {nullptr, nullptr};
-    void *rho = nullptr, *ux = nullptr, *uy = nullptr;
-    double *cw = nullptr, *part = nullptr, *series = nullptr, *q_top = nullptr, *last = nullptr;
+    // moments and per-block partials are double-buffered by parity, so the
+    // diagnostics kernel of step n (side stream) can overlap the flow kernel
+    // of step n + 1
+    void *rho[2] = {nullptr, nullptr}, *ux[2] = {nullptr, nullptr}, *uy[2] = {nullptr, nullptr};
+    double *part[2] = {nullptr, nullptr};
+    double *cw = nullptr, *series = nullptr, *q_top = nullptr, *last = nullptr;
+    cudaStream_t dstream = nullptr;  // diagnostics stream
+    cudaEvent_t ev_heat = nullptr, ev_diag = nullptr;    // plain launches
+    cudaEvent_t cev_heat = nullptr, cev_diag = nullptr;  // inside stream captures
     double *scratch = nullptr;
     double *stage = nullptr;        // float64 staging for read-back / import
     size_t stage_elems = 0;
@@ -45,7 +52,8 @@ struct lbm_run {
     int nblk = 0;                   // blocks of the selected flow variant
     int fv = 0, hv = 0;             // selected flow / heat variants
     int version = 0;                // bumped when captured launch parameters change
-    cudaGraphExec_t graph = nullptr;
+    cudaGraphExec_t graph = nullptr;   // two steps
+    cudaGraphExec_t graph8 = nullptr;  // eight steps
     bool timing = false;
     std::vector<EventPair> ev[3];
     double t_ms[3] = {0, 0, 0};
@@ -74,11 +82,11 @@ static StepBuffers buffers(lbm_run *h, int par) {
     b.f_out = h->f[par ^ 1];
     b.T_in = h->T[par];
     b.T_out = h->T[par ^ 1];
-    b.rho = h->rho;
-    b.ux = h->ux;
-    b.uy = h->uy;
+    b.rho = h->rho[par];
+    b.ux = h->ux[par];
+    b.uy = h->uy[par];
     b.cw = h->cw;
-    b.part = h->part;
+    b.part = h->part[par];
     b.err = h->err;
     b.step = h->dstep;
     b.series = h->series;
@@ -91,16 +99,29 @@ static StepBuffers buffers(lbm_run *h, int par) {
 // Buffers describing the current state as the "output" side (init / import)
 // and as the "input" side (export).
 static StepBuffers state_as_out(lbm_run *h) { return buffers(h, h->parity ^ 1); }
-static StepBuffers state_as_in(lbm_run *h) { return buffers(h, h->parity); }
+static StepBuffers state_as_in(lbm_run *h) {
+    StepBuffers b = buffers(h, h->parity);
+    // the moments of the last step were written with the other parity
+    b.rho = h->rho[h->parity ^ 1];
+    b.ux = h->ux[h->parity ^ 1];
+    b.uy = h->uy[h->parity ^ 1];
+    return b;
+}
 
 static void free_all(lbm_run *h) {
     if (h->graph) cudaGraphExecDestroy(h->graph);
+    if (h->graph8) cudaGraphExecDestroy(h->graph8);
     for (int k = 0; k < 2; k++) {
         cudaFree(h->f[k]);
         cudaFree(h->T[k]);
     }
-    cudaFree(h->rho); cudaFree(h->ux); cudaFree(h->uy);
-    cudaFree(h->cw); cudaFree(h->part); cudaFree(h->series); cudaFree(h->q_top); cudaFree(h->last);
+    for (int k = 0; k < 2; k++) {
+        cudaFree(h->rho[k]); cudaFree(h->ux[k]); cudaFree(h->uy[k]); cudaFree(h->part[k]);
+    }
+    cudaFree(h->cw); cudaFree(h->series); cudaFree(h->q_top); cudaFree(h->last);
+    for (cudaEvent_t ev : {h->ev_heat, h->ev_diag, h->cev_heat, h->cev_diag})
+        if (ev) cudaEventDestroy(ev);
+    if (h->dstream) cudaStreamDestroy(h->dstream);
     cudaFree(h->scratch); cudaFree(h->stage); cudaFree(h->err); cudaFree(h->dstep);
     for (auto &v : h->ev)
         for (auto &e : v) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
@@ -246,6 +267,14 @@ int lbm_create(const lbm_domain_t *domain, const lbm_heater_t *heater, const lbm
         if (e != cudaSuccess) { cuda_fail(h, e, "cudaStreamCreate"); return bad(LBM_E_CUDA); }
         h->own_stream = true;
     }
+    if ((e = cudaStreamCreateWithFlags(&h->dstream, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&h->ev_heat, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&h->ev_diag, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&h->cev_heat, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&h->cev_diag, cudaEventDisableTiming)) != cudaSuccess) {
+        cuda_fail(h, e, "diagnostics stream");
+        return bad(LBM_E_CUDA);
+    }
     for (int v = 0; v < h->ks->n_heat; v++)
         if ((e = h->ks->heat[v].prepare()) != cudaSuccess) { cuda_fail(h, e, "kernel attributes"); return bad(LBM_E_CUDA); }
     for (int v = 0; v < h->ks->n_flow; v++)
@@ -258,8 +287,11 @@ int lbm_create(const lbm_domain_t *domain, const lbm_heater_t *heater, const lbm
     struct A { void **ptr; size_t bytes; } allocs[] = {
         {&h->f[0], 9 * nfl * h->ks->f_elem}, {&h->f[1], 9 * nfl * h->ks->f_elem},
         {&h->T[0], ntl * h->ks->T_elem}, {&h->T[1], ntl * h->ks->T_elem},
-        {&h->rho, nfl * h->ks->m_elem}, {&h->ux, nfl * h->ks->m_elem}, {&h->uy, nfl * h->ks->m_elem},
-        {(void **)&h->cw, (size_t)p.nx * sizeof(double)}, {(void **)&h->part, 2 * (size_t)max_blocks * sizeof(double)},
+        {&h->rho[0], nfl * h->ks->m_elem}, {&h->ux[0], nfl * h->ks->m_elem}, {&h->uy[0], nfl * h->ks->m_elem},
+        {&h->rho[1], nfl * h->ks->m_elem}, {&h->ux[1], nfl * h->ks->m_elem}, {&h->uy[1], nfl * h->ks->m_elem},
+        {(void **)&h->cw, (size_t)p.nx * sizeof(double)},
+        {(void **)&h->part[0], 2 * (size_t)max_blocks * sizeof(double)},
+        {(void **)&h->part[1], 2 * (size_t)max_blocks * sizeof(double)},
         {(void **)&h->series, (size_t)h->series_cap * SERIES_WIDTH * sizeof(double)},
         {(void **)&h->q_top, (size_t)p.nx * sizeof(double)}, {(void **)&h->last, SERIES_WIDTH * sizeof(double)},
         {(void **)&h->scratch, 1024 * sizeof(double)}, {(void **)&h->err, sizeof(unsigned)},
@@ -314,6 +346,7 @@ int lbm_create(const lbm_domain_t *domain, const lbm_heater_t *heater, const lbm
 int lbm_destroy(lbm_handle h) {
     if (!h) return LBM_OK;
     cudaSetDevice(h->device);
+    if (h->dstream) cudaStreamSynchronize(h->dstream);
     if (h->stream) cudaStreamSynchronize(h->stream);
     free_all(h);
     delete h;
@@ -323,40 +356,63 @@ int lbm_destroy(lbm_handle h) {
 static cudaError_t launch_kernel(lbm_run *h, int k, const StepBuffers &b) {
     if (k == 0) return h->ks->flow[h->fv].launch(h->p, b, h->stream);
     if (k == 1) return h->ks->heat[h->hv].launch(h->p, b, h->stream);
-    return h->ks->diag(h->p, b, h->nblk, h->stream);
+    return h->ks->diag(h->p, b, h->nblk, h->dstream);
 }
 
-static int launch_step(lbm_run *h, bool timed) {
+// Make the main stream wait for the last queued diagnostics kernel.  Events
+// recorded inside a stream capture cannot be waited on outside it, so
+// captures use their own pair.
+static cudaError_t join_diag(lbm_run *h, bool capturing = false) {
+    return cudaStreamWaitEvent(h->stream, capturing ? h->cev_diag : h->ev_diag, 0);
+}
+
+// One step: flow and heat on the main stream, diagnostics on the side
+// stream after the heat kernel.  The next step's flow kernel does not wait
+// for the diagnostics (moments and partials are double-buffered); its heat
+// kernel does (it reads the step counter the diagnostics kernel advances).
+// wait_prev_diag is false for the first step of a stream capture, which is
+// ordered after earlier work by the graph launch itself.
+static int launch_step(lbm_run *h, bool timed, bool wait_prev_diag = true, bool capturing = false) {
     StepBuffers b = buffers(h, h->parity);
     cudaError_t e;
+    cudaEvent_t eh = capturing ? h->cev_heat : h->ev_heat, ed = capturing ? h->cev_diag : h->ev_diag;
     for (int k = 0; k < 3; k++) {
+        cudaStream_t st = (k == 2) ? h->dstream : h->stream;
+        if (k == 1 && wait_prev_diag) CK(h, cudaStreamWaitEvent(h->stream, ed, 0));
+        if (k == 2) {
+            CK(h, cudaEventRecord(eh, h->stream));
+            CK(h, cudaStreamWaitEvent(h->dstream, eh, 0));
+        }
         EventPair ep;
         if (timed) {
             CK(h, cudaEventCreate(&ep.a));
             CK(h, cudaEventCreate(&ep.b));
-            CK(h, cudaEventRecord(ep.a, h->stream));
+            CK(h, cudaEventRecord(ep.a, st));
         }
         if ((e = launch_kernel(h, k, b)) != cudaSuccess) return cuda_fail(h, e, k == 0 ? "flow kernel" : (k == 1 ? "heat kernel" : "diagnostics kernel"));
         if (timed) {
-            CK(h, cudaEventRecord(ep.b, h->stream));
+            CK(h, cudaEventRecord(ep.b, st));
             h->ev[k].push_back(ep);
         }
+        if (k == 2) CK(h, cudaEventRecord(ed, h->dstream));
     }
     h->parity ^= 1;
     return LBM_OK;
 }
 
-static int build_graph(lbm_run *h) {
+static int build_graph(lbm_run *h, int nsteps, cudaGraphExec_t *out) {
     cudaGraph_t g = nullptr;
     CK(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
-    int rc = launch_step(h, false);
-    if (rc == LBM_OK) rc = launch_step(h, false);
+    int rc = LBM_OK;
+    for (int i = 0; i < nsteps && rc == LBM_OK; i++) rc = launch_step(h, false, i > 0, true);
+    cudaError_t ej = (rc == LBM_OK) ? join_diag(h, true) : cudaSuccess;
     cudaError_t e = cudaStreamEndCapture(h->stream, &g);
     if (rc != LBM_OK) { if (g) cudaGraphDestroy(g); return rc; }
+    if (ej != cudaSuccess) { if (g) cudaGraphDestroy(g); return cuda_fail(h, ej, "graph join"); }
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamEndCapture");
-    e = cudaGraphInstantiate(&h->graph, g, 0);
+    e = cudaGraphInstantiate(out, g, 0);
     cudaGraphDestroy(g);
-    if (e != cudaSuccess) { h->graph = nullptr; return cuda_fail(h, e, "cudaGraphInstantiate"); }
+    if (e != cudaSuccess) { *out = nullptr; return cuda_fail(h, e, "cudaGraphInstantiate"); }
     return LBM_OK;
 }
 
@@ -367,8 +423,17 @@ int lbm_step(lbm_handle h, int64_t n) {
     int rc;
     const bool graphs = h->use_graphs && !h->timing && h->stream != nullptr;
     while (n > 0) {
+        if (graphs && n >= 8 && h->parity == 0) {
+            if (!h->graph8 && (rc = build_graph(h, 8, &h->graph8)) != LBM_OK) return rc;
+            CK(h, join_diag(h));  // the graph's first heat kernel reads the step counter
+            CK(h, cudaGraphLaunch(h->graph8, h->stream));
+            n -= 8;
+            h->steps += 8;
+            continue;
+        }
         if (graphs && n >= 2 && h->parity == 0) {
-            if (!h->graph && (rc = build_graph(h)) != LBM_OK) return rc;
+            if (!h->graph && (rc = build_graph(h, 2, &h->graph)) != LBM_OK) return rc;
+            CK(h, join_diag(h));
             CK(h, cudaGraphLaunch(h->graph, h->stream));
             n -= 2;
             h->steps += 2;
@@ -378,12 +443,15 @@ int lbm_step(lbm_handle h, int64_t n) {
         n -= 1;
         h->steps += 1;
     }
+    // later work on the main stream sees this call's diagnostics
+    CK(h, join_diag(h));
     return LBM_OK;
 }
 
 int lbm_sync(lbm_handle h) {
     if (!h) return LBM_E_INVAL;
     CK(h, cudaSetDevice(h->device));
+    CK(h, cudaStreamSynchronize(h->dstream));
     CK(h, cudaStreamSynchronize(h->stream));
     return check_err_word(h);
 }
@@ -581,11 +649,11 @@ static int batch_build_graph(lbm_batch_s *b) {
     for (size_t i = 0; i < b->runs.size() && rc == LBM_OK; i++) {
         lbm_run *h = b->runs[i];
         if ((e = cudaStreamWaitEvent(h->stream, b->fork, 0)) != cudaSuccess) { rc = LBM_E_CUDA; break; }
-        if ((rc = launch_step(h, false)) != LBM_OK || (rc = launch_step(h, false)) != LBM_OK) {
+        if ((rc = launch_step(h, false, false, true)) != LBM_OK || (rc = launch_step(h, false, true, true)) != LBM_OK) {
             b->msg = h->msg;
             break;
         }
-        if ((e = cudaEventRecord(b->join[i], h->stream)) != cudaSuccess ||
+        if ((e = join_diag(h, true)) != cudaSuccess || (e = cudaEventRecord(b->join[i], h->stream)) != cudaSuccess ||
             (e = cudaStreamWaitEvent(b->stream, b->join[i], 0)) != cudaSuccess) { rc = LBM_E_CUDA; break; }
     }
     cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
@@ -747,6 +815,7 @@ int lbm_select_variants(lbm_handle h, int flow, int heat) {
     CK(h, cudaSetDevice(h->device));
     CK(h, cudaStreamSynchronize(h->stream));
     if (h->graph) { cudaGraphExecDestroy(h->graph); h->graph = nullptr; }
+    if (h->graph8) { cudaGraphExecDestroy(h->graph8); h->graph8 = nullptr; }
     h->fv = flow;
     h->hv = heat;
     h->version++;
