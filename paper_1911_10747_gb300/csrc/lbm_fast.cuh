@@ -1346,7 +1346,9 @@ k_heat_wide(const FParams p, int tiles_x, int ntiles, const typename P::tst *__r
     const long long n = *stepp;
     unsigned errbits = 0;
 
-    float Tn[CPT], Tc[CPT], acc[CPT], kk[CPT][8], ks[CPT], ax[CPT], ay[CPT], c1[CPT], c2[CPT];
+    // kk: link weights of conduction with the advection of Eq. 24 folded in
+    // (-u . grad T with the Eq. 27 gradient is linear in the neighbours' T)
+    float Tn[CPT], Tc[CPT], acc[CPT], kk[CPT][8], ks[CPT], c1[CPT], c2[CPT];
     int kd[CPT];
     float pT[CPT], pr[CPT], pux[CPT], puy[CPT];
     int pkd[CPT], prow[CPT], px[CPT];  // kind, row and column of the prefetched cells
@@ -1418,7 +1420,7 @@ k_heat_wide(const FParams p, int tiles_x, int ntiles, const typename P::tst *__r
             const int hy = ty + c * BY;
             #pragma unroll
             for (int a = 0; a < 8; a++) kk[c][a] = 0.0f;
-            ks[c] = 0.0f; ax[c] = 0.0f; ay[c] = 0.0f; c1[c] = 0.0f; c2[c] = 0.0f; acc[c] = 0.0f;
+            ks[c] = 0.0f; c1[c] = 0.0f; c2[c] = 0.0f; acc[c] = 0.0f;
             const bool inner = hy >= 1 && hy < SH - 1 && tx >= 1 && tx < BW - 1;
             if (inner && (kd[c] == 1 || kd[c] == 2)) {
                 const float r0l = sLam[hy][tx];
@@ -1433,8 +1435,16 @@ k_heat_wide(const FParams p, int tiles_x, int ntiles, const typename P::tst *__r
                     ks[c] += kk[c][a];
                 }
                 if (kd[c] == 2) {
-                    ax[c] = -3.0f * sUx[hy][tx];
-                    ay[c] = -3.0f * sUy[hy][tx];
+                    // -u . grad T = sum_a adv_a T_a with adv_a = -3 w_a (e_a . u)
+                    const float vx = -3.0f * sUx[hy][tx], vy = -3.0f * sUy[hy][tx];
+                    kk[c][0] += w1 * vx;          // e = ( 1,  0)
+                    kk[c][1] += w1 * vy;          // e = ( 0,  1)
+                    kk[c][2] -= w1 * vx;          // e = (-1,  0)
+                    kk[c][3] -= w1 * vy;          // e = ( 0, -1)
+                    kk[c][4] += w2 * (vx + vy);   // e = ( 1,  1)
+                    kk[c][5] += w2 * (vy - vx);   // e = (-1,  1)
+                    kk[c][6] -= w2 * (vx + vy);   // e = (-1, -1)
+                    kk[c][7] += w2 * (vx - vy);   // e = ( 1, -1)
                     const float dx = w1 * (sUx[hy][tx + 1] - sUx[hy][tx - 1]) +
                                      w2 * ((sUx[hy + 1][tx + 1] - sUx[hy - 1][tx - 1]) + (sUx[hy - 1][tx + 1] - sUx[hy + 1][tx - 1]));
                     const float dy = w1 * (sUy[hy + 1][tx] - sUy[hy - 1][tx]) +
@@ -1472,11 +1482,8 @@ k_heat_wide(const FParams p, int tiles_x, int ntiles, const typename P::tst *__r
                     float h = kk[c][0] * T1 + kk[c][1] * Tu + kk[c][2] * T3 + kk[c][3] * Td + kk[c][4] * T5 +
                               kk[c][5] * T6 + kk[c][6] * T7 + kk[c][7] * T8 - ks[c] * T0;
                     if (kd[c] == 2) {
-                        const float a = T5 - T7, b = T8 - T6;
-                        const float gx = w1 * (T1 - T3) + w2 * (a + b);
-                        const float gy = w1 * (Tu - Td) + w2 * (a - b);
                         const float Ta = fmaxf(T0 + p.T_sat, 1e-30f);
-                        h += ax[c] * gx + ay[c] * gy + c1[c] * Ta + c2[c] * fast_sqrt(Ta);
+                        h += c1[c] * Ta + c2[c] * fast_sqrt(Ta);
                     }
                     float Tnext;
                     if (st == 0) { acc[c] = h; Tnext = Tn[c] + 0.5f * h; }
