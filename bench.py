@@ -383,7 +383,13 @@ def run_ours(args):
 
     # launch-shape autotuning (does not advance the run), then warm-up (also
     # builds the two-step graph)
-    tuned_ms = run.autotune(5)
+    variants = run.variants()
+    if args.flow_variant or args.heat_variant:
+        fv = variants["flow"].index(args.flow_variant) if args.flow_variant else variants["selected"][0]
+        hv = variants["heat"].index(args.heat_variant) if args.heat_variant else variants["selected"][1]
+        run.select_variants(fv, hv)
+    else:
+        run.autotune(5)
     variants = run.variants()
     run.step(max(args.warmup, 3))
     run.sync()
@@ -533,6 +539,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--sweep-steps", type=int, default=200)
+    ap.add_argument("--flow-variant", default="", help="pin the flow kernel variant (no autotuning)")
+    ap.add_argument("--heat-variant", default="", help="pin the heat kernel variant (no autotuning)")
     ap.add_argument("--chf", action="store_true", help="also measure the FP32 vs FP64 boiling curve")
     ap.add_argument("--chf-steps", type=int, default=20000)
     ap.add_argument("--serve", action="store_true", help="also measure the request loop")

@@ -356,7 +356,9 @@ int lbm_destroy(lbm_handle h) {
 static cudaError_t launch_kernel(lbm_run *h, int k, const StepBuffers &b) {
     if (k == 0) return h->ks->flow[h->fv].launch(h->p, b, h->stream);
     if (k == 1) return h->ks->heat[h->hv].launch(h->p, b, h->stream);
-    return h->ks->diag(h->p, b, h->nblk, h->dstream);
+    // per-kernel timing runs the diagnostics on the main stream, so its events
+    // time the kernel itself rather than its wait behind an overlapping kernel
+    return h->ks->diag(h->p, b, h->nblk, h->timing ? h->stream : h->dstream);
 }
 
 // Make the main stream wait for the last queued diagnostics kernel.  Events
@@ -377,9 +379,9 @@ static int launch_step(lbm_run *h, bool timed, bool wait_prev_diag = true, bool 
     cudaError_t e;
     cudaEvent_t eh = capturing ? h->cev_heat : h->ev_heat, ed = capturing ? h->cev_diag : h->ev_diag;
     for (int k = 0; k < 3; k++) {
-        cudaStream_t st = (k == 2) ? h->dstream : h->stream;
+        cudaStream_t st = (k == 2 && !h->timing) ? h->dstream : h->stream;
         if (k == 1 && wait_prev_diag) CK(h, cudaStreamWaitEvent(h->stream, ed, 0));
-        if (k == 2) {
+        if (k == 2 && !h->timing) {
             CK(h, cudaEventRecord(eh, h->stream));
             CK(h, cudaStreamWaitEvent(h->dstream, eh, 0));
         }
@@ -394,7 +396,7 @@ static int launch_step(lbm_run *h, bool timed, bool wait_prev_diag = true, bool 
             CK(h, cudaEventRecord(ep.b, st));
             h->ev[k].push_back(ep);
         }
-        if (k == 2) CK(h, cudaEventRecord(ed, h->dstream));
+        if (k == 2) CK(h, cudaEventRecord(ed, st));
     }
     h->parity ^= 1;
     return LBM_OK;
