@@ -26,7 +26,7 @@ struct FParams {
     unsigned long long seed;
     long long sine_t0, sine_t1;
     float rho_shift, T_sat, inv_Tc, kappa, a, b, R, two_over_G, mG;
-    float tau_V, rho_V, inv_drho, dtau, rho_mean, g, varpi12, inv_tauem, sgn_over_taus;
+    float tau_V, rho_V, inv_drho, dtau, rho_mean, g, varpi12G2, inv_tauem, sgn_over_taus;
     float s[9], hs[9];
     float c_w_top, vap_threshold;
     float lambda_s, cv_chi, c_v, rho_c_s;
@@ -44,7 +44,8 @@ inline FParams make_fparams(const DevParams &p) {
     q.two_over_G = (float)(2.0 / p.G); q.mG = (float)(-p.G);
     q.tau_V = (float)p.tau_V; q.rho_V = (float)p.rho_V; q.inv_drho = (float)(1.0 / p.drho_LV);
     q.dtau = (float)p.dtau_LV; q.rho_mean = (float)p.rho_mean; q.g = (float)p.g;
-    q.varpi12 = (float)p.varpi12; q.inv_tauem = (float)(1.0 / p.tau_e_m);
+    // |F_m|^2 / psi^2 = G^2 |stencil|^2 (Eq. 10), so eta needs no division by psi^2
+    q.varpi12G2 = (float)(p.varpi12 * p.G * p.G); q.inv_tauem = (float)(1.0 / p.tau_e_m);
     q.sgn_over_taus = (float)(p.sign_eps / p.tau_s_m);
     for (int k = 0; k < 9; k++) { q.s[k] = (float)p.s[k]; q.hs[k] = (float)p.hs[k]; }
     q.c_w_top = (float)p.c_w_top; q.vap_threshold = (float)p.vap_threshold;
@@ -85,10 +86,10 @@ __device__ __forceinline__ float psi_fast(const FParams &q, float rho, float T, 
     const float t2 = 1.0f + q.kappa * (1.0f - t1);
     const float phi = t2 * t2;
     const float br = q.b * rho;
-    const float p1 = rho * q.R * T * fast_rcp(1.0f - br);
-    const float den = 1.0f + br * (2.0f - br);
-    const float p2 = q.a * phi * rho * rho * fast_rcp(den);
-    const float arg = q.two_over_G * ((p1 - p2) - rho * (1.0f / 3.0f));
+    const float omb = 1.0f - br, den = 1.0f + br * (2.0f - br);
+    // p = rho R T / (1 - b rho) - a phi rho^2 / den over one common denominator
+    const float p = rho * ((q.R * T) * den - (q.a * phi) * rho * omb) * fast_rcp(omb * den);
+    const float arg = q.two_over_G * (p - rho * (1.0f / 3.0f));
     if (!(arg > 0.0f)) {
         if (!(arg == 0.0f)) errbits |= ERRW_PSI;
         return 0.0f;
@@ -212,8 +213,8 @@ k_flow_fast(const FParams p, const typename P::fst *__restrict__ fin, typename P
         if (top && outflow) { pNx = psi; pNE = pE; pNW = pW; }  // open top: zero normal gradient
         const float a = pNE - pSW, b = pSE - pNW;
         const float pre = mG * psi;
-        const float Fmx = pre * (w1 * (pE - pW) + w2 * (a + b));
-        const float Fmy = pre * (w1 * (pNx - pS) + w2 * (a - b));
+        const float sx = w1 * (pE - pW) + w2 * (a + b), sy = w1 * (pNx - pS) + w2 * (a - b);
+        const float Fmx = pre * sx, Fmy = pre * sy;
         const int xm = wrap1(x - 1, nx), xp = wrap1(x + 1, nx);
         float Fax = 0.0f, Fay = 0.0f;
         if (bot) {  // Eq. 14 with the heater sites below (i = 4, 7, 8)
@@ -248,7 +249,7 @@ k_flow_fast(const FParams p, const typename P::fst *__restrict__ fin, typename P
         const float q3 = rho * ux, q5 = rho * uy;
         const float q7 = rho * (ux * ux - uy * uy), q8 = rho * (ux * uy);
         const float uF = ux * Fx + uy * Fy;
-        const float eps = (psi > 0.0f) ? p.varpi12 * (Fmx * Fmx + Fmy * Fmy) * fast_rcp(psi * psi) : 0.0f;
+        const float eps = (psi > 0.0f) ? p.varpi12G2 * (sx * sx + sy * sy) : 0.0f;
         const float S1 = 6.0f * uF + eps * p.inv_tauem;
         const float S2 = -6.0f * uF + eps * p.sgn_over_taus;
         // Eq. 7 (m0 unchanged; q4 = -q3, q6 = -q5)
@@ -343,6 +344,13 @@ k_flow_pers(const FParams p, int tiles_x, int ntiles, const typename P::fst *__r
 
     const int nx = p.nx, nf = p.nf;
     const size_t plane = (size_t)nf * nx;
+    // per-plane base pointers (uniform); site offsets below are 32-bit (the
+    // runtime rejects domains of more than 2e9 sites, so one plane indexes in 31 bits)
+    const S *fplane[9];
+    S *oplane[9];
+    #pragma unroll
+    for (int i = 0; i < 9; i++) { fplane[i] = fin + i * plane; oplane[i] = fout + i * plane; }
+    const typename P::tst *Tfl = Tin + (size_t)p.ns * nx;  // first fluid row of T
     const bool py = (p.flags & FLAG_PERIODIC_Y) != 0;
     const bool frozen = (p.flags & FLAG_FROZEN_FLOW) != 0;
     const bool outflow = p.top_mode == TOP_OUTFLOW;
@@ -368,6 +376,7 @@ k_flow_pers(const FParams p, int tiles_x, int ntiles, const typename P::fst *__r
     static_assert(RING <= NT, "one ring site per thread");
     float rg[9], rT = 0.0f;
     bool rvalid = false;
+    int rslot = 0;  // shared-memory slot of this thread's ring site (set by fetch)
     auto ring_site = [&](int k, int x0, int y0, int &hx, int &hy, int &x, int &y) {
         if (k < SW) { hx = k; hy = 0; }
         else if (k < 2 * SW) { hx = k - SW; hy = SH - 1; }
@@ -383,11 +392,12 @@ k_flow_pers(const FParams p, int tiles_x, int ntiles, const typename P::fst *__r
         if (tid < RING && !frozen) {
             int hx, hy, x, y;
             rvalid = ring_site(tid, x0, y0, hx, hy, x, y);
+            rslot = hy * SW + hx;
             if (rvalid) {
-                const size_t kk = (size_t)y * nx + x;
+                const int kk = y * nx + x;
                 #pragma unroll
-                for (int i = 0; i < 9; i++) rg[i] = ld_as<float>(fin + i * plane + kk);
-                rT = ld_as<float>(Tin + (size_t)(p.ns + y) * nx + x);
+                for (int i = 0; i < 9; i++) rg[i] = ld_as<float>(fplane[i] + kk);
+                rT = ld_as<float>(Tfl + kk);
             }
         }
         #pragma unroll
@@ -398,10 +408,10 @@ k_flow_pers(const FParams p, int tiles_x, int ntiles, const typename P::fst *__r
             const bool has = py || y < nf;
             if (py) y = wy(y);
             if (has) {
-                const size_t k = (size_t)y * nx + x;
+                const int k = y * nx + x;
                 #pragma unroll
-                for (int i = 0; i < 9; i++) pg[r][i] = ld_as<float>(fin + i * plane + k);
-                pTv[r] = ld_as<float>(Tin + (size_t)(p.ns + y) * nx + x);
+                for (int i = 0; i < 9; i++) pg[r][i] = ld_as<float>(fplane[i] + k);
+                pTv[r] = ld_as<float>(Tfl + k);
             } else {
                 #pragma unroll
                 for (int i = 0; i < 9; i++) pg[r][i] = 0.0f;
@@ -440,14 +450,12 @@ k_flow_pers(const FParams p, int tiles_x, int ntiles, const typename P::fst *__r
     }
     // ---- halo ring, from the prefetched registers ----
     if (!frozen && tid < RING) {
-        int hx, hy, x, y;
-        ring_site(tid, x0, y0, hx, hy, x, y);
         float psi = 0.0f;
         if (rvalid) {
             const float d = ((rg[0] + rg[1]) + (rg[2] + rg[3])) + ((rg[4] + rg[5]) + (rg[6] + rg[7])) + rg[8];
             psi = psi_fast(p, d + rho0, rT + tsat, errbits);
         }
-        s_psi[hy * SW + hx] = psi;
+        s_psi[rslot] = psi;
     }
     // the next tile's loads (own sites and ring) fly during this tile's collisions
     if (tile + (int)gridDim.x < ntiles) fetch(nxt, nyt);
@@ -462,7 +470,7 @@ k_flow_pers(const FParams p, int tiles_x, int ntiles, const typename P::fst *__r
         const int lx = threadIdx.x, ly = threadIdx.y + r * BY;
         const int x = x0 + lx, y = y0 + ly;
         if (x >= nx || y >= nf) continue;
-        const size_t k = (size_t)y * nx + x;
+        const int k = y * nx + x;
         const float d = dd[r];
         const float rho = d + rho0;
         if (!(fabsf(rho) < 1e30f)) errbits |= ERRW_NONFINITE_RHO;
@@ -470,7 +478,7 @@ k_flow_pers(const FParams p, int tiles_x, int ntiles, const typename P::fst *__r
         nvap += (rho < p.vap_threshold) ? 1.0f : 0.0f;
         if (frozen) {
             #pragma unroll
-            for (int i = 0; i < 9; i++) st_as(fout + i * plane + k, g[r][i]);
+            for (int i = 0; i < 9; i++) st_as(oplane[i] + k, g[r][i]);
             rho_o[k] = rho;
             ux_o[k] = 0.0f;
             uy_o[k] = 0.0f;
@@ -486,8 +494,8 @@ k_flow_pers(const FParams p, int tiles_x, int ntiles, const typename P::fst *__r
         if (top && outflow) { pNx = psi; pNE = pE; pNW = pW; }  // open top: zero normal gradient
         const float a = pNE - pSW, b = pSE - pNW;
         const float pre = mG * psi;
-        const float Fmx = pre * (w1 * (pE - pW) + w2 * (a + b));
-        const float Fmy = pre * (w1 * (pNx - pS) + w2 * (a - b));
+        const float sx = w1 * (pE - pW) + w2 * (a + b), sy = w1 * (pNx - pS) + w2 * (a - b);
+        const float Fmx = pre * sx, Fmy = pre * sy;
         const int xm = wrap1(x - 1, nx), xp = wrap1(x + 1, nx);
         float Fax = 0.0f, Fay = 0.0f;
         if (bot) {  // Eq. 14 with the heater sites below (i = 4, 7, 8)
@@ -522,7 +530,7 @@ k_flow_pers(const FParams p, int tiles_x, int ntiles, const typename P::fst *__r
         const float q3 = rho * ux, q5 = rho * uy;
         const float q7 = rho * (ux * ux - uy * uy), q8 = rho * (ux * uy);
         const float uF = ux * Fx + uy * Fy;
-        const float eps = (psi > 0.0f) ? p.varpi12 * (Fmx * Fmx + Fmy * Fmy) * fast_rcp(psi * psi) : 0.0f;
+        const float eps = (psi > 0.0f) ? p.varpi12G2 * (sx * sx + sy * sy) : 0.0f;
         const float S1 = 6.0f * uF + eps * p.inv_tauem;
         const float S2 = -6.0f * uF + eps * p.sgn_over_taus;
         // Eq. 7 (m0 unchanged; q4 = -q3, q6 = -q5)
@@ -554,35 +562,35 @@ k_flow_pers(const FParams p, int tiles_x, int ntiles, const typename P::fst *__r
         ux_o[k] = ux;
         uy_o[k] = uy;
         // Eq. 8, push; halfway bounce-back at the heater and the top wall
-        S *o = fout;
-        const size_t ro = (size_t)y * nx;
-        st_as(o + ro + x, fo0);
-        st_as(o + plane + ro + xp, fo1);
-        st_as(o + 3 * plane + ro + xm, fo3);
-        const size_t ru = (size_t)(py && y == nf - 1 ? 0 : y + 1) * nx;
-        const size_t rd = (size_t)(py && y == 0 ? nf - 1 : y - 1) * nx;
+        // (32-bit offsets from this site: east / west columns, rows above / below)
+        const int dxp = xp - x, dxm = xm - x;
+        const int kn = (py && y == nf - 1) ? x : k + nx;      // row above
+        const int ks_ = (py && y == 0) ? (nf - 1) * nx + x : k - nx;  // row below
+        st_as(oplane[0] + k, fo0);
+        st_as(oplane[1] + k + dxp, fo1);
+        st_as(oplane[3] + k + dxm, fo3);
         if (!top) {
-            st_as(o + 2 * plane + ru + x, fo2);
-            st_as(o + 5 * plane + ru + xp, fo5);
-            st_as(o + 6 * plane + ru + xm, fo6);
+            st_as(oplane[2] + kn, fo2);
+            st_as(oplane[5] + kn + dxp, fo5);
+            st_as(oplane[6] + kn + dxm, fo6);
         } else if (!outflow) {
-            st_as(o + 4 * plane + ro + x, fo2);
-            st_as(o + 7 * plane + ro + x, fo5);
-            st_as(o + 8 * plane + ro + x, fo6);
+            st_as(oplane[4] + k, fo2);
+            st_as(oplane[7] + k, fo5);
+            st_as(oplane[8] + k, fo6);
         }
         if (!bot) {
-            st_as(o + 4 * plane + rd + x, fo4);
-            st_as(o + 7 * plane + rd + xm, fo7);
-            st_as(o + 8 * plane + rd + xp, fo8);
+            st_as(oplane[4] + ks_, fo4);
+            st_as(oplane[7] + ks_ + dxm, fo7);
+            st_as(oplane[8] + ks_ + dxp, fo8);
         } else {
-            st_as(o + 2 * plane + ro + x, fo4);
-            st_as(o + 5 * plane + ro + x, fo7);
-            st_as(o + 6 * plane + ro + x, fo8);
+            st_as(oplane[2] + k, fo4);
+            st_as(oplane[5] + k, fo7);
+            st_as(oplane[6] + k, fo8);
         }
         if (top && outflow) {
-            st_as(o + 4 * plane + ro + x, fo4);
-            st_as(o + 7 * plane + ro + xm, fo7);
-            st_as(o + 8 * plane + ro + xp, fo8);
+            st_as(oplane[4] + k, fo4);
+            st_as(oplane[7] + k + dxm, fo7);
+            st_as(oplane[8] + k + dxp, fo8);
         }
     }
     __syncthreads();  // s_psi is rewritten by the next tile
