@@ -815,52 +815,6 @@ k_heat_fast(const FParams p, const typename P::tst *__restrict__ Tin, typename P
     if (errbits) atomicOr(err, errbits);
 }
 
-// ---- diagnostics for the FP32 path: per-column flux in FP32, FP64 sums ----
-template <class P, int NT>
-__global__ void __launch_bounds__(NT)
-k_diag_fast(const FParams p, const float *__restrict__ T, const float *__restrict__ rho,
-            const double *__restrict__ part, int nblk, double *__restrict__ q_top, double *__restrict__ series,
-            int cap, double *__restrict__ last, long long *__restrict__ stepp) {
-    __shared__ double sh[2][NT / 32];
-    const int nx = p.nx, ns = p.ns;
-    const bool py = (p.flags & FLAG_PERIODIC_Y) != 0;
-    double mass = 0.0, nvap = 0.0;
-    for (int b = threadIdx.x; b < nblk; b += NT) {
-        mass += part[2 * b];
-        nvap += part[2 * b + 1];
-    }
-    block_sum2<NT>(mass, nvap, sh);
-    __syncthreads();
-    double qb = 0.0, qt = 0.0;
-    const float lams = p.lambda_s, cvchi = p.cv_chi;
-    if (!py && ns >= 3) {
-        for (int x = threadIdx.x; x < nx; x += NT) {
-            // theta differences: T_sat cancels in the gradients
-            const float t0 = T[x], t1 = T[nx + x], t2 = T[2 * nx + x];
-            qb += (double)(-lams * (0.5f * ((4.0f * t1 - t2) - 3.0f * t0)));
-            const float lf1 = cvchi * rho[x];
-            const float lf = 2.0f * lams * lf1 * fast_rcp(lams + lf1);
-            const float q = -lf * (T[(size_t)ns * nx + x] - T[(size_t)(ns - 1) * nx + x]);
-            q_top[x] = (double)q;
-            qt += (double)q;
-        }
-    }
-    block_sum2<NT>(qb, qt, sh);
-    if (threadIdx.x == 0) {
-        const long long n = *stepp;
-        const double nfl = (double)nx * (double)p.nf;
-        double v[SERIES_WIDTH] = {qb / (double)nx, qt / (double)nx, nvap / nfl, mass};
-        if (py || ns < 3) { v[0] = 0.0; v[1] = 0.0; }
-        const long long slot = n % cap;
-        #pragma unroll
-        for (int k = 0; k < SERIES_WIDTH; k++) {
-            series[slot * SERIES_WIDTH + k] = v[k];
-            last[k] = v[k];
-        }
-        *stepp = n + 1;
-    }
-}
-
 template <class P, int BX, int BY, int RY, int MINB>
 struct FlowFastShape {
     static cudaError_t prepare() { return cudaSuccess; }
@@ -916,413 +870,6 @@ struct HeatFastShape {
     }
 };
 
-template <class P, int NT>
-cudaError_t launch_diag_fast(const DevParams &p, const StepBuffers &b, int nblk, cudaStream_t s) {
-    k_diag_fast<P, NT><<<1, NT, 0, s>>>(make_fparams(p), (const float *)b.T_out, (const float *)b.rho, b.part, nblk, b.q_top,
-                                        b.series, b.series_cap, b.last, b.step);
-    return cudaGetLastError();
-}
-
-}  // namespace lbmgb
-
-namespace lbmgb {
-
-// ============================================================================
-// Heat kernel, FP32, register-resident variant.  A block covers 32 columns x
-// SH = NWARP * CPT rows of cells (4-cell halo on every side, so 24 x (SH - 8)
-// outputs).  Lane = column, warp w owns rows w, w + NWARP, ...  Each thread
-// keeps its cells' per-step coefficients (8 link weights and their sum,
-// -3u, C1, C2), T^n and the RK accumulator in registers for all four
-// stages; a stage exchanges only the stage temperature: the row above and
-// below through shared memory, the left and right columns by warp shuffle.
-// Same arithmetic as k_heat_fast.
-// ============================================================================
-template <class P, int NWARP, int CPT>
-__global__ void __launch_bounds__(NWARP * 32, (NWARP * 32 <= 512) ? 2 : 1)
-k_heat_reg(const FParams p, const typename P::tst *__restrict__ Tin, typename P::tst *__restrict__ Tout,
-           const float *__restrict__ rho_i, const float *__restrict__ ux_i, const float *__restrict__ uy_i,
-           const long long *__restrict__ stepp, unsigned *__restrict__ err) {
-    constexpr int H = 4, SH = NWARP * CPT, TXO = 32 - 2 * H, TYO = SH - 2 * H;
-    __shared__ float sT[2][SH][32];
-    __shared__ float sLam[SH][32], sUx[SH][32], sUy[SH][32];
-    const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5;
-    const int nx = p.nx, nt = p.nt, ns = p.ns, nf = p.nf;
-    const bool py = (p.flags & FLAG_PERIODIC_Y) != 0;
-    const bool iso = (p.flags & FLAG_ISOTHERMAL) != 0;
-    const int x0 = blockIdx.x * TXO, r0 = blockIdx.y * TYO;
-    const int x = wrapi(x0 + lane - H, nx);
-    const long long n = *stepp;
-    unsigned errbits = 0;
-
-    float Tn[CPT], acc[CPT], kk[CPT][8], ks[CPT], ax[CPT], ay[CPT], c1[CPT], c2[CPT], rcv[CPT], rho[CPT];
-    int kd[CPT];  // 0 outside, 1 solid, 2 fluid, 3 fixed (bottom Dirichlet row / top ghost)
-
-    // ---- load ----
-    #pragma unroll
-    for (int c = 0; c < CPT; c++) {
-        const int hy = wy + c * NWARP;
-        int row = r0 + hy - H;
-        int k;
-        if (py) { row = wrapi(row, nt); k = 2; }
-        else if (row < 0 || row > nt) k = 0;
-        else if (row == 0 || row == nt) k = 3;
-        else k = (row < ns) ? 1 : 2;
-        float T = 0.0f, lam = 0.0f, ux = 0.0f, uy = 0.0f, rc = 1.0f, r = 0.0f;
-        if (k == 1) {
-            T = Tin[(size_t)row * nx + x];
-            lam = p.lambda_s;
-            rc = p.rho_c_s;
-        } else if (k == 2) {
-            const size_t kf = (size_t)(row - ns) * nx + x;
-            T = Tin[(size_t)row * nx + x];
-            r = rho_i[kf];
-            ux = ux_i[kf];
-            uy = uy_i[kf];
-            lam = p.cv_chi * r;
-            rc = r * p.c_v;
-        } else if (k == 3) {
-            if (row == 0) {
-                T = bottom_theta(p, x, n);
-                lam = p.lambda_s;
-            } else {
-                lam = p.cv_chi * rho_i[(size_t)(nf - 1) * nx + x];
-            }
-        }
-        kd[c] = k;
-        Tn[c] = T;
-        rcv[c] = rc;
-        rho[c] = r;
-        sT[0][hy][lane] = T;
-        sT[1][hy][lane] = T;
-        sLam[hy][lane] = lam;
-        sUx[hy][lane] = ux;
-        sUy[hy][lane] = uy;
-    }
-    __syncthreads();
-    // ---- per-step coefficients ----
-    const float w1 = 1.0f / 9.0f, w2 = 1.0f / 36.0f;
-    #pragma unroll
-    for (int c = 0; c < CPT; c++) {
-        const int hy = wy + c * NWARP;
-        #pragma unroll
-        for (int a = 0; a < 8; a++) kk[c][a] = 0.0f;
-        ks[c] = 0.0f; ax[c] = 0.0f; ay[c] = 0.0f; c1[c] = 0.0f; c2[c] = 0.0f;
-        acc[c] = 0.0f;
-        const bool inner = hy >= 1 && hy < SH - 1 && lane >= 1 && lane < 31;
-        if (inner && (kd[c] == 1 || kd[c] == 2)) {
-            const float l0 = sLam[hy][lane];
-            const float inv6 = 6.0f * fast_rcp(rcv[c]);
-            const float la[8] = {sLam[hy][lane + 1], sLam[hy + 1][lane], sLam[hy][lane - 1], sLam[hy - 1][lane],
-                                 sLam[hy + 1][lane + 1], sLam[hy + 1][lane - 1], sLam[hy - 1][lane - 1],
-                                 sLam[hy - 1][lane + 1]};
-            #pragma unroll
-            for (int a = 0; a < 8; a++) {
-                const float hm = 2.0f * l0 * la[a] * fast_rcp(l0 + la[a]);
-                kk[c][a] = (a < 4 ? w1 : w2) * hm * inv6;
-                ks[c] += kk[c][a];
-            }
-            if (kd[c] == 2) {
-                ax[c] = -3.0f * sUx[hy][lane];
-                ay[c] = -3.0f * sUy[hy][lane];
-                const float dx = w1 * (sUx[hy][lane + 1] - sUx[hy][lane - 1]) +
-                                 w2 * ((sUx[hy + 1][lane + 1] - sUx[hy - 1][lane - 1]) +
-                                       (sUx[hy - 1][lane + 1] - sUx[hy + 1][lane - 1]));
-                const float dy = w1 * (sUy[hy + 1][lane] - sUy[hy - 1][lane]) +
-                                 w2 * ((sUy[hy + 1][lane + 1] - sUy[hy - 1][lane - 1]) -
-                                       (sUy[hy - 1][lane + 1] - sUy[hy + 1][lane - 1]));
-                const float divu = 3.0f * (dx + dy);
-                const float br = p.b * rho[c];
-                const float iden = fast_rcp(1.0f + br * (2.0f - br));
-                const float pa = p.a_kappa * rho[c] * rho[c] * iden;
-                const float A = rho[c] * p.R * fast_rcp(1.0f - br) - pa * p.kappa_over_Tc;
-                const float B = pa * p.B_coef;
-                const float g0 = -divu * fast_rcp(rcv[c]);
-                c1[c] = g0 * A;
-                c2[c] = g0 * B;
-            }
-        }
-    }
-    // ---- four RK stages ----
-    if (!iso) {
-        #pragma unroll
-        for (int st = 0; st < 4; st++) {
-            const int m = st + 1;
-            const int rb = st & 1, wb = rb ^ 1;
-            #pragma unroll
-            for (int c = 0; c < CPT; c++) {
-                const int hy = wy + c * NWARP;
-                const float T0 = sT[rb][hy][lane];
-                const float Tu = (hy + 1 < SH) ? sT[rb][hy + 1][lane] : 0.0f;
-                const float Td = (hy >= 1) ? sT[rb][hy - 1][lane] : 0.0f;
-                const float T1 = __shfl_down_sync(0xffffffffu, T0, 1);
-                const float T3 = __shfl_up_sync(0xffffffffu, T0, 1);
-                const float T5 = __shfl_down_sync(0xffffffffu, Tu, 1);
-                const float T6 = __shfl_up_sync(0xffffffffu, Tu, 1);
-                const float T8 = __shfl_down_sync(0xffffffffu, Td, 1);
-                const float T7 = __shfl_up_sync(0xffffffffu, Td, 1);
-                const bool act = hy >= m && hy < SH - m && lane >= m && lane < 32 - m && (kd[c] == 1 || kd[c] == 2);
-                if (act) {
-                    float h = kk[c][0] * T1 + kk[c][1] * Tu + kk[c][2] * T3 + kk[c][3] * Td + kk[c][4] * T5 +
-                              kk[c][5] * T6 + kk[c][6] * T7 + kk[c][7] * T8 - ks[c] * T0;
-                    if (kd[c] == 2) {
-                        const float a = T5 - T7, b = T8 - T6;
-                        const float gx = w1 * (T1 - T3) + w2 * (a + b);
-                        const float gy = w1 * (Tu - Td) + w2 * (a - b);
-                        const float Ta = fmaxf(T0 + p.T_sat, 1e-30f);
-                        h += ax[c] * gx + ay[c] * gy + c1[c] * Ta + c2[c] * fast_sqrt(Ta);
-                    }
-                    if (st == 0) { acc[c] = h; sT[wb][hy][lane] = Tn[c] + 0.5f * h; }
-                    else if (st == 1) { acc[c] += 2.0f * h; sT[wb][hy][lane] = Tn[c] + 0.5f * h; }
-                    else if (st == 2) { acc[c] += 2.0f * h; sT[wb][hy][lane] = Tn[c] + h; }
-                    else { acc[c] += h; }
-                }
-            }
-            __syncthreads();
-        }
-    }
-    // ---- write the tile ----
-    #pragma unroll
-    for (int c = 0; c < CPT; c++) {
-        const int hy = wy + c * NWARP;
-        const int row = r0 + hy - H, xo = x0 + lane - H;
-        if (lane >= H && lane < 32 - H && hy >= H && hy < SH - H && row < nt && xo < nx) {
-            float v = Tn[c];
-            if ((kd[c] == 1 || kd[c] == 2) && !iso) v = Tn[c] + acc[c] * (1.0f / 6.0f);
-            if (!(fabsf(v) < 1e30f)) errbits |= ERRW_NONFINITE_T;
-            Tout[(size_t)row * nx + xo] = v;
-        }
-    }
-    if (errbits) atomicOr(err, errbits);
-}
-
-template <class P, int NWARP, int CPT>
-__global__ void __launch_bounds__(NWARP * 32, (NWARP * 32 <= 512) ? 2 : 1)
-k_heat_pers(const FParams p, int tiles_x, int ntiles, const typename P::tst *__restrict__ Tin, typename P::tst *__restrict__ Tout,
-           const float *__restrict__ rho_i, const float *__restrict__ ux_i, const float *__restrict__ uy_i,
-           const long long *__restrict__ stepp, unsigned *__restrict__ err) {
-    constexpr int H = 4, SH = NWARP * CPT, TXO = 32 - 2 * H, TYO = SH - 2 * H;
-    __shared__ float sT[2][SH][32];
-    __shared__ float sLam[SH][32], sUx[SH][32], sUy[SH][32];
-    const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5;
-    const int nx = p.nx, nt = p.nt, ns = p.ns, nf = p.nf;
-    const bool py = (p.flags & FLAG_PERIODIC_Y) != 0;
-    const bool iso = (p.flags & FLAG_ISOTHERMAL) != 0;
-    const long long n = *stepp;
-    unsigned errbits = 0;
-
-    float Tn[CPT], acc[CPT], kk[CPT][8], ks[CPT], ax[CPT], ay[CPT], c1[CPT], c2[CPT], rcv[CPT], rho[CPT];
-    int kd[CPT];  // 0 outside, 1 solid, 2 fluid, 3 fixed (bottom Dirichlet row / top ghost)
-    // raw inputs of the next tile, loaded while the current one is computed
-    float pT[CPT], pr[CPT], pux[CPT], puy[CPT];
-
-    auto classify = [&](int tile, int c, int &row, int &x) {
-        const int x0 = (tile % tiles_x) * TXO, r0 = (tile / tiles_x) * TYO;
-        const int hy = wy + c * NWARP;
-        x = wrapi(x0 + lane - H, nx);
-        row = r0 + hy - H;
-        int k;
-        if (py) { row = wrapi(row, nt); k = 2; }
-        else if (row < 0 || row > nt) k = 0;
-        else if (row == 0 || row == nt) k = 3;
-        else k = (row < ns) ? 1 : 2;
-        return k;
-    };
-    auto fetch = [&](int tile) {
-        #pragma unroll
-        for (int c = 0; c < CPT; c++) {
-            int row, x;
-            const int k = classify(tile, c, row, x);
-            pT[c] = 0.0f; pr[c] = 0.0f; pux[c] = 0.0f; puy[c] = 0.0f;
-            if (k == 1 || k == 2) pT[c] = Tin[(size_t)row * nx + x];
-            if (k == 2) {
-                const size_t kf = (size_t)(row - ns) * nx + x;
-                pr[c] = rho_i[kf]; pux[c] = ux_i[kf]; puy[c] = uy_i[kf];
-            } else if (k == 3 && row == nt) {
-                pr[c] = rho_i[(size_t)(nf - 1) * nx + x];
-            }
-        }
-    };
-    if (blockIdx.x < ntiles) fetch(blockIdx.x);
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int x0 = (tile % tiles_x) * TXO, r0 = (tile / tiles_x) * TYO;
-    const int x = wrapi(x0 + lane - H, nx);
-
-    // ---- load (from the prefetched registers) ----
-    #pragma unroll
-    for (int c = 0; c < CPT; c++) {
-        const int hy = wy + c * NWARP;
-        int row, xx;
-        const int k = classify(tile, c, row, xx);
-        float T = 0.0f, lam = 0.0f, ux = 0.0f, uy = 0.0f, rc = 1.0f, r = 0.0f;
-        if (k == 1) {
-            T = pT[c];
-            lam = p.lambda_s;
-            rc = p.rho_c_s;
-        } else if (k == 2) {
-            T = pT[c];
-            r = pr[c];
-            ux = pux[c];
-            uy = puy[c];
-            lam = p.cv_chi * r;
-            rc = r * p.c_v;
-        } else if (k == 3) {
-            if (row == 0) {
-                T = bottom_theta(p, x, n);
-                lam = p.lambda_s;
-            } else {
-                lam = p.cv_chi * pr[c];
-            }
-        }
-        kd[c] = k;
-        Tn[c] = T;
-        rcv[c] = rc;
-        rho[c] = r;
-        sT[0][hy][lane] = T;
-        sT[1][hy][lane] = T;
-        sLam[hy][lane] = lam;
-        sUx[hy][lane] = ux;
-        sUy[hy][lane] = uy;
-    }
-    // issue the next tile's loads now; they complete during this tile's stages
-    if (tile + (int)gridDim.x < ntiles) fetch(tile + gridDim.x);
-    __syncthreads();
-    // ---- per-step coefficients ----
-    const float w1 = 1.0f / 9.0f, w2 = 1.0f / 36.0f;
-    #pragma unroll
-    for (int c = 0; c < CPT; c++) {
-        const int hy = wy + c * NWARP;
-        #pragma unroll
-        for (int a = 0; a < 8; a++) kk[c][a] = 0.0f;
-        ks[c] = 0.0f; ax[c] = 0.0f; ay[c] = 0.0f; c1[c] = 0.0f; c2[c] = 0.0f;
-        acc[c] = 0.0f;
-        const bool inner = hy >= 1 && hy < SH - 1 && lane >= 1 && lane < 31;
-        if (inner && (kd[c] == 1 || kd[c] == 2)) {
-            const float l0 = sLam[hy][lane];
-            const float inv6 = 6.0f * fast_rcp(rcv[c]);
-            const float la[8] = {sLam[hy][lane + 1], sLam[hy + 1][lane], sLam[hy][lane - 1], sLam[hy - 1][lane],
-                                 sLam[hy + 1][lane + 1], sLam[hy + 1][lane - 1], sLam[hy - 1][lane - 1],
-                                 sLam[hy - 1][lane + 1]};
-            #pragma unroll
-            for (int a = 0; a < 8; a++) {
-                const float hm = 2.0f * l0 * la[a] * fast_rcp(l0 + la[a]);
-                kk[c][a] = (a < 4 ? w1 : w2) * hm * inv6;
-                ks[c] += kk[c][a];
-            }
-            if (kd[c] == 2) {
-                ax[c] = -3.0f * sUx[hy][lane];
-                ay[c] = -3.0f * sUy[hy][lane];
-                const float dx = w1 * (sUx[hy][lane + 1] - sUx[hy][lane - 1]) +
-                                 w2 * ((sUx[hy + 1][lane + 1] - sUx[hy - 1][lane - 1]) +
-                                       (sUx[hy - 1][lane + 1] - sUx[hy + 1][lane - 1]));
-                const float dy = w1 * (sUy[hy + 1][lane] - sUy[hy - 1][lane]) +
-                                 w2 * ((sUy[hy + 1][lane + 1] - sUy[hy - 1][lane - 1]) -
-                                       (sUy[hy - 1][lane + 1] - sUy[hy + 1][lane - 1]));
-                const float divu = 3.0f * (dx + dy);
-                const float br = p.b * rho[c];
-                const float iden = fast_rcp(1.0f + br * (2.0f - br));
-                const float pa = p.a_kappa * rho[c] * rho[c] * iden;
-                const float A = rho[c] * p.R * fast_rcp(1.0f - br) - pa * p.kappa_over_Tc;
-                const float B = pa * p.B_coef;
-                const float g0 = -divu * fast_rcp(rcv[c]);
-                c1[c] = g0 * A;
-                c2[c] = g0 * B;
-            }
-        }
-    }
-    // ---- four RK stages ----
-    if (!iso) {
-        #pragma unroll
-        for (int st = 0; st < 4; st++) {
-            const int m = st + 1;
-            const int rb = st & 1, wb = rb ^ 1;
-            #pragma unroll
-            for (int c = 0; c < CPT; c++) {
-                const int hy = wy + c * NWARP;
-                const float T0 = sT[rb][hy][lane];
-                const float Tu = (hy + 1 < SH) ? sT[rb][hy + 1][lane] : 0.0f;
-                const float Td = (hy >= 1) ? sT[rb][hy - 1][lane] : 0.0f;
-                const float T1 = __shfl_down_sync(0xffffffffu, T0, 1);
-                const float T3 = __shfl_up_sync(0xffffffffu, T0, 1);
-                const float T5 = __shfl_down_sync(0xffffffffu, Tu, 1);
-                const float T6 = __shfl_up_sync(0xffffffffu, Tu, 1);
-                const float T8 = __shfl_down_sync(0xffffffffu, Td, 1);
-                const float T7 = __shfl_up_sync(0xffffffffu, Td, 1);
-                const bool act = hy >= m && hy < SH - m && lane >= m && lane < 32 - m && (kd[c] == 1 || kd[c] == 2);
-                if (act) {
-                    float h = kk[c][0] * T1 + kk[c][1] * Tu + kk[c][2] * T3 + kk[c][3] * Td + kk[c][4] * T5 +
-                              kk[c][5] * T6 + kk[c][6] * T7 + kk[c][7] * T8 - ks[c] * T0;
-                    if (kd[c] == 2) {
-                        const float a = T5 - T7, b = T8 - T6;
-                        const float gx = w1 * (T1 - T3) + w2 * (a + b);
-                        const float gy = w1 * (Tu - Td) + w2 * (a - b);
-                        const float Ta = fmaxf(T0 + p.T_sat, 1e-30f);
-                        h += ax[c] * gx + ay[c] * gy + c1[c] * Ta + c2[c] * fast_sqrt(Ta);
-                    }
-                    if (st == 0) { acc[c] = h; sT[wb][hy][lane] = Tn[c] + 0.5f * h; }
-                    else if (st == 1) { acc[c] += 2.0f * h; sT[wb][hy][lane] = Tn[c] + 0.5f * h; }
-                    else if (st == 2) { acc[c] += 2.0f * h; sT[wb][hy][lane] = Tn[c] + h; }
-                    else { acc[c] += h; }
-                }
-            }
-            __syncthreads();
-        }
-    }
-    // ---- write the tile ----
-    #pragma unroll
-    for (int c = 0; c < CPT; c++) {
-        const int hy = wy + c * NWARP;
-        const int row = r0 + hy - H, xo = x0 + lane - H;
-        if (lane >= H && lane < 32 - H && hy >= H && hy < SH - H && row < nt && xo < nx) {
-            float v = Tn[c];
-            if ((kd[c] == 1 || kd[c] == 2) && !iso) v = Tn[c] + acc[c] * (1.0f / 6.0f);
-            if (!(fabsf(v) < 1e30f)) errbits |= ERRW_NONFINITE_T;
-            Tout[(size_t)row * nx + xo] = v;
-        }
-    }
-    __syncthreads();  // shared tiles are rewritten by the next iteration
-    }
-    if (errbits) atomicOr(err, errbits);
-}
-
-template <class P, int NWARP, int CPT>
-struct HeatPersShape {
-    static int grid_blocks;
-    static cudaError_t prepare() {
-        int dev = 0, sms = 0, per = 0;
-        cudaError_t e = cudaGetDevice(&dev);
-        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_heat_pers<P, NWARP, CPT>, NWARP * 32, 0);
-        if (e != cudaSuccess) return e;
-        grid_blocks = sms * (per > 0 ? per : 1);
-        return cudaSuccess;
-    }
-    static cudaError_t launch(const DevParams &p, const StepBuffers &b, cudaStream_t s) {
-        constexpr int TXO = 24, TYO = NWARP * CPT - 8;
-        const int tx = (p.nx + TXO - 1) / TXO, ty = (p.nt + TYO - 1) / TYO;
-        const int ntiles = tx * ty;
-        const int g = ntiles < grid_blocks ? ntiles : grid_blocks;
-        k_heat_pers<P, NWARP, CPT><<<g, NWARP * 32, 0, s>>>(
-            make_fparams(p), tx, ntiles, (const typename P::tst *)b.T_in, (typename P::tst *)b.T_out,
-            (const float *)b.rho, (const float *)b.ux, (const float *)b.uy, b.step, b.err);
-        return cudaGetLastError();
-    }
-};
-template <class P, int NWARP, int CPT>
-int HeatPersShape<P, NWARP, CPT>::grid_blocks = 152;
-
-template <class P, int NWARP, int CPT>
-struct HeatRegShape {
-    static cudaError_t prepare() { return cudaSuccess; }
-    static cudaError_t launch(const DevParams &p, const StepBuffers &b, cudaStream_t s) {
-        constexpr int TXO = 24, TYO = NWARP * CPT - 8;
-        dim3 g((p.nx + TXO - 1) / TXO, (p.nt + TYO - 1) / TYO);
-        k_heat_reg<P, NWARP, CPT><<<g, NWARP * 32, 0, s>>>(
-            make_fparams(p), (const typename P::tst *)b.T_in, (typename P::tst *)b.T_out, (const float *)b.rho,
-            (const float *)b.ux, (const float *)b.uy, b.step, b.err);
-        return cudaGetLastError();
-    }
-};
-
 }  // namespace lbmgb
 
 namespace lbmgb {
@@ -1336,7 +883,7 @@ namespace lbmgb {
 // A warp covers 32 columns of one row, so rows outside a stage's region are
 // skipped by whole warps.  The next tile's raw inputs are fetched into
 // registers while the current tile is computed.  Same arithmetic as
-// k_heat_fast / k_heat_reg.
+// k_heat_fast.
 // ============================================================================
 template <class P, int BW, int BY, int CPT, int MINB, bool WIDE>
 __global__ void __launch_bounds__(BW * BY, MINB)
@@ -1557,6 +1104,284 @@ struct HeatWideShape {
 };
 template <class P, int BW, int BY, int CPT, int MINB>
 int HeatWideShape<P, BW, BY, CPT, MINB>::grid_blocks = 152;
+
+// ============================================================================
+// Heat kernel, FP32, row-strip persistent variant.  Same tiling as
+// k_heat_wide (BW columns x SH = R BY rows of cells, 4-cell halo) but thread
+// (tx, ty) owns the R vertically adjacent cells of rows R ty .. R ty + R - 1:
+// their vertical neighbours are its own registers, and one stage of all R
+// cells reads 2 R + 6 words of shared memory (bank-conflict free).  Cells
+// that do not evolve (outside the domain, the Dirichlet bottom row, the top
+// ghost) get zero coefficients, so every cell runs the same branch-free
+// update and keeps T^n; cells outside a stage's shrinking region compute
+// values nobody reads.  The source of Eq. 24 is folded into the link form
+//   K(T) = sum_a k_a T_a - ks T_0 + c0 + c2 sqrt(T_0 + T_sat),
+// with ks = sum of the conduction weights - C1 and c0 = C1 T_sat.  The next
+// tile's raw inputs are staged in shared memory by cp.async (no registers).
+// ============================================================================
+enum : int { HK_OUT = 0, HK_SOLID = 1, HK_FLUID = 2, HK_BOTTOM = 3, HK_GHOST = 4 };
+
+// 4-byte global -> shared copy that does not pass through registers
+// (zero-filled and not read when !pred; src must still be a valid address)
+__device__ __forceinline__ void cp_async4(float *dst, const float *src, bool pred) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sa), "l"(src), "r"(pred ? 4 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+template <class P, int BW, int BY, int R, int MINB, bool WIDE>
+__global__ void __launch_bounds__(BW * BY, MINB)
+k_heat_rows(const FParams p, int tiles_x, int ntiles, const typename P::tst *__restrict__ Tin,
+            typename P::tst *__restrict__ Tout, const float *__restrict__ rho_i, const float *__restrict__ ux_i,
+            const float *__restrict__ uy_i, const long long *__restrict__ stepp, unsigned *__restrict__ err) {
+    constexpr int H = 4, SH = R * BY, TXO = BW - 2 * H, TYO = SH - 2 * H;
+    static_assert(BW % 32 == 0, "a warp must cover whole columns of one row strip");
+    __shared__ float sT[2][SH][BW];
+    // 1/lambda, u_x, u_y of the tile for the coefficient pass; afterwards the
+    // same arrays (and gV) stage the next tile's raw T, rho, u_x, u_y, each
+    // cell's slot written and read by its owning thread only
+    __shared__ float sL[SH][BW], sU[SH][BW], sV[SH][BW], gV[SH][BW];
+    const int tx = threadIdx.x, ty = threadIdx.y, y0 = R * ty;
+    const int nx = p.nx, nt = p.nt, ns = p.ns;
+    const bool py = (p.flags & FLAG_PERIODIC_Y) != 0;
+    const bool iso = (p.flags & FLAG_ISOTHERMAL) != 0;
+    const float tsat = p.T_sat;
+    unsigned errbits = 0;
+
+    float Tn[R], Tc[R], acc[R], kk[R][8], ks[R], c0[R], c2[R];
+    int pk = 0, px = 0;  // kinds of the staged cells (3 bits per cell) and their column
+
+    const int gdx = (int)gridDim.x % tiles_x, gdy = (int)gridDim.x / tiles_x;
+    auto fetch = [&](int txt, int tyt) {
+        const int x0 = txt * TXO, r0 = tyt * TYO;
+        const int x = WIDE ? wrap1(x0 + tx - H, nx) : wrapi(x0 + tx - H, nx);
+        px = x;
+        pk = 0;
+        #pragma unroll
+        for (int c = 0; c < R; c++) {
+            int row = r0 + y0 + c - H, k;
+            if (py) { row = WIDE ? wrap1(row, nt) : wrapi(row, nt); k = HK_FLUID; }
+            else if (row < 0 || row > nt) k = HK_OUT;
+            else if (row == 0) k = HK_BOTTOM;
+            else if (row == nt) k = HK_GHOST;
+            else k = (row < ns) ? HK_SOLID : HK_FLUID;
+            pk |= k << (3 * c);
+            const bool inT = k == HK_SOLID || k == HK_FLUID, fl = k == HK_FLUID, gh = k == HK_GHOST;
+            const int kt = inT ? row * nx + x : 0;                                   // T index
+            const int kf = fl ? kt - ns * nx : (gh ? (nt - ns - 1) * nx + x : 0);  // fluid index (ghost: top row)
+            cp_async4(&sL[y0 + c][tx], Tin + kt, inT);
+            cp_async4(&sU[y0 + c][tx], rho_i + kf, fl || gh);
+            cp_async4(&sV[y0 + c][tx], ux_i + kf, fl);
+            cp_async4(&gV[y0 + c][tx], uy_i + kf, fl);
+        }
+    };
+    const float w1 = 1.0f / 9.0f, w2 = 1.0f / 36.0f;
+    int cxt = (int)blockIdx.x % tiles_x, cyt = (int)blockIdx.x / tiles_x;
+    if ((int)blockIdx.x < ntiles) fetch(cxt, cyt);
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        int nxt = cxt + gdx, nyt = cyt + gdy;
+        if (nxt >= tiles_x) { nxt -= tiles_x; nyt += 1; }
+        const bool more = tile + (int)gridDim.x < ntiles;
+        int kd[R];
+        float irc[R], rho[R], ux[R], uy[R], lam[R];
+        cp_async_wait_all();
+        #pragma unroll
+        for (int c = 0; c < R; c++) {
+            const float Tr = sL[y0 + c][tx];
+            rho[c] = sU[y0 + c][tx]; ux[c] = sV[y0 + c][tx]; uy[c] = gV[y0 + c][tx];
+            const int k = (pk >> (3 * c)) & 7;
+            kd[c] = k;
+            float T = Tr, l = 0.0f, rc = 1.0f;
+            if (k == HK_SOLID) { l = p.lambda_s; rc = p.rho_c_s; }
+            else if (k == HK_FLUID) { l = p.cv_chi * rho[c]; rc = rho[c] * p.c_v; }
+            else if (k == HK_BOTTOM) { T = bottom_theta(p, px, *stepp); l = p.lambda_s; }
+            else if (k == HK_GHOST) l = p.cv_chi * rho[c];
+            Tn[c] = T; Tc[c] = T; irc[c] = fast_rcp(rc);
+            // 1/lambda: the harmonic mean of a link is 2 / (1/l0 + 1/la)
+            lam[c] = (l > 0.0f) ? fast_rcp(l) : 1e30f;
+            sT[0][y0 + c][tx] = T;
+            sT[1][y0 + c][tx] = T;
+            sL[y0 + c][tx] = lam[c];
+            sU[y0 + c][tx] = ux[c];
+            sV[y0 + c][tx] = uy[c];
+        }
+        __syncthreads();
+        // neighbour columns and rows, clamped into the tile (edge cells compute
+        // values nobody reads from them)
+        const int xl = tx > 0 ? tx - 1 : 0, xr = tx < BW - 1 ? tx + 1 : BW - 1;
+        const int yb = y0 > 0 ? y0 - 1 : 0, yt = y0 + R < SH ? y0 + R : SH - 1;
+        // rows y0 - 1 .. y0 + R of column x - 1 / x + 1 (index j = row - y0 + 1)
+        auto column = [&](const float (*a)[BW], int x, float *v) {
+            v[0] = a[yb][x];
+            #pragma unroll
+            for (int j = 0; j < R; j++) v[j + 1] = a[y0 + j][x];
+            v[R + 1] = a[yt][x];
+        };
+        // ---- per-step coefficients (neighbour order E, N, W, S, NE, NW, SW, SE) ----
+        {
+            // conduction: 6 w_a lambda_face / (rho c), lambda_face = 2 / (1/l0 + 1/la)
+            float Ll[R + 2], Lr[R + 2];
+            column(sL, xl, Ll);
+            column(sL, xr, Lr);
+            const float Lb = sL[yb][tx], Lt = sL[yt][tx];
+            #pragma unroll
+            for (int c = 0; c < R; c++) {
+                const float l0 = lam[c];
+                const float lN = c + 1 < R ? lam[c + 1] : Lt, lS = c > 0 ? lam[c - 1] : Lb;
+                const int k = kd[c];
+                const bool moves = (k == HK_SOLID || k == HK_FLUID) && !iso;
+                const float f12 = moves ? 12.0f * irc[c] : 0.0f;
+                const float cax = w1 * f12, cdg = w2 * f12;
+                kk[c][0] = cax * fast_rcp(l0 + Lr[c + 1]);
+                kk[c][1] = cax * fast_rcp(l0 + lN);
+                kk[c][2] = cax * fast_rcp(l0 + Ll[c + 1]);
+                kk[c][3] = cax * fast_rcp(l0 + lS);
+                kk[c][4] = cdg * fast_rcp(l0 + Lr[c + 2]);
+                kk[c][5] = cdg * fast_rcp(l0 + Ll[c + 2]);
+                kk[c][6] = cdg * fast_rcp(l0 + Ll[c]);
+                kk[c][7] = cdg * fast_rcp(l0 + Lr[c]);
+                ks[c] = ((kk[c][0] + kk[c][1]) + (kk[c][2] + kk[c][3])) + ((kk[c][4] + kk[c][5]) + (kk[c][6] + kk[c][7]));
+                c0[c] = 0.0f;
+                c2[c] = 0.0f;
+                acc[c] = 0.0f;
+            }
+        }
+        bool any_fluid = false;
+        #pragma unroll
+        for (int c = 0; c < R; c++) any_fluid |= kd[c] == HK_FLUID;
+        if (!iso && any_fluid) {
+            // advection (-u . grad T = sum_a adv_a T_a, adv_a = -3 w_a (e_a . u))
+            // and the (dp/dT)_rho div u source of Eq. 24, with the Eq. 27 gradient
+            float dd[R];
+            {
+                float Ul[R + 2], Ur[R + 2];
+                column(sU, xl, Ul);
+                column(sU, xr, Ur);
+                #pragma unroll
+                for (int c = 0; c < R; c++)
+                    dd[c] = w1 * (Ur[c + 1] - Ul[c + 1]) + w2 * ((Ur[c + 2] - Ul[c]) + (Ur[c] - Ul[c + 2]));
+            }
+            {
+                float Vl[R + 2], Vr[R + 2];
+                column(sV, xl, Vl);
+                column(sV, xr, Vr);
+                const float Vb = sV[yb][tx], Vt = sV[yt][tx];
+                #pragma unroll
+                for (int c = 0; c < R; c++) {
+                    const float vN = c + 1 < R ? uy[c + 1] : Vt, vS = c > 0 ? uy[c - 1] : Vb;
+                    dd[c] += w1 * (vN - vS) + w2 * ((Vr[c + 2] - Vl[c]) - (Vr[c] - Vl[c + 2]));
+                }
+            }
+            #pragma unroll
+            for (int c = 0; c < R; c++) {
+                if (kd[c] != HK_FLUID) continue;
+                const float vx = -3.0f * ux[c], vy = -3.0f * uy[c];
+                kk[c][0] += w1 * vx;          // e = ( 1,  0)
+                kk[c][1] += w1 * vy;          // e = ( 0,  1)
+                kk[c][2] -= w1 * vx;          // e = (-1,  0)
+                kk[c][3] -= w1 * vy;          // e = ( 0, -1)
+                kk[c][4] += w2 * (vx + vy);   // e = ( 1,  1)
+                kk[c][5] += w2 * (vy - vx);   // e = (-1,  1)
+                kk[c][6] -= w2 * (vx + vy);   // e = (-1, -1)
+                kk[c][7] += w2 * (vx - vy);   // e = ( 1, -1)
+                const float divu = 3.0f * dd[c];
+                const float r = rho[c];
+                const float br = p.b * r;
+                const float omb = 1.0f - br, den = 1.0f + br * (2.0f - br);
+                const float iod = fast_rcp(omb * den);
+                const float pa = p.a_kappa * r * r * (omb * iod);
+                const float A = r * p.R * (den * iod) - pa * p.kappa_over_Tc;
+                const float B = pa * p.B_coef;
+                const float g0 = -divu * irc[c];
+                const float C1 = g0 * A;
+                ks[c] -= C1;
+                c0[c] = C1 * tsat;
+                c2[c] = g0 * B;
+            }
+        }
+        // ---- four RK stages; stage s reads sT[s & 1], writes sT[(s + 1) & 1] ----
+        if (!iso) {
+            #pragma unroll
+            for (int st = 0; st < 4; st++) {
+                const int m = st + 1;
+                const int rb = st & 1, wb = rb ^ 1;
+                if (st > 0) __syncthreads();  // the previous stage's writes are visible
+                // the coefficient arrays are no longer read: stage the next tile
+                if (st == 1 && more) fetch(nxt, nyt);
+                if (y0 + R - 1 < m || y0 >= SH - m) continue;  // whole warp outside the region
+                float Tl[R + 2], Tr[R + 2];
+                column(sT[rb], xl, Tl);
+                column(sT[rb], xr, Tr);
+                const float Tb = sT[rb][yb][tx], Tt = sT[rb][yt][tx];
+                float h[R];
+                #pragma unroll
+                for (int c = 0; c < R; c++) {
+                    const float t0 = Tc[c];
+                    const float tN = c + 1 < R ? Tc[c + 1] : Tt, tS = c > 0 ? Tc[c - 1] : Tb;
+                    // T_0 + T_sat > 0 in every cell whose value is used
+                    float v = c0[c] + c2[c] * fast_sqrt(t0 + tsat);
+                    v += kk[c][0] * Tr[c + 1] + kk[c][1] * tN + kk[c][2] * Tl[c + 1] + kk[c][3] * tS +
+                         kk[c][4] * Tr[c + 2] + kk[c][5] * Tl[c + 2] + kk[c][6] * Tl[c] + kk[c][7] * Tr[c] - ks[c] * t0;
+                    h[c] = v;
+                }
+                #pragma unroll
+                for (int c = 0; c < R; c++) {
+                    if (st == 0) { acc[c] = h[c]; Tc[c] = Tn[c] + 0.5f * h[c]; }
+                    else if (st == 1) { acc[c] += 2.0f * h[c]; Tc[c] = Tn[c] + 0.5f * h[c]; }
+                    else if (st == 2) { acc[c] += 2.0f * h[c]; Tc[c] = Tn[c] + h[c]; }
+                    else acc[c] += h[c];
+                    if (st < 3) sT[wb][y0 + c][tx] = Tc[c];
+                }
+            }
+        } else if (more) {
+            __syncthreads();  // the coefficient arrays are staged into next
+            fetch(nxt, nyt);
+        }
+        // ---- write the tile (fixed cells have acc = 0) ----
+        const int x0 = cxt * TXO, r0 = cyt * TYO;
+        #pragma unroll
+        for (int c = 0; c < R; c++) {
+            const int hy = y0 + c;
+            const int row = r0 + hy - H, xo = x0 + tx - H;
+            if (tx >= H && tx < BW - H && hy >= H && hy < SH - H && row < nt && xo < nx) {
+                const float v = Tn[c] + acc[c] * (1.0f / 6.0f);
+                if (!(fabsf(v) < 1e30f)) errbits |= ERRW_NONFINITE_T;
+                Tout[row * nx + xo] = v;
+            }
+        }
+        __syncthreads();  // shared tiles are rewritten by the next tile
+        cxt = nxt; cyt = nyt;
+    }
+    if (errbits) atomicOr(err, errbits);
+}
+
+template <class P, int BW, int BY, int R, int MINB>
+struct HeatRowsShape {
+    static int grid_blocks;
+    static cudaError_t prepare() {
+        int dev = 0, sms = 0, per = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_heat_rows<P, BW, BY, R, MINB, true>, BW * BY, 0);
+        if (e != cudaSuccess) return e;
+        grid_blocks = sms * (per > 0 ? per : 1);
+        return cudaSuccess;
+    }
+    static cudaError_t launch(const DevParams &p, const StepBuffers &b, cudaStream_t s) {
+        constexpr int TXO = BW - 8, TYO = R * BY - 8;
+        const int tx = (p.nx + TXO - 1) / TXO, ty = (p.nt + TYO - 1) / TYO;
+        const int ntiles = tx * ty;
+        const int g = ntiles < grid_blocks ? ntiles : grid_blocks;
+        const bool wide = p.nx >= BW && (!(p.flags & FLAG_PERIODIC_Y) || p.nt >= R * BY);
+        auto k = wide ? k_heat_rows<P, BW, BY, R, MINB, true> : k_heat_rows<P, BW, BY, R, MINB, false>;
+        k<<<g, dim3(BW, BY), 0, s>>>(
+            make_fparams(p), tx, ntiles, (const typename P::tst *)b.T_in, (typename P::tst *)b.T_out,
+            (const float *)b.rho, (const float *)b.ux, (const float *)b.uy, b.step, b.err);
+        return cudaGetLastError();
+    }
+};
+template <class P, int BW, int BY, int R, int MINB>
+int HeatRowsShape<P, BW, BY, R, MINB>::grid_blocks = 152;
 
 }  // namespace lbmgb
 

@@ -17,10 +17,8 @@ cudaError_t diag(const DevParams &p, const StepBuffers &b, int nblk, cudaStream_
      FlowPersShape<P, BX, BY, RY, MB>::blocks, FlowPersShape<P, BX, BY, RY, MB>::prepare}
 #define HEATW(P, BW, BY, CPT, MB) \
     {"heatwide_" #BW "x" #BY "x" #CPT, HeatWideShape<P, BW, BY, CPT, MB>::launch, HeatWideShape<P, BW, BY, CPT, MB>::prepare}
-#define HEATP(P, NW, CPT) \
-    {"heatpers_24x" #NW "x" #CPT, HeatPersShape<P, NW, CPT>::launch, HeatPersShape<P, NW, CPT>::prepare}
-#define HEATR(P, NW, CPT) \
-    {"heatreg_24x" #NW "x" #CPT, HeatRegShape<P, NW, CPT>::launch, HeatRegShape<P, NW, CPT>::prepare}
+#define HEATS(P, BW, BY, R, MB) \
+    {"heatrows_" #BW "x" #BY "x" #R, HeatRowsShape<P, BW, BY, R, MB>::launch, HeatRowsShape<P, BW, BY, R, MB>::prepare}
 #define HEATV(P, TX, TY, BX, BY) \
     {"heat_" #TX "x" #TY "_t" #BX "x" #BY, HeatFastShape<P, TX, TY, BX, BY>::launch, HeatFastShape<P, TX, TY, BX, BY>::prepare}
 
@@ -30,14 +28,13 @@ const FlowVariant flows32[] = {
     FLOWV(PolicyF32, 64, 4, 2, 3), FLOWV(PolicyF32, 32, 8, 1, 4), FLOWV(PolicyF32, 64, 8, 2, 2),
 };
 const HeatVariant heats32[] = {
-    HEATW(PolicyF32, 64, 16, 2, 1), HEATW(PolicyF32, 64, 8, 4, 1), HEATW(PolicyF32, 32, 16, 2, 2),
-    HEATP(PolicyF32, 16, 2), HEATP(PolicyF32, 8, 4),
-    HEATR(PolicyF32, 16, 2), HEATR(PolicyF32, 8, 4), HEATR(PolicyF32, 32, 2),
-    HEATV(PolicyF32, 32, 16, 32, 8), HEATV(PolicyF32, 32, 32, 32, 16), HEATV(PolicyF32, 64, 16, 64, 4),
-    HEATV(PolicyF32, 64, 32, 32, 16),
+    HEATS(PolicyF32, 64, 10, 3, 1), HEATS(PolicyF32, 64, 8, 4, 1), HEATS(PolicyF32, 64, 6, 5, 1),
+    HEATS(PolicyF32, 64, 7, 4, 1), HEATS(PolicyF32, 64, 9, 3, 1), HEATS(PolicyF32, 32, 8, 4, 2),
+    HEATW(PolicyF32, 64, 16, 2, 1), HEATV(PolicyF32, 32, 16, 32, 8), HEATV(PolicyF32, 64, 32, 32, 16),
 };
 const FlowVariant flows16[] = {FLOWP(PolicyF16, 32, 8, 2, 2), FLOWV(PolicyF16, 32, 8, 2, 3)};
-const HeatVariant heats16[] = {HEATW(PolicyF16, 64, 16, 2, 1), HEATP(PolicyF16, 16, 2), HEATR(PolicyF16, 16, 2), HEATR(PolicyF16, 8, 4), HEATV(PolicyF16, 32, 32, 32, 16)};
+const HeatVariant heats16[] = {HEATS(PolicyF16, 64, 10, 3, 1), HEATS(PolicyF16, 64, 8, 4, 1), HEATW(PolicyF16, 64, 16, 2, 1),
+                               HEATV(PolicyF16, 32, 32, 32, 16)};
 
 const KernelSet ks32 = {"fp32", sizeof(float), sizeof(float), sizeof(float),
                         (int)(sizeof(flows32) / sizeof(flows32[0])), flows32,
