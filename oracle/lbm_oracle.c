@@ -19,6 +19,14 @@
  * 0..nx-1); temperature T[r][x] for rows r = 0..nt-1, nt = ns + nf, where
  * rows 0..ns-1 are the solid heater (row 0 = heater bottom, Dirichlet) and
  * fluid row y is temperature row ns + y.
+ *
+ * Model A (Fig. 1a, Sec. 4.1: no solid, the temperature given at the bottom
+ * surface of the fluid) is flag F_MODEL_A with ns = 1: row 0 is then not a
+ * heater row but the Dirichlet row of the heated wall, holding T_b(x, n).
+ * reading: it is coupled to the first fluid row like the top ghost row is
+ * to the last one -- the link conducts with the fluid's lambda (the mean of
+ * lambda_f with itself), so T_b sits one lattice spacing below the first
+ * fluid row, half a spacing below the halfway wall of the flow part.
  */
 #include <math.h>
 #include <stdint.h>
@@ -50,7 +58,7 @@ static const int MM[9][9] = {
 static const double INVN[9] = {1.0 / 9.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 6.0, 1.0 / 12.0,
                                1.0 / 6.0, 1.0 / 12.0, 1.0 / 4.0, 1.0 / 4.0};
 
-enum { F_PERIODIC_Y = 1, F_ISOTHERMAL = 2, F_FROZEN_FLOW = 4 };
+enum { F_PERIODIC_Y = 1, F_ISOTHERMAL = 2, F_FROZEN_FLOW = 4, F_MODEL_A = 8 };
 enum { TOP_WALL = 0, TOP_OUTFLOW = 1 };
 enum { BC_SPOTS = 0, BC_NOISE = 1, BC_SINE = 2 };
 enum { ERR_PSI = 1, ERR_NONFINITE = 2 };
@@ -488,7 +496,8 @@ static void fd_part(orc_run *r)
         for (int x = 0; x < nx; x++) {
             size_t k = (size_t)row * nx + x;
             if (row < ns) {
-                r->lam[k] = p->lambda_s;
+                /* Model A: the wall row conducts like the first fluid row */
+                r->lam[k] = (p->flags & F_MODEL_A) ? p->cv_chi * r->rho[x] : p->lambda_s;
                 r->uxe[k] = 0.0; r->uye[k] = 0.0; r->rhoe[k] = 0.0;
             } else if (row < nt) {
                 size_t kf = (size_t)(row - ns) * nx + x;
@@ -546,15 +555,18 @@ static void fd_part(orc_run *r)
 
 /* Diagnostics after the step: Eq. 36/39 heat flux at the heater bottom
  * (lambda_s, rows 0-2), local flux through the heater/fluid interface, vapour
- * fraction (rho below the mean of the coexistence densities), total mass. */
+ * fraction (rho below the mean of the coexistence densities), total mass.
+ * Model A has no heater: both fluxes are the flux through the heated wall,
+ * -lambda_f (T(first fluid row) - T_b). */
 static void diagnostics(orc_run *r)
 {
     const orc_params *p = &r->p;
     const int nx = p->nx, nf = p->nf, ns = p->ns;
+    const int model_a = (p->flags & F_MODEL_A) != 0;
     double qb = 0.0, qt = 0.0, mass = 0.0;
     long long nvap = 0;
     double thr = 0.5 * (p->rho_L + p->rho_V);
-    if (ns >= 3 && !(p->flags & F_PERIODIC_Y)) {
+    if (ns >= 3 && !model_a && !(p->flags & F_PERIODIC_Y)) {
         for (int x = 0; x < nx; x++) {
             double T0 = r->T[x], T1 = r->T[nx + x], T2 = r->T[2 * nx + x];
             double dTdy = ((4.0 * T1 - T2) - 3.0 * T0) / 2.0;
@@ -564,12 +576,14 @@ static void diagnostics(orc_run *r)
     }
     if (ns >= 1 && !(p->flags & F_PERIODIC_Y)) {
         for (int x = 0; x < nx; x++) {
-            double lf = hmean(p->lambda_s, p->cv_chi * r->rho[x]);
+            double lw = model_a ? p->cv_chi * r->rho[x] : p->lambda_s;
+            double lf = hmean(lw, p->cv_chi * r->rho[x]);
             double q = -lf * (r->T[(size_t)ns * nx + x] - r->T[(size_t)(ns - 1) * nx + x]);
             r->q_top[x] = q;
             qt += q;
         }
         qt = qt / (double)nx;
+        if (model_a) qb = qt;
     }
     for (size_t k = 0; k < (size_t)nx * nf; k++) {
         mass += r->rho[k];

@@ -104,9 +104,11 @@ def _dp(a: np.ndarray):
 
 def _params(cfg) -> _Params:
     p = _Params()
-    p.nx, p.nf, p.ns, p.liquid_rows = cfg.nx, cfg.nf, cfg.ns, cfg.liquid_rows
+    # Model A (no heater): row 0 of T is the wall's Dirichlet row
+    p.nx, p.nf, p.ns, p.liquid_rows = cfg.nx, cfg.nf, cfg.t_rows - cfg.nf, cfg.liquid_rows
     p.top_mode = {"wall": 0, "outflow": 1}[cfg.top_mode]
-    p.flags = (1 if cfg.periodic_y else 0) | (2 if cfg.isothermal else 0) | (4 if cfg.frozen_flow else 0)
+    p.flags = ((1 if cfg.periodic_y else 0) | (2 if cfg.isothermal else 0) | (4 if cfg.frozen_flow else 0)
+               | (8 if cfg.model_a else 0))
     p.bc_mode = {"spots": 0, "noise": 1, "sine": 2}[cfg.bc_mode]
     if len(cfg.spot_x) > 8 or len(cfg.c_w_spot) < len(cfg.spot_x):
         raise ValueError("at most 8 spots, each with a c_w value")
@@ -129,7 +131,7 @@ def _params(cfg) -> _Params:
 
 class OracleRun:
     """One boiling run advanced by the oracle.  Arrays are returned as copies:
-    f[9, nf, nx], T[ns + nf, nx], rho/ux/uy[nf, nx] (the moments of the last
+    f[9, nf, nx], T[t_rows, nx] (ns + nf rows; Model A: 1 + nf), rho/ux/uy[nf, nx] (the moments of the last
     step, i.e. rho^n and the force-corrected u^n used by the collision)."""
 
     def __init__(self, cfg):
@@ -138,7 +140,7 @@ class OracleRun:
         self._h = lib().orc_create(C.byref(self._p))
         if not self._h:
             raise MemoryError("oracle allocation failed")
-        self.nx, self.nf, self.nt = cfg.nx, cfg.nf, cfg.ns + cfg.nf
+        self.nx, self.nf, self.nt = cfg.nx, cfg.nf, cfg.t_rows
 
     def __del__(self):
         h = getattr(self, "_h", None)

@@ -48,7 +48,7 @@ class RunConfig:
 
     nx: int                      # columns (periodic)
     nf: int                      # fluid rows
-    ns: int                      # heater (solid) rows; row 0 is the heater bottom
+    ns: int                      # heater (solid) rows; row 0 is the heater bottom; 0: Model A
     liquid_rows: int             # initial liquid layer thickness (fluid rows)
     top_mode: str = "wall"       # "wall" (paper) or "outflow"
     periodic_y: bool = False     # test mode: periodic in y, no heater, no walls
@@ -98,8 +98,19 @@ class RunConfig:
         return self.nx * self.nf
 
     @property
+    def model_a(self) -> bool:
+        """Model A of Fig. 1a: no heater (ns = 0, walls at the bottom)."""
+        return self.ns == 0 and not self.periodic_y
+
+    @property
+    def t_rows(self) -> int:
+        """Rows of the temperature field: the heater and the fluid, or for
+        Model A the wall's Dirichlet row (row 0) and the fluid."""
+        return self.nf + (1 if self.model_a else self.ns)
+
+    @property
     def temperature_sites(self) -> int:
-        return self.nx * (self.ns + self.nf)
+        return self.nx * self.t_rows
 
 
 #: Largest buoyancy head (rho_mean - rho_V) g H_vapour the runs are given.

@@ -73,6 +73,50 @@ def test_steady_conduction_through_heater_and_fluid_slab():
     assert d["q_top"] == pytest.approx(-q, rel=1e-9)
 
 
+def test_model_a_steady_conduction_is_linear_between_the_two_dirichlet_rows():
+    """Model A (no heater): frozen uniform liquid between the wall row (row
+    0, T_b) and the top ghost (row nt, T_sat).  Every link conducts with the
+    same lambda_f, so the steady discrete solution is linear in the row
+    index with slope (T_sat - T_b) / nt, and the wall flux the diagnostics
+    report is -lambda_f times that slope.  A heater conductivity on the
+    wall link would put a kink at row 0."""
+    nx, nf = 4, 6
+    cfg = W.RunConfig(nx=nx, nf=nf, ns=0, liquid_rows=nf, frozen_flow=True, bc_mode="spots",
+                      init_noise=0.0, lambda_s=3.25, rho_c_s=39.0, T_b_over_Tc=0.96, g=0.0)
+    assert cfg.model_a and cfg.t_rows == nf + 1
+    r = O.OracleRun(cfg)
+    r.step(20000)
+    tc = r.Tc
+    tb, tsat = 0.96 * tc, 0.86 * tc
+    nt = nf + 1
+    prof = tb + (tsat - tb) * np.arange(nt) / nt
+    np.testing.assert_allclose(r.T, np.broadcast_to(prof[:, None], (nt, nx)), rtol=0, atol=1e-13)
+    d = r.diagnostics()
+    lam_f = 0.05 * 6.5
+    q = -lam_f * (tsat - tb) / nt
+    assert d["q_bottom"] == pytest.approx(q, rel=1e-9)
+    assert d["q_top"] == pytest.approx(q, rel=1e-9)
+    np.testing.assert_allclose(r.q_top, q, rtol=1e-9)
+
+
+def test_model_a_wall_row_follows_the_bottom_condition_and_sets_the_flux():
+    """Model A with the noisy bottom: after a step row 0 holds
+    T_b (1 + A (2U - 1)) with U the counter-based draw of that column and
+    step, and the wall flux is -lambda_f (T(row 1) - T(row 0)) with
+    lambda_f = cv_chi rho of the first fluid row."""
+    nx, nf = 16, 8
+    cfg = W.RunConfig(nx=nx, nf=nf, ns=0, liquid_rows=nf, frozen_flow=True, isothermal=True,
+                      bc_mode="noise", init_noise=0.0, T_b_over_Tc=0.96, g=0.0, seed=11)
+    r = O.OracleRun(cfg)
+    r.step(3)
+    tb = 0.96 * r.Tc
+    U = np.array([O.uniform(11, 2, 2, x) for x in range(nx)])
+    np.testing.assert_allclose(r.T[0], tb * (1 + cfg.bc_noise * (2 * U - 1)), rtol=1e-15, atol=0)
+    q = -(cfg.cv_chi * r.rho[0]) * (r.T[1] - r.T[0])
+    np.testing.assert_allclose(r.q_top, q, rtol=1e-13)
+    assert r.diagnostics()["q_bottom"] == pytest.approx(q.mean(), rel=1e-13)
+
+
 def test_wall_flux_formula_exact_on_quadratic_profile():
     """Eq. 36 is second-order one-sided: exact for T = T_b + alpha y + beta y^2."""
     nx, ns, nf = 6, 4, 4
