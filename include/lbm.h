@@ -2,7 +2,9 @@
  * lbm.h -- C ABI of the GB300 boiling time-step library (liblbm_gb300.so).
  *
  * One run = one 2-D domain of NX periodic columns: NS solid heater rows
- * (row 0 = heater bottom) under NF fluid rows.  Each time step advances
+ * (row 0 = heater bottom) under NF fluid rows (model B of Fig. 1b), or with
+ * NS = 0 the fluid alone on a heated wall (model A of Fig. 1a).  Each time
+ * step advances
  *   - the flow: D2Q9 multiple-relaxation-time lattice Boltzmann collision with
  *     the pseudopotential force of a Peng-Robinson fluid and Li's improved
  *     forcing, fused with streaming and halfway bounce-back
@@ -28,8 +30,10 @@
  *   - A handle is not thread-safe; distinct handles are independent.
  *
  * Layouts (row-major, x fastest): populations f[9][NF][NX] in the order of
- * Eq. 2; temperature T[NS+NF][NX]; rho, ux, uy [NF][NX].  Values crossing the
- * ABI are always float64, whatever the internal storage precision.
+ * Eq. 2; temperature T[NT][NX] with NT = NS + NF (model A: NT = 1 + NF, row
+ * 0 being the heated wall's Dirichlet row); rho, ux, uy [NF][NX].  Values
+ * crossing the ABI are always float64, whatever the internal storage
+ * precision.
  */
 #ifndef LBM_GB300_H
 #define LBM_GB300_H
@@ -86,9 +90,15 @@ typedef struct {
 } lbm_domain_t;
 
 /* Solid heater for conjugate heat transfer (Fig. 1b, Sec. 3.1).  Heater rows
- * conduct only: dT/dt = div(lambda_s grad T) / rho_c_s. */
+ * conduct only: dT/dt = div(lambda_s grad T) / rho_c_s.
+ * ny_solid = 0 on a domain that is not periodic in y selects model A
+ * (Fig. 1a, Sec. 4.1): no heater; the bottom temperature T_b(x, n) of
+ * lbm_bc_t is held in T row 0, one lattice spacing below the first fluid
+ * row and coupled to it with the fluid's conductivity (the mirror of the
+ * top row's coupling to T_sat); lambda_s and rho_c_s are ignored and both
+ * flux diagnostics report the wall flux -lambda_f (T(row 1) - T_b). */
 typedef struct {
-    int32_t ny_solid;    /* NS heater rows; >= 3 unless the domain is periodic in y */
+    int32_t ny_solid;    /* NS heater rows: >= 3, or 0 (model A; required when periodic in y) */
     int32_t pad0;
     double lambda_s;     /* heater conductivity */
     double rho_c_s;      /* heater volumetric heat capacity rho_S c_S */
@@ -151,13 +161,13 @@ int64_t lbm_step_count(lbm_handle h);
 
 /* Copy fields out as float64.  For each bit set in mask, in the order RHO,
  * UX, UY, T, F, the next pointer of dst receives the field (rho/ux/uy:
- * NF*NX values, the moments of the last step; T: (NS+NF)*NX; F: 9*NF*NX,
+ * NF*NX values, the moments of the last step; T: NT*NX; F: 9*NF*NX,
  * post-stream populations).  dst_is_device: 1 if the pointers are device
  * memory on the run's device, 0 for host memory.  Synchronises. */
 int lbm_fields(lbm_handle h, unsigned mask, double *const *dst, int dst_is_device);
 
 /* Replace the state: post-stream populations f (9*NF*NX) and temperature T
- * ((NS+NF)*NX), float64, host or device; either may be NULL to keep it.
+ * (NT*NX), float64, host or device; either may be NULL to keep it.
  * Sets the step counter to `step` (the counter keys the noisy bottom). */
 int lbm_set_state(lbm_handle h, const double *f, const double *T, int64_t step,
                   int src_is_device);

@@ -454,7 +454,8 @@ k_heat(const DevParams p, const typename P::tst *__restrict__ Tin, typename P::t
         } else if (kd == 3) {
             if (row == 0) {
                 T = R(bottom_temperature(p, x, n) - (P::shifted ? p.T_sat : 0.0));
-                lam = (ns > 0) ? R(p.lambda_s) : R(p.cv_chi) * rho_i[x];
+                // Model A: the wall row conducts like the first fluid row
+                lam = (p.flags & FLAG_MODEL_A) ? R(p.cv_chi) * rho_i[x] : R(p.lambda_s);
             } else {
                 T = P::shifted ? R(0) : R(p.T_sat);
                 lam = R(p.cv_chi) * rho_i[(size_t)(nf - 1) * nx + x];
@@ -615,6 +616,7 @@ k_diag(const DevParams p, const typename P::tst *__restrict__ T, const typename 
     __shared__ double sh[2][NT / 32];
     const int nx = p.nx, ns = p.ns;
     const bool py = (p.flags & FLAG_PERIODIC_Y) != 0;
+    const bool model_a = (p.flags & FLAG_MODEL_A) != 0;  // no heater: wall flux for both
     const double toff = P::shifted ? p.T_sat : 0.0;
     double mass = 0.0, nvap = 0.0;
     for (int b = threadIdx.x; b < nblk; b += NT) {
@@ -625,13 +627,13 @@ k_diag(const DevParams p, const typename P::tst *__restrict__ T, const typename 
     __syncthreads();
     double qb = 0.0, qt = 0.0;
     for (int x = threadIdx.x; x < nx; x += NT) {
-        if (ns >= 3 && !py) {
+        if (ns >= 3 && !model_a && !py) {
             const double T0 = (double)T[x] + toff, T1 = (double)T[nx + x] + toff, T2 = (double)T[2 * nx + x] + toff;
             const double dTdy = ((4.0 * T1 - T2) - 3.0 * T0) / 2.0;
             qb += (-p.lambda_s) * dTdy;
         }
         if (ns >= 1 && !py) {
-            const double lf0 = p.lambda_s, lf1 = p.cv_chi * (double)rho[x];
+            const double lf1 = p.cv_chi * (double)rho[x], lf0 = model_a ? p.cv_chi * (double)rho[x] : p.lambda_s;
             const double lf = (2.0 * (lf0 * lf1)) / (lf0 + lf1);
             const double Tu = (double)T[(size_t)ns * nx + x] + toff;
             const double Td = (double)T[(size_t)(ns - 1) * nx + x] + toff;
@@ -645,8 +647,9 @@ k_diag(const DevParams p, const typename P::tst *__restrict__ T, const typename 
         const long long n = *stepp;
         const double nfl = (double)nx * (double)p.nf;
         double v[SERIES_WIDTH] = {qb / (double)nx, qt / (double)nx, nvap / nfl, mass};
-        if (!(ns >= 3 && !py)) v[0] = 0.0;
+        if (!(ns >= 3 && !model_a && !py)) v[0] = 0.0;
         if (!(ns >= 1 && !py)) v[1] = 0.0;
+        if (model_a) v[0] = v[1];
         const long long slot = n % cap;
         #pragma unroll
         for (int k = 0; k < SERIES_WIDTH; k++) {

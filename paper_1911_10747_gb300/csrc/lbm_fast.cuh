@@ -684,9 +684,9 @@ k_heat_fast(const FParams p, const typename P::tst *__restrict__ Tin, typename P
                 lam = p.cv_chi * rho;
                 rcv = rho * p.c_v;
             } else if (kd == 3) {
-                if (row == 0) {
+                if (row == 0) {  // Model A: the wall row conducts like the first fluid row
                     T = bottom_theta(p, x, n);
-                    lam = p.lambda_s;
+                    lam = (p.flags & FLAG_MODEL_A) ? p.cv_chi * rho_i[x] : p.lambda_s;
                 } else {
                     T = 0.0f;
                     lam = p.cv_chi * rho_i[(size_t)(nf - 1) * nx + x];
@@ -875,240 +875,10 @@ struct HeatFastShape {
 namespace lbmgb {
 
 // ============================================================================
-// Heat kernel, FP32, wide persistent variant.  A block covers BW columns x
-// SH = BY * CPT rows of cells (4-cell halo, so (BW - 8) x (SH - 8) outputs);
-// thread (tx, ty) owns column tx, rows ty + c BY.  Per-step coefficients,
-// T^n, the current stage temperature and the RK accumulator stay in
-// registers; neighbours' stage temperatures are read from shared memory.
-// A warp covers 32 columns of one row, so rows outside a stage's region are
-// skipped by whole warps.  The next tile's raw inputs are fetched into
-// registers while the current tile is computed.  Same arithmetic as
-// k_heat_fast.
-// ============================================================================
-template <class P, int BW, int BY, int CPT, int MINB, bool WIDE>
-__global__ void __launch_bounds__(BW * BY, MINB)
-k_heat_wide(const FParams p, int tiles_x, int ntiles, const typename P::tst *__restrict__ Tin,
-            typename P::tst *__restrict__ Tout, const float *__restrict__ rho_i, const float *__restrict__ ux_i,
-            const float *__restrict__ uy_i, const long long *__restrict__ stepp, unsigned *__restrict__ err) {
-    constexpr int H = 4, SH = BY * CPT, TXO = BW - 2 * H, TYO = SH - 2 * H;
-    static_assert(BW % 32 == 0, "a warp must cover whole columns of one row");
-    __shared__ float sT[2][SH][BW];
-    __shared__ float sLam[SH][BW], sUx[SH][BW], sUy[SH][BW];
-    const int tx = threadIdx.x, ty = threadIdx.y;
-    const int nx = p.nx, nt = p.nt, ns = p.ns, nf = p.nf;
-    const bool py = (p.flags & FLAG_PERIODIC_Y) != 0;
-    const bool iso = (p.flags & FLAG_ISOTHERMAL) != 0;
-    const long long n = *stepp;
-    unsigned errbits = 0;
-
-    // kk: link weights of conduction with the advection of Eq. 24 folded in
-    // (-u . grad T with the Eq. 27 gradient is linear in the neighbours' T)
-    float Tn[CPT], Tc[CPT], acc[CPT], kk[CPT][8], ks[CPT], c1[CPT], c2[CPT];
-    int kd[CPT];
-    float pT[CPT], pr[CPT], pux[CPT], puy[CPT];
-    int pkd[CPT], prow[CPT], px[CPT];  // kind, row and column of the prefetched cells
-
-    // WIDE (compile time): nx >= BW and, if periodic in y, nt >= SH, so the
-    // wraps below are one compare instead of an integer modulo
-    const int gdx = (int)gridDim.x % tiles_x, gdy = (int)gridDim.x / tiles_x;
-    auto classify = [&](int txt, int tyt, int c, int &row, int &x) {
-        const int x0 = txt * TXO, r0 = tyt * TYO;
-        x = WIDE ? wrap1(x0 + tx - H, nx) : wrapi(x0 + tx - H, nx);
-        row = r0 + ty + c * BY - H;
-        int k;
-        if (py) { row = WIDE ? wrap1(row, nt) : wrapi(row, nt); k = 2; }
-        else if (row < 0 || row > nt) k = 0;
-        else if (row == 0 || row == nt) k = 3;
-        else k = (row < ns) ? 1 : 2;
-        return k;
-    };
-    auto fetch = [&](int txt, int tyt) {
-        #pragma unroll
-        for (int c = 0; c < CPT; c++) {
-            int row, x;
-            const int k = classify(txt, tyt, c, row, x);
-            pkd[c] = k; prow[c] = row; px[c] = x;
-            pT[c] = 0.0f; pr[c] = 0.0f; pux[c] = 0.0f; puy[c] = 0.0f;
-            if (k == 1 || k == 2) pT[c] = Tin[(size_t)row * nx + x];
-            if (k == 2) {
-                const size_t kf = (size_t)(row - ns) * nx + x;
-                pr[c] = rho_i[kf]; pux[c] = ux_i[kf]; puy[c] = uy_i[kf];
-            } else if (k == 3 && row == nt) {
-                pr[c] = rho_i[(size_t)(nf - 1) * nx + x];
-            }
-        }
-    };
-    const float w1 = 1.0f / 9.0f, w2 = 1.0f / 36.0f;
-    int cxt = (int)blockIdx.x % tiles_x, cyt = (int)blockIdx.x / tiles_x;  // current tile
-    if ((int)blockIdx.x < ntiles) fetch(cxt, cyt);
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int x0 = cxt * TXO, r0 = cyt * TYO;
-        int nxt = cxt + gdx, nyt = cyt + gdy;  // next tile of this block
-        if (nxt >= tiles_x) { nxt -= tiles_x; nyt += 1; }
-        float rcv[CPT], rho[CPT];
-        // ---- load from the prefetched registers ----
-        #pragma unroll
-        for (int c = 0; c < CPT; c++) {
-            const int hy = ty + c * BY;
-            const int row = prow[c], x = px[c], k = pkd[c];
-            float T = 0.0f, lam = 0.0f, ux = 0.0f, uy = 0.0f, rc = 1.0f, r = 0.0f;
-            if (k == 1) {
-                T = pT[c]; lam = p.lambda_s; rc = p.rho_c_s;
-            } else if (k == 2) {
-                T = pT[c]; r = pr[c]; ux = pux[c]; uy = puy[c];
-                lam = p.cv_chi * r; rc = r * p.c_v;
-            } else if (k == 3) {
-                if (row == 0) { T = bottom_theta(p, x, n); lam = p.lambda_s; }
-                else lam = p.cv_chi * pr[c];
-            }
-            kd[c] = k; Tn[c] = T; Tc[c] = T; rcv[c] = rc; rho[c] = r;
-            sT[0][hy][tx] = T;
-            // 1/lambda: the harmonic mean of a link is 2 / (1/l0 + 1/la)
-            sLam[hy][tx] = (lam > 0.0f) ? fast_rcp(lam) : 1e30f;
-            sUx[hy][tx] = ux; sUy[hy][tx] = uy;
-        }
-        if (tile + (int)gridDim.x < ntiles) fetch(nxt, nyt);
-        __syncthreads();
-        // ---- per-step coefficients ----
-        #pragma unroll
-        for (int c = 0; c < CPT; c++) {
-            const int hy = ty + c * BY;
-            #pragma unroll
-            for (int a = 0; a < 8; a++) kk[c][a] = 0.0f;
-            ks[c] = 0.0f; c1[c] = 0.0f; c2[c] = 0.0f; acc[c] = 0.0f;
-            const bool inner = hy >= 1 && hy < SH - 1 && tx >= 1 && tx < BW - 1;
-            if (inner && (kd[c] == 1 || kd[c] == 2)) {
-                const float r0l = sLam[hy][tx];
-                const float inv12 = 12.0f * fast_rcp(rcv[c]);
-                const float ra[8] = {sLam[hy][tx + 1], sLam[hy + 1][tx], sLam[hy][tx - 1], sLam[hy - 1][tx],
-                                     sLam[hy + 1][tx + 1], sLam[hy + 1][tx - 1], sLam[hy - 1][tx - 1], sLam[hy - 1][tx + 1]};
-                const float c_ax = w1 * inv12, c_dg = w2 * inv12;
-                #pragma unroll
-                for (int a = 0; a < 8; a++) {
-                    // 6 w_a lambda_face / (rho c) with lambda_face = 2 / (1/l0 + 1/la)
-                    kk[c][a] = (a < 4 ? c_ax : c_dg) * fast_rcp(r0l + ra[a]);
-                    ks[c] += kk[c][a];
-                }
-                if (kd[c] == 2) {
-                    // -u . grad T = sum_a adv_a T_a with adv_a = -3 w_a (e_a . u)
-                    const float vx = -3.0f * sUx[hy][tx], vy = -3.0f * sUy[hy][tx];
-                    kk[c][0] += w1 * vx;          // e = ( 1,  0)
-                    kk[c][1] += w1 * vy;          // e = ( 0,  1)
-                    kk[c][2] -= w1 * vx;          // e = (-1,  0)
-                    kk[c][3] -= w1 * vy;          // e = ( 0, -1)
-                    kk[c][4] += w2 * (vx + vy);   // e = ( 1,  1)
-                    kk[c][5] += w2 * (vy - vx);   // e = (-1,  1)
-                    kk[c][6] -= w2 * (vx + vy);   // e = (-1, -1)
-                    kk[c][7] += w2 * (vx - vy);   // e = ( 1, -1)
-                    const float dx = w1 * (sUx[hy][tx + 1] - sUx[hy][tx - 1]) +
-                                     w2 * ((sUx[hy + 1][tx + 1] - sUx[hy - 1][tx - 1]) + (sUx[hy - 1][tx + 1] - sUx[hy + 1][tx - 1]));
-                    const float dy = w1 * (sUy[hy + 1][tx] - sUy[hy - 1][tx]) +
-                                     w2 * ((sUy[hy + 1][tx + 1] - sUy[hy - 1][tx - 1]) - (sUy[hy - 1][tx + 1] - sUy[hy + 1][tx - 1]));
-                    const float divu = 3.0f * (dx + dy);
-                    const float br = p.b * rho[c];
-                    const float iden = fast_rcp(1.0f + br * (2.0f - br));
-                    const float pa = p.a_kappa * rho[c] * rho[c] * iden;
-                    const float A = rho[c] * p.R * fast_rcp(1.0f - br) - pa * p.kappa_over_Tc;
-                    const float B = pa * p.B_coef;
-                    const float g0 = -divu * fast_rcp(rcv[c]);
-                    c1[c] = g0 * A;
-                    c2[c] = g0 * B;
-                }
-            }
-        }
-        // ---- four RK stages; stage s reads sT[s & 1], writes sT[(s + 1) & 1] ----
-        if (!iso) {
-            #pragma unroll
-            for (int st = 0; st < 4; st++) {
-                const int m = st + 1;
-                const int rb = st & 1, wb = rb ^ 1;
-                if (st > 0) __syncthreads();  // the previous stage's writes are visible
-                #pragma unroll
-                for (int c = 0; c < CPT; c++) {
-                    const int hy = ty + c * BY;
-                    if (hy < m || hy >= SH - m) continue;  // whole warp
-                    const bool act = tx >= m && tx < BW - m && (kd[c] == 1 || kd[c] == 2);
-                    if (!act) continue;
-                    const float T0 = Tc[c];
-                    const float T1 = sT[rb][hy][tx + 1], T3 = sT[rb][hy][tx - 1];
-                    const float Tu = sT[rb][hy + 1][tx], Td = sT[rb][hy - 1][tx];
-                    const float T5 = sT[rb][hy + 1][tx + 1], T6 = sT[rb][hy + 1][tx - 1];
-                    const float T7 = sT[rb][hy - 1][tx - 1], T8 = sT[rb][hy - 1][tx + 1];
-                    float h = kk[c][0] * T1 + kk[c][1] * Tu + kk[c][2] * T3 + kk[c][3] * Td + kk[c][4] * T5 +
-                              kk[c][5] * T6 + kk[c][6] * T7 + kk[c][7] * T8 - ks[c] * T0;
-                    if (kd[c] == 2) {
-                        const float Ta = fmaxf(T0 + p.T_sat, 1e-30f);
-                        h += c1[c] * Ta + c2[c] * fast_sqrt(Ta);
-                    }
-                    float Tnext;
-                    if (st == 0) { acc[c] = h; Tnext = Tn[c] + 0.5f * h; }
-                    else if (st == 1) { acc[c] += 2.0f * h; Tnext = Tn[c] + 0.5f * h; }
-                    else if (st == 2) { acc[c] += 2.0f * h; Tnext = Tn[c] + h; }
-                    else { acc[c] += h; Tnext = Tn[c]; }
-                    if (st < 3) { Tc[c] = Tnext; sT[wb][hy][tx] = Tnext; }
-                }
-                // cells outside this stage's region keep their value in the
-                // other buffer too (fixed cells, or values no longer read)
-                if (st == 0) {
-                    #pragma unroll
-                    for (int c = 0; c < CPT; c++) {
-                        const int hy = ty + c * BY;
-                        const bool act = hy >= 1 && hy < SH - 1 && tx >= 1 && tx < BW - 1 && (kd[c] == 1 || kd[c] == 2);
-                        if (!act) sT[1][hy][tx] = Tn[c];
-                    }
-                }
-            }
-        }
-        // ---- write the tile ----
-        #pragma unroll
-        for (int c = 0; c < CPT; c++) {
-            const int hy = ty + c * BY;
-            const int row = r0 + hy - H, xo = x0 + tx - H;
-            if (tx >= H && tx < BW - H && hy >= H && hy < SH - H && row < nt && xo < nx) {
-                float v = Tn[c];
-                if ((kd[c] == 1 || kd[c] == 2) && !iso) v = Tn[c] + acc[c] * (1.0f / 6.0f);
-                if (!(fabsf(v) < 1e30f)) errbits |= ERRW_NONFINITE_T;
-                Tout[(size_t)row * nx + xo] = v;
-            }
-        }
-        __syncthreads();  // shared tiles are rewritten by the next tile
-        cxt = nxt; cyt = nyt;
-    }
-    if (errbits) atomicOr(err, errbits);
-}
-
-template <class P, int BW, int BY, int CPT, int MINB>
-struct HeatWideShape {
-    static int grid_blocks;
-    static cudaError_t prepare() {
-        int dev = 0, sms = 0, per = 0;
-        cudaError_t e = cudaGetDevice(&dev);
-        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_heat_wide<P, BW, BY, CPT, MINB, true>, BW * BY, 0);
-        if (e != cudaSuccess) return e;
-        grid_blocks = sms * (per > 0 ? per : 1);
-        return cudaSuccess;
-    }
-    static cudaError_t launch(const DevParams &p, const StepBuffers &b, cudaStream_t s) {
-        constexpr int TXO = BW - 8, TYO = BY * CPT - 8;
-        const int tx = (p.nx + TXO - 1) / TXO, ty = (p.nt + TYO - 1) / TYO;
-        const int ntiles = tx * ty;
-        const int g = ntiles < grid_blocks ? ntiles : grid_blocks;
-        const bool wide = p.nx >= BW && (!(p.flags & FLAG_PERIODIC_Y) || p.nt >= BY * CPT);
-        auto k = wide ? k_heat_wide<P, BW, BY, CPT, MINB, true> : k_heat_wide<P, BW, BY, CPT, MINB, false>;
-        k<<<g, dim3(BW, BY), 0, s>>>(
-            make_fparams(p), tx, ntiles, (const typename P::tst *)b.T_in, (typename P::tst *)b.T_out,
-            (const float *)b.rho, (const float *)b.ux, (const float *)b.uy, b.step, b.err);
-        return cudaGetLastError();
-    }
-};
-template <class P, int BW, int BY, int CPT, int MINB>
-int HeatWideShape<P, BW, BY, CPT, MINB>::grid_blocks = 152;
-
-// ============================================================================
-// Heat kernel, FP32, row-strip persistent variant.  Same tiling as
-// k_heat_wide (BW columns x SH = R BY rows of cells, 4-cell halo) but thread
-// (tx, ty) owns the R vertically adjacent cells of rows R ty .. R ty + R - 1:
+// Heat kernel, FP32, row-strip persistent variant.  A block covers BW
+// columns x SH = R BY rows of cells (4-cell halo for the four RK stages, so
+// (BW - 8) x (SH - 8) outputs per tile) and loops over tiles; thread (tx, ty)
+// owns the R vertically adjacent cells of rows R ty .. R ty + R - 1:
 // their vertical neighbours are its own registers, and one stage of all R
 // cells reads 2 R + 6 words of shared memory (bank-conflict free).  Cells
 // that do not evolve (outside the domain, the Dirichlet bottom row, the top
@@ -1144,6 +914,7 @@ k_heat_rows(const FParams p, int tiles_x, int ntiles, const typename P::tst *__r
     const int tx = threadIdx.x, ty = threadIdx.y, y0 = R * ty;
     const int nx = p.nx, nt = p.nt, ns = p.ns;
     const bool py = (p.flags & FLAG_PERIODIC_Y) != 0;
+    const bool model_a = (p.flags & FLAG_MODEL_A) != 0;
     const bool iso = (p.flags & FLAG_ISOTHERMAL) != 0;
     const float tsat = p.T_sat;
     unsigned errbits = 0;
@@ -1167,10 +938,11 @@ k_heat_rows(const FParams p, int tiles_x, int ntiles, const typename P::tst *__r
             else k = (row < ns) ? HK_SOLID : HK_FLUID;
             pk |= k << (3 * c);
             const bool inT = k == HK_SOLID || k == HK_FLUID, fl = k == HK_FLUID, gh = k == HK_GHOST;
+            const bool wa = k == HK_BOTTOM && model_a;  // Model A wall row: rho of the first fluid row
             const int kt = inT ? row * nx + x : 0;                                   // T index
-            const int kf = fl ? kt - ns * nx : (gh ? (nt - ns - 1) * nx + x : 0);  // fluid index (ghost: top row)
+            const int kf = fl ? kt - ns * nx : (gh ? (nt - ns - 1) * nx + x : (wa ? x : 0));  // fluid index
             cp_async4(&sL[y0 + c][tx], Tin + kt, inT);
-            cp_async4(&sU[y0 + c][tx], rho_i + kf, fl || gh);
+            cp_async4(&sU[y0 + c][tx], rho_i + kf, fl || gh || wa);
             cp_async4(&sV[y0 + c][tx], ux_i + kf, fl);
             cp_async4(&gV[y0 + c][tx], uy_i + kf, fl);
         }
@@ -1194,7 +966,7 @@ k_heat_rows(const FParams p, int tiles_x, int ntiles, const typename P::tst *__r
             float T = Tr, l = 0.0f, rc = 1.0f;
             if (k == HK_SOLID) { l = p.lambda_s; rc = p.rho_c_s; }
             else if (k == HK_FLUID) { l = p.cv_chi * rho[c]; rc = rho[c] * p.c_v; }
-            else if (k == HK_BOTTOM) { T = bottom_theta(p, px, *stepp); l = p.lambda_s; }
+            else if (k == HK_BOTTOM) { T = bottom_theta(p, px, *stepp); l = model_a ? p.cv_chi * rho[c] : p.lambda_s; }
             else if (k == HK_GHOST) l = p.cv_chi * rho[c];
             Tn[c] = T; Tc[c] = T; irc[c] = fast_rcp(rc);
             // 1/lambda: the harmonic mean of a link is 2 / (1/l0 + 1/la)
@@ -1396,7 +1168,8 @@ k_diag_flat(const FParams p, const float *__restrict__ T, const float *__restric
             int cap, double *__restrict__ last, long long *__restrict__ stepp, double inv_nx, double inv_nfl) {
     __shared__ double sh[4][NT / 32];
     const int nx = p.nx, ns = p.ns, t = threadIdx.x;
-    const bool flux = !(p.flags & FLAG_PERIODIC_Y) && ns >= 3;
+    const bool model_a = (p.flags & FLAG_MODEL_A) != 0;  // no heater: wall flux for both
+    const bool flux = !(p.flags & FLAG_PERIODIC_Y) && (ns >= 3 || model_a);
     double v[4] = {0.0, 0.0, 0.0, 0.0};  // mass, vapour count, bottom flux, surface flux
     for (int b = t; b < nblk; b += NT) {
         v[0] += part[2 * b];
@@ -1407,11 +1180,11 @@ k_diag_flat(const FParams p, const float *__restrict__ T, const float *__restric
         for (int x = t; x < nx; x += NT) {
             const float t0 = T[x], t1 = T[nx + x], t2 = T[2 * nx + x];
             const float tu = T[(size_t)ns * nx + x], td = T[(size_t)(ns - 1) * nx + x];
-            const float lf1 = cvchi * rho[x];
-            // Eq. 36 (theta differences: T_sat cancels) and the face flux
-            const float qb = -lams * (0.5f * ((4.0f * t1 - t2) - 3.0f * t0));
-            const float lf = 2.0f * lams * lf1 * fast_rcp(lams + lf1);
+            const float lf1 = cvchi * rho[x], lw = model_a ? lf1 : lams;
+            // the face flux, and Eq. 36 (theta differences: T_sat cancels)
+            const float lf = 2.0f * lw * lf1 * fast_rcp(lw + lf1);
             const float q = -lf * (tu - td);
+            const float qb = model_a ? q : -lams * (0.5f * ((4.0f * t1 - t2) - 3.0f * t0));
             q_top[x] = (double)q;
             v[2] += (double)qb;
             v[3] += (double)q;

@@ -15,8 +15,6 @@ cudaError_t diag(const DevParams &p, const StepBuffers &b, int nblk, cudaStream_
 #define FLOWP(P, BX, BY, RY, MB)                                                                  \
     {"flowpers_" #BX "x" #BY "x" #RY "_b" #MB, FlowPersShape<P, BX, BY, RY, MB>::launch,            \
      FlowPersShape<P, BX, BY, RY, MB>::blocks, FlowPersShape<P, BX, BY, RY, MB>::prepare}
-#define HEATW(P, BW, BY, CPT, MB) \
-    {"heatwide_" #BW "x" #BY "x" #CPT, HeatWideShape<P, BW, BY, CPT, MB>::launch, HeatWideShape<P, BW, BY, CPT, MB>::prepare}
 #define HEATS(P, BW, BY, R, MB) \
     {"heatrows_" #BW "x" #BY "x" #R, HeatRowsShape<P, BW, BY, R, MB>::launch, HeatRowsShape<P, BW, BY, R, MB>::prepare}
 #define HEATV(P, TX, TY, BX, BY) \
@@ -30,10 +28,10 @@ const FlowVariant flows32[] = {
 const HeatVariant heats32[] = {
     HEATS(PolicyF32, 64, 10, 3, 1), HEATS(PolicyF32, 64, 8, 4, 1), HEATS(PolicyF32, 64, 6, 5, 1),
     HEATS(PolicyF32, 64, 7, 4, 1), HEATS(PolicyF32, 64, 9, 3, 1), HEATS(PolicyF32, 32, 8, 4, 2),
-    HEATW(PolicyF32, 64, 16, 2, 1), HEATV(PolicyF32, 32, 16, 32, 8), HEATV(PolicyF32, 64, 32, 32, 16),
+    HEATV(PolicyF32, 32, 16, 32, 8), HEATV(PolicyF32, 64, 32, 32, 16),
 };
 const FlowVariant flows16[] = {FLOWP(PolicyF16, 32, 8, 2, 2), FLOWV(PolicyF16, 32, 8, 2, 3)};
-const HeatVariant heats16[] = {HEATS(PolicyF16, 64, 10, 3, 1), HEATS(PolicyF16, 64, 8, 4, 1), HEATW(PolicyF16, 64, 16, 2, 1),
+const HeatVariant heats16[] = {HEATS(PolicyF16, 64, 10, 3, 1), HEATS(PolicyF16, 64, 8, 4, 1),
                                HEATV(PolicyF16, 32, 32, 32, 16)};
 
 const KernelSet ks32 = {"fp32", sizeof(float), sizeof(float), sizeof(float),

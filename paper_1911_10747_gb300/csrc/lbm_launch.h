@@ -8,7 +8,8 @@
 
 namespace lbmgb {
 
-enum { FLAG_PERIODIC_Y = 1, FLAG_ISOTHERMAL = 2, FLAG_FROZEN_FLOW = 4 };
+// FLAG_MODEL_A is set by the library (heater.ny_solid = 0), never by callers
+enum { FLAG_PERIODIC_Y = 1, FLAG_ISOTHERMAL = 2, FLAG_FROZEN_FLOW = 4, FLAG_MODEL_A = 8 };
 enum { TOP_WALL = 0, TOP_OUTFLOW = 1 };
 enum { BCM_SPOTS = 0, BCM_NOISE = 1, BCM_SINE = 2 };
 enum { ERRW_PSI = 1, ERRW_NONFINITE_RHO = 2, ERRW_NONFINITE_T = 4 };

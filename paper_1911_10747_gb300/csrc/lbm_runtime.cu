@@ -139,8 +139,12 @@ static int fill_params(const lbm_domain_t *d, const lbm_heater_t *ht, const lbm_
     if (d->flags & ~7) { why = "domain.flags has unknown bits"; return 0; }
     const bool py = (d->flags & LBM_PERIODIC_Y) != 0;
     if (py && ht->ny_solid != 0) { why = "periodic-y test mode needs heater.ny_solid = 0"; return 0; }
-    if (!py && ht->ny_solid < 3) { why = "heater.ny_solid must be >= 3 (bottom flux uses rows 0..2)"; return 0; }
-    if ((double)d->nx * (double)(d->ny_fluid + ht->ny_solid) > 2.0e9) { why = "domain too large for 32-bit row indexing"; return 0; }
+    const bool model_a = !py && ht->ny_solid == 0;  // Fig. 1a: no heater
+    if (!py && !model_a && ht->ny_solid < 3) {
+        why = "heater.ny_solid must be 0 (Model A) or >= 3 (bottom flux uses rows 0..2)";
+        return 0;
+    }
+    if ((double)d->nx * (double)(d->ny_fluid + ht->ny_solid + 1) > 2.0e9) { why = "domain too large for 32-bit row indexing"; return 0; }
     if (!(eo->G < 0)) { why = "eos.G must be negative (psi real for p_EOS < rho/3)"; return 0; }
     if (!(eo->a > 0 && eo->b > 0 && eo->R > 0)) { why = "eos.a, eos.b, eos.R must be positive"; return 0; }
     if (!(eo->rho_L > eo->rho_V && eo->rho_V > 0)) { why = "eos needs rho_L > rho_V > 0"; return 0; }
@@ -148,15 +152,17 @@ static int fill_params(const lbm_domain_t *d, const lbm_heater_t *ht, const lbm_
     for (int k = 0; k < 9; k++)
         if (!(d->s[k] > 0 && d->s[k] < 2)) { why = "MRT rates must lie in (0, 2)"; return 0; }
     if (!(d->c_v > 0 && d->cv_chi > 0)) { why = "c_v and cv_chi must be positive"; return 0; }
-    if (!py && !(ht->lambda_s > 0 && ht->rho_c_s > 0)) { why = "heater lambda_s and rho_c_s must be positive"; return 0; }
+    if (!py && !model_a && !(ht->lambda_s > 0 && ht->rho_c_s > 0)) { why = "heater lambda_s and rho_c_s must be positive"; return 0; }
     if (bc->mode < 0 || bc->mode > 2) { why = "bc.mode invalid"; return 0; }
     if (bc->n_spots < 0 || bc->n_spots > 8) { why = "bc.n_spots must be in 0..8"; return 0; }
     if (bc->mode == LBM_BC_SINE && !(bc->sine_wavelength > 0)) { why = "bc.sine_wavelength must be positive"; return 0; }
     p.nx = d->nx;
     p.nf = d->ny_fluid;
-    p.ns = ht->ny_solid;
+    // Model A: temperature row 0 is the wall's Dirichlet row (T_b), coupled to
+    // the first fluid row with the fluid's conductivity
+    p.ns = model_a ? 1 : ht->ny_solid;
     p.nt = p.ns + p.nf;
-    p.flags = d->flags;
+    p.flags = d->flags | (model_a ? FLAG_MODEL_A : 0);
     p.top_mode = d->top_mode;
     p.bc_mode = bc->mode;
     p.liquid_rows = d->liquid_rows;
@@ -787,7 +793,8 @@ int lbm_device_bytes(const lbm_domain_t *domain, const lbm_heater_t *heater, con
     if (!ks) return fail(nullptr, LBM_E_INVAL, "opts.precision invalid");
     if (domain->nx < 1 || domain->ny_fluid < 1 || heater->ny_solid < 0) return fail(nullptr, LBM_E_INVAL, "bad sizes");
     const uint64_t nfl = (uint64_t)domain->nx * domain->ny_fluid;
-    const uint64_t ntl = (uint64_t)domain->nx * (domain->ny_fluid + heater->ny_solid);
+    const bool model_a = heater->ny_solid == 0 && !(domain->flags & LBM_PERIODIC_Y);
+    const uint64_t ntl = (uint64_t)domain->nx * (domain->ny_fluid + (model_a ? 1 : heater->ny_solid));
     const uint64_t cap = opts->series_capacity > 0 ? (uint64_t)opts->series_capacity : 4096;
     // populations x2, temperature x2, moments x3, per-column arrays, per-block
     // partials (at most one block per 32 sites), series ring, small words

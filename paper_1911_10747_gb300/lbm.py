@@ -202,7 +202,7 @@ class Run:
         rc = L.lbm_create(*[C.byref(s) for s in self._structs], C.byref(h))
         _check(rc, None, "lbm_create")
         self._h = h
-        self.nx, self.nf, self.nt = cfg.nx, cfg.nf, cfg.ns + cfg.nf
+        self.nx, self.nf, self.nt = cfg.nx, cfg.nf, cfg.t_rows
 
     def close(self):
         if getattr(self, "_h", None):
@@ -275,7 +275,7 @@ class Run:
             if fa is not None and fa.size != 9 * self.nf * self.nx:
                 raise ValueError("f must have 9 * nf * nx values")
             if ta is not None and ta.size != self.nt * self.nx:
-                raise ValueError("T must have (ns + nf) * nx values")
+                raise ValueError("T must have t_rows * nx values")
             fp = None if fa is None else fa.ctypes.data
             tp = None if ta is None else ta.ctypes.data
             keep = (fa, ta)
@@ -432,7 +432,7 @@ class Server:
         cfg = self._cfg[rid]
         diag = np.zeros(4)
         rho = np.empty((cfg.nf, cfg.nx)) if fields else None
-        T = np.empty((cfg.ns + cfg.nf, cfg.nx)) if fields else None
+        T = np.empty((cfg.t_rows, cfg.nx)) if fields else None
         self._check(load().lbm_server_result(self._s, int(rid), diag.ctypes.data_as(_D),
                                              None if rho is None else rho.ctypes.data_as(_D),
                                              None if T is None else T.ctypes.data_as(_D)), "lbm_server_result")

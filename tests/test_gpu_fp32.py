@@ -88,6 +88,17 @@ def test_fp32_outflow_ragged_top_tile():
     assert errs["rho"] < 1e-4 and errs["T"] < 1e-5, errs
 
 
+def test_fp32_model_a_error_report():
+    """Model A (no heater) through the FP32 kernels, against the oracle."""
+    cfg = W.small_parity(precision="fp32").replace(ns=0, rho_mean=2.42)
+    g, o = run_both(cfg, 200)
+    errs = field_errors(g, o)
+    print("fp32 model A 200-step errors", errs)
+    assert errs["rho"] < 1e-3 and errs["T"] < 1e-5, errs
+    d = o.diagnostics()
+    assert g.wall_heat_flux() == pytest.approx(d["q_bottom"], rel=1e-3)
+
+
 @pytest.mark.parametrize("tb", [0.96, 1.0])
 def test_fp32_long_run_statistics_match_fp64(tb):
     """20,000 steps of the 64 x 96 boiling case: the time averages of the

@@ -74,6 +74,9 @@ def test_fp64_parity_computed_mean_density():
          c_w_spot=(-0.9, -0.8, -0.7), top_mode="outflow"),
     dict(nx=33, nf=40, ns=9, liquid_rows=12, bc_mode="sine", sine_t0=3, sine_t1=40, sine_wavelength=33.0,
          spot_x=(), c_w_spot=()),
+    # model A (Fig. 1a): no heater, T_b on the wall row
+    dict(ns=0),
+    dict(nx=45, nf=40, ns=0, liquid_rows=13, bc_mode="noise", spot_x=(), c_w_spot=(), T_b_over_Tc=1.0),
 ])
 def test_fp64_parity_ragged_domains_and_bc_modes(kw):
     cfg = W.small_parity().replace(rho_mean=2.3, **kw)
