@@ -296,6 +296,24 @@ def measure_serving(lbm, W, n_requests, step_scale, load=0.8):
             "capacity_mlups": {k: v / 1e6 for k, v in rate.items()}}
 
 
+def measure_wetting(steps):
+    """Contact angles of sessile drops at the library's wettability
+    coefficients (the three nucleate-spot values and the base), stepped
+    together in one batch: the calibration check of Eq. 14's c_w."""
+    from paper_1911_10747_gb300 import calibration as K
+    from paper_1911_10747_gb300 import workloads as W
+    cws = list(W.DEFAULT_CW_SPOTS) + [W.DEFAULT_CW_BASE]
+    t0 = time.perf_counter()
+    table = K.measure(cws, steps=steps)
+    dt = time.perf_counter() - t0
+    return {"c_w": cws, "target_deg": [105.0, 115.0, 125.0, 55.0],
+            "theta_deg": [None if r["theta_deg"] is None else round(r["theta_deg"], 2) for r in table],
+            "mass_drift": [r.get("mass_drift") for r in table],
+            "setting": f"200x100 fluid, drop radius 30, isothermal at T_sat, g = 0, FP32, {steps} steps, "
+                       "4 runs in one batch; 55 deg is outside the stable range (base c_w = -1.6)",
+            "seconds": dt}
+
+
 def measure_chf(lbm, W, steps):
     """Boiling curve on a 256 x 384 domain over 16 heater rows (constant
     bottom with nucleate spots): time-averaged heater-bottom flux Q'' over
@@ -480,6 +498,10 @@ def run_ours(args):
     if not args.no_sweep:
         sweep = measure_sweep(lbm, W, torch, dev, args.sweep_steps)
 
+    wetting = None
+    if rank == 0 and not args.no_wetting:
+        wetting = measure_wetting(args.wetting_steps)
+
     chf = None
     if args.chf:
         chf = measure_chf(lbm, W, args.chf_steps)
@@ -520,6 +542,7 @@ def run_ours(args):
             "sweep": sweep,
             "serve": serve,
             "chf": chf,
+            "wetting": wetting,
         }
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -541,6 +564,8 @@ def main():
     ap.add_argument("--sweep-steps", type=int, default=200)
     ap.add_argument("--flow-variant", default="", help="pin the flow kernel variant (no autotuning)")
     ap.add_argument("--heat-variant", default="", help="pin the heat kernel variant (no autotuning)")
+    ap.add_argument("--no-wetting", action="store_true", help="skip the contact-angle check of the c_w values")
+    ap.add_argument("--wetting-steps", type=int, default=30000)
     ap.add_argument("--chf", action="store_true", help="also measure the FP32 vs FP64 boiling curve")
     ap.add_argument("--chf-steps", type=int, default=20000)
     ap.add_argument("--serve", action="store_true", help="also measure the request loop")

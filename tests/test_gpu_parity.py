@@ -150,3 +150,21 @@ def test_numerical_fault_is_reported():
     # a fresh run on the same device still works
     h = lbm.Run(cfg).step(2)
     h.sync()
+
+
+def test_fp64_parity_sessile_drop_from_set_state():
+    """The wettability-calibration setting: an isothermal, gravity-free drop
+    on the bottom wall, loaded through lbm_set_state on both sides."""
+    from paper_1911_10747_gb300 import calibration as K
+    cfg = K.drop_config(-1.1, nx=72, nf=40, precision="fp64")
+    f, T = K.drop_state(cfg, 14.0)
+    g = lbm.Run(cfg)
+    g.set_state(f, T, step=0)
+    o = O.OracleRun(cfg)
+    o.set_f(f)
+    o.set_T(T)
+    g.step(120)
+    g.sync()
+    o.step(120)
+    errs = field_errors(g, o)
+    assert all(v <= TOL64 for v in errs.values()), errs
