@@ -314,6 +314,29 @@ def measure_wetting(steps):
             "seconds": dt}
 
 
+def measure_validation():
+    """The paper's validation cases on the GPU path: the Laplace test (surface
+    tension), film boiling against Berenson (Eq. 34 vs Eq. 35) for three wall
+    wettabilities, and the storage-precision report (coexistence densities,
+    film-boiling Nu, mass drift in FP64 / FP32 / FP16 storage)."""
+    from paper_1911_10747_gb300 import validation as V
+    t0 = time.perf_counter()
+    lap = V.laplace([16, 20, 25, 30, 36], precision="fp64")
+    dp_max = max(d["dp"] for d in lap["drops"])
+    film = {}
+    for cw in (-1.6, -1.2, -0.465):
+        fb = V.film_boiling(lap["sigma"], precision="fp32", c_w=cw)
+        film[f"c_w={cw}"] = {k: fb[k] for k in ("nu_lbm_surface", "nu_lbm_bottom", "nu_berenson", "rel_dev_surface",
+                                                 "T_w_over_Tc", "rho_first_fluid_row")}
+    prec = V.precision_report(lap["sigma"])
+    return {"laplace": {"sigma": lap["sigma"], "r2": lap["r2"], "intercept_over_max_dp": lap["intercept"] / dp_max,
+                        "setting": lap["setting"]},
+            "film_boiling": {"setting": f"model B {fb['domain']}, T_b = 1.27 Tc, sine 5 < t* < 24.98, "
+                                        f"averages over 41.63 < t* < 60 ({fb['steps']} steps), FP32",
+                             "lambda_d": fb["lambda_d"], "t0": fb["t0"], "by_wall": film},
+            "precision": prec, "seconds": time.perf_counter() - t0}
+
+
 def measure_chf(lbm, W, steps):
     """Boiling curve on a 256 x 384 domain over 16 heater rows (constant
     bottom with nucleate spots): time-averaged heater-bottom flux Q'' over
@@ -501,6 +524,9 @@ def run_ours(args):
     wetting = None
     if rank == 0 and not args.no_wetting:
         wetting = measure_wetting(args.wetting_steps)
+    validation = None
+    if rank == 0 and not args.no_validation:
+        validation = measure_validation()
 
     chf = None
     if args.chf:
@@ -543,6 +569,7 @@ def run_ours(args):
             "serve": serve,
             "chf": chf,
             "wetting": wetting,
+            "validation": validation,
         }
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -565,6 +592,7 @@ def main():
     ap.add_argument("--flow-variant", default="", help="pin the flow kernel variant (no autotuning)")
     ap.add_argument("--heat-variant", default="", help="pin the heat kernel variant (no autotuning)")
     ap.add_argument("--no-wetting", action="store_true", help="skip the contact-angle check of the c_w values")
+    ap.add_argument("--no-validation", action="store_true", help="skip the Laplace / film-boiling / precision cases")
     ap.add_argument("--wetting-steps", type=int, default=30000)
     ap.add_argument("--chf", action="store_true", help="also measure the FP32 vs FP64 boiling curve")
     ap.add_argument("--chf-steps", type=int, default=20000)

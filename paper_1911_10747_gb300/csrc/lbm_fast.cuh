@@ -104,18 +104,59 @@ __device__ __forceinline__ float psi_fast(const FParams &q, float rho, float T, 
 // populations (L2 hits).  Rows outside the fluid hold psi = 0 (walls add
 // their pull through F_ads) or, for an open top, the psi of the top row.
 // ============================================================================
+// Population stores.  FP32: plain.  FP16 storage rounds stochastically: a
+// dither drawn uniformly from the 13 float mantissa bits a half drops is
+// added to the magnitude, which is then truncated (Connolly, Higham and Mary,
+// SIAM J. Sci. Comput. 43 (2021), "Stochastic rounding and its probabilistic
+// backward error analysis").  Expected stored value = exact value, so the
+// per-step rounding errors no longer add up to a drift of the mass; the
+// dither comes from an xorshift32 stream seeded per site and step (values
+// in the half-subnormal range keep round-to-nearest).
+struct PopDither {
+    uint32_t s;
+    __device__ __forceinline__ uint32_t next() {
+        s ^= s << 13;
+        s ^= s >> 17;
+        s ^= s << 5;
+        return s;
+    }
+};
+template <class S>
+__device__ __forceinline__ PopDither pop_dither(const FParams &p, long long n, int k) {
+    PopDither d{1u};
+    if constexpr (sizeof(S) == 2) {
+        const uint64_t gam = 0x9E3779B97F4A7C15ULL;
+        uint64_t h = smix((p.seed ^ 0x5bd1e995ULL) + gam);
+        h = smix((h ^ (uint64_t)n) + gam);
+        h = smix((h ^ (uint64_t)(unsigned)k) + gam);
+        d.s = (uint32_t)(h >> 32) | 1u;
+    }
+    return d;
+}
+__device__ __forceinline__ void st_pop(float *q, float v, PopDither &) { *q = v; }
+__device__ __forceinline__ void st_pop(__half *q, float v, PopDither &d) {
+    const uint32_t b = __float_as_uint(v), e = (b >> 23) & 0xffu;
+    if (e >= 113u && e < 142u) {  // |v| in the normal half range [2^-14, 2^15)
+        const uint32_t m = ((b & 0x7fffffffu) + (d.next() & 0x1fffu)) & ~0x1fffu;
+        *q = __float2half_rz(__uint_as_float((b & 0x80000000u) | m));  // exact
+    } else {
+        *q = __float2half_rn(v);
+    }
+}
+
 template <class P, int BX, int BY, int RY, int MINB>
 __global__ void __launch_bounds__(BX *BY, MINB)
 k_flow_fast(const FParams p, const typename P::fst *__restrict__ fin, typename P::fst *__restrict__ fout,
             const typename P::tst *__restrict__ Tin, float *__restrict__ rho_o, float *__restrict__ ux_o,
             float *__restrict__ uy_o, const double *__restrict__ cw, double *__restrict__ part,
-            unsigned *__restrict__ err) {
+            unsigned *__restrict__ err, const long long *__restrict__ stepp) {
     using S = typename P::fst;
     constexpr int TX = BX, TY = BY * RY, SW = TX + 2, SH = TY + 2, NT = BX * BY;
     __shared__ float s_psi[SH * SW];
     __shared__ float s_red[2][NT / 32];
 
     const int nx = p.nx, nf = p.nf;
+    const long long nstep = sizeof(S) == 2 ? *stepp : 0;  // keys the FP16 store dither
     const size_t plane = (size_t)nf * nx;
     const bool py = (p.flags & FLAG_PERIODIC_Y) != 0;
     const bool frozen = (p.flags & FLAG_FROZEN_FLOW) != 0;
@@ -190,6 +231,7 @@ k_flow_fast(const FParams p, const typename P::fst *__restrict__ fin, typename P
         const int x = x0 + lx, y = y0 + ly;
         if (x >= nx || y >= nf) continue;
         const size_t k = (size_t)y * nx + x;
+        PopDither dz = pop_dither<S>(p, nstep, (int)k);
         const float d = dd[r];
         const float rho = d + rho0;
         if (!(fabsf(rho) < 1e30f)) errbits |= ERRW_NONFINITE_RHO;
@@ -197,7 +239,7 @@ k_flow_fast(const FParams p, const typename P::fst *__restrict__ fin, typename P
         nvap += (rho < p.vap_threshold) ? 1.0f : 0.0f;
         if (frozen) {
             #pragma unroll
-            for (int i = 0; i < 9; i++) st_as(fout + i * plane + k, g[r][i]);
+            for (int i = 0; i < 9; i++) st_pop(fout + i * plane + k, g[r][i], dz);
             rho_o[k] = rho;
             ux_o[k] = 0.0f;
             uy_o[k] = 0.0f;
@@ -283,33 +325,33 @@ k_flow_fast(const FParams p, const typename P::fst *__restrict__ fin, typename P
         // Eq. 8, push; halfway bounce-back at the heater and the top wall
         S *o = fout;
         const size_t ro = (size_t)y * nx;
-        st_as(o + ro + x, fo0);
-        st_as(o + plane + ro + xp, fo1);
-        st_as(o + 3 * plane + ro + xm, fo3);
+        st_pop(o + ro + x, fo0, dz);
+        st_pop(o + plane + ro + xp, fo1, dz);
+        st_pop(o + 3 * plane + ro + xm, fo3, dz);
         const size_t ru = (size_t)(py && y == nf - 1 ? 0 : y + 1) * nx;
         const size_t rd = (size_t)(py && y == 0 ? nf - 1 : y - 1) * nx;
         if (!top) {
-            st_as(o + 2 * plane + ru + x, fo2);
-            st_as(o + 5 * plane + ru + xp, fo5);
-            st_as(o + 6 * plane + ru + xm, fo6);
+            st_pop(o + 2 * plane + ru + x, fo2, dz);
+            st_pop(o + 5 * plane + ru + xp, fo5, dz);
+            st_pop(o + 6 * plane + ru + xm, fo6, dz);
         } else if (!outflow) {
-            st_as(o + 4 * plane + ro + x, fo2);
-            st_as(o + 7 * plane + ro + x, fo5);
-            st_as(o + 8 * plane + ro + x, fo6);
+            st_pop(o + 4 * plane + ro + x, fo2, dz);
+            st_pop(o + 7 * plane + ro + x, fo5, dz);
+            st_pop(o + 8 * plane + ro + x, fo6, dz);
         }
         if (!bot) {
-            st_as(o + 4 * plane + rd + x, fo4);
-            st_as(o + 7 * plane + rd + xm, fo7);
-            st_as(o + 8 * plane + rd + xp, fo8);
+            st_pop(o + 4 * plane + rd + x, fo4, dz);
+            st_pop(o + 7 * plane + rd + xm, fo7, dz);
+            st_pop(o + 8 * plane + rd + xp, fo8, dz);
         } else {
-            st_as(o + 2 * plane + ro + x, fo4);
-            st_as(o + 5 * plane + ro + x, fo7);
-            st_as(o + 6 * plane + ro + x, fo8);
+            st_pop(o + 2 * plane + ro + x, fo4, dz);
+            st_pop(o + 5 * plane + ro + x, fo7, dz);
+            st_pop(o + 6 * plane + ro + x, fo8, dz);
         }
         if (top && outflow) {
-            st_as(o + 4 * plane + ro + x, fo4);
-            st_as(o + 7 * plane + ro + xm, fo7);
-            st_as(o + 8 * plane + ro + xp, fo8);
+            st_pop(o + 4 * plane + ro + x, fo4, dz);
+            st_pop(o + 7 * plane + ro + xm, fo7, dz);
+            st_pop(o + 8 * plane + ro + xp, fo8, dz);
         }
     }
     // per-block mass and vapour count: FP32 inside the block, FP64 across blocks
@@ -336,13 +378,14 @@ __global__ void __launch_bounds__(BX *BY, MINB)
 k_flow_pers(const FParams p, int tiles_x, int ntiles, const typename P::fst *__restrict__ fin, typename P::fst *__restrict__ fout,
             const typename P::tst *__restrict__ Tin, float *__restrict__ rho_o, float *__restrict__ ux_o,
             float *__restrict__ uy_o, const double *__restrict__ cw, double *__restrict__ part,
-            unsigned *__restrict__ err) {
+            unsigned *__restrict__ err, const long long *__restrict__ stepp) {
     using S = typename P::fst;
     constexpr int TX = BX, TY = BY * RY, SW = TX + 2, SH = TY + 2, NT = BX * BY;
     __shared__ float s_psi[SH * SW];
     __shared__ float s_red[2][NT / 32];
 
     const int nx = p.nx, nf = p.nf;
+    const long long nstep = sizeof(S) == 2 ? *stepp : 0;  // keys the FP16 store dither
     const size_t plane = (size_t)nf * nx;
     // per-plane base pointers (uniform); site offsets below are 32-bit (the
     // runtime rejects domains of more than 2e9 sites, so one plane indexes in 31 bits)
@@ -471,6 +514,7 @@ k_flow_pers(const FParams p, int tiles_x, int ntiles, const typename P::fst *__r
         const int x = x0 + lx, y = y0 + ly;
         if (x >= nx || y >= nf) continue;
         const int k = y * nx + x;
+        PopDither dz = pop_dither<S>(p, nstep, (int)k);
         const float d = dd[r];
         const float rho = d + rho0;
         if (!(fabsf(rho) < 1e30f)) errbits |= ERRW_NONFINITE_RHO;
@@ -478,7 +522,7 @@ k_flow_pers(const FParams p, int tiles_x, int ntiles, const typename P::fst *__r
         nvap += (rho < p.vap_threshold) ? 1.0f : 0.0f;
         if (frozen) {
             #pragma unroll
-            for (int i = 0; i < 9; i++) st_as(oplane[i] + k, g[r][i]);
+            for (int i = 0; i < 9; i++) st_pop(oplane[i] + k, g[r][i], dz);
             rho_o[k] = rho;
             ux_o[k] = 0.0f;
             uy_o[k] = 0.0f;
@@ -566,31 +610,31 @@ k_flow_pers(const FParams p, int tiles_x, int ntiles, const typename P::fst *__r
         const int dxp = xp - x, dxm = xm - x;
         const int kn = (py && y == nf - 1) ? x : k + nx;      // row above
         const int ks_ = (py && y == 0) ? (nf - 1) * nx + x : k - nx;  // row below
-        st_as(oplane[0] + k, fo0);
-        st_as(oplane[1] + k + dxp, fo1);
-        st_as(oplane[3] + k + dxm, fo3);
+        st_pop(oplane[0] + k, fo0, dz);
+        st_pop(oplane[1] + k + dxp, fo1, dz);
+        st_pop(oplane[3] + k + dxm, fo3, dz);
         if (!top) {
-            st_as(oplane[2] + kn, fo2);
-            st_as(oplane[5] + kn + dxp, fo5);
-            st_as(oplane[6] + kn + dxm, fo6);
+            st_pop(oplane[2] + kn, fo2, dz);
+            st_pop(oplane[5] + kn + dxp, fo5, dz);
+            st_pop(oplane[6] + kn + dxm, fo6, dz);
         } else if (!outflow) {
-            st_as(oplane[4] + k, fo2);
-            st_as(oplane[7] + k, fo5);
-            st_as(oplane[8] + k, fo6);
+            st_pop(oplane[4] + k, fo2, dz);
+            st_pop(oplane[7] + k, fo5, dz);
+            st_pop(oplane[8] + k, fo6, dz);
         }
         if (!bot) {
-            st_as(oplane[4] + ks_, fo4);
-            st_as(oplane[7] + ks_ + dxm, fo7);
-            st_as(oplane[8] + ks_ + dxp, fo8);
+            st_pop(oplane[4] + ks_, fo4, dz);
+            st_pop(oplane[7] + ks_ + dxm, fo7, dz);
+            st_pop(oplane[8] + ks_ + dxp, fo8, dz);
         } else {
-            st_as(oplane[2] + k, fo4);
-            st_as(oplane[5] + k, fo7);
-            st_as(oplane[6] + k, fo8);
+            st_pop(oplane[2] + k, fo4, dz);
+            st_pop(oplane[5] + k, fo7, dz);
+            st_pop(oplane[6] + k, fo8, dz);
         }
         if (top && outflow) {
-            st_as(oplane[4] + k, fo4);
-            st_as(oplane[7] + k + dxm, fo7);
-            st_as(oplane[8] + k + dxp, fo8);
+            st_pop(oplane[4] + k, fo4, dz);
+            st_pop(oplane[7] + k + dxm, fo7, dz);
+            st_pop(oplane[8] + k + dxp, fo8, dz);
         }
     }
     __syncthreads();  // s_psi is rewritten by the next tile
@@ -823,7 +867,7 @@ struct FlowFastShape {
     static cudaError_t launch(const DevParams &p, const StepBuffers &b, cudaStream_t s) {
         k_flow_fast<P, BX, BY, RY, MINB><<<grid(p), dim3(BX, BY), 0, s>>>(
             make_fparams(p), (const typename P::fst *)b.f_in, (typename P::fst *)b.f_out, (const typename P::tst *)b.T_in,
-            (float *)b.rho, (float *)b.ux, (float *)b.uy, b.cw, b.part, b.err);
+            (float *)b.rho, (float *)b.ux, (float *)b.uy, b.cw, b.part, b.err, b.step);
         return cudaGetLastError();
     }
 };
@@ -847,7 +891,7 @@ struct FlowPersShape {
         auto k = wide ? k_flow_pers<P, BX, BY, RY, MINB, true> : k_flow_pers<P, BX, BY, RY, MINB, false>;
         k<<<blocks(p), dim3(BX, BY), 0, s>>>(
             make_fparams(p), (p.nx + BX - 1) / BX, tiles(p), (const typename P::fst *)b.f_in, (typename P::fst *)b.f_out,
-            (const typename P::tst *)b.T_in, (float *)b.rho, (float *)b.ux, (float *)b.uy, b.cw, b.part, b.err);
+            (const typename P::tst *)b.T_in, (float *)b.rho, (float *)b.ux, (float *)b.uy, b.cw, b.part, b.err, b.step);
         return cudaGetLastError();
     }
 };

@@ -384,9 +384,13 @@ static int launch_step(lbm_run *h, bool timed, bool wait_prev_diag = true, bool 
     StepBuffers b = buffers(h, h->parity);
     cudaError_t e;
     cudaEvent_t eh = capturing ? h->cev_heat : h->ev_heat, ed = capturing ? h->cev_diag : h->ev_diag;
+    // The heat kernel reads the step counter the previous diagnostics kernel
+    // advanced, so it waits for it; the flow kernel overlaps that kernel,
+    // except with FP16 storage, whose store dither is keyed by the counter.
+    const int first_reader = h->ks->f_elem == 2 ? 0 : 1;
     for (int k = 0; k < 3; k++) {
         cudaStream_t st = (k == 2 && !h->timing) ? h->dstream : h->stream;
-        if (k == 1 && wait_prev_diag) CK(h, cudaStreamWaitEvent(h->stream, ed, 0));
+        if (k == first_reader && wait_prev_diag) CK(h, cudaStreamWaitEvent(h->stream, ed, 0));
         if (k == 2 && !h->timing) {
             CK(h, cudaEventRecord(eh, h->stream));
             CK(h, cudaStreamWaitEvent(h->dstream, eh, 0));

@@ -1,0 +1,246 @@
+"""Paper validation cases run on the library: the Laplace test that gives the
+surface tension, and film boiling against Berenson's correlation (Sec. 3.2,
+Eq. 29-36).  Host code only -- the runs are stepped by the CUDA path; this
+file builds their states, evaluates the closed forms the paper compares
+with, and reduces the fields and the diagnostics series.
+
+Units are lattice units (delta_x = delta_t = 1).  Readings of the printed
+equations:
+  * Eq. 30 as printed lacks the pi that Eq. 29 and Eq. 34 carry; lambda_d =
+    2 pi sqrt(3) l0 is used (Eq. 29 with Eq. 31).
+  * Eq. 33 prints lambda_V to the first power inside the quarter power;
+    Berenson's correlation, and the step from Eq. 33 to Eq. 34 the paper
+    makes, need lambda_V cubed there, which is what berenson_h uses.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from . import workloads as W
+
+_WL = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+
+
+# ---- closed forms -------------------------------------------------------------
+
+def critical_temperature(a: float, b: float, R: float) -> float:
+    """Tc of the Peng-Robinson fluid, Tc = 0.0778 a / (0.45724 b R) (Sec. 2.1)."""
+    return (0.0778 * a) / (0.45724 * b * R)
+
+
+def pr_pressure(rho, T, a: float, b: float, R: float, omega: float):
+    """Peng-Robinson pressure, Eq. 13; the pseudopotential pressure
+    rho/3 + G psi^2 / 2 equals it by construction of psi (Eq. 12)."""
+    tc = critical_temperature(a, b, R)
+    kap = 0.37464 + 1.54226 * omega - 0.26992 * omega * omega
+    phi = (1.0 + kap * (1.0 - np.sqrt(T / tc))) ** 2
+    rho = np.asarray(rho, dtype=float)
+    return rho * R * T / (1.0 - b * rho) - a * phi * rho * rho / (1.0 + 2.0 * b * rho - (b * rho) ** 2)
+
+
+def capillary_length(sigma: float, g: float, drho: float) -> float:
+    """l0 = sqrt(sigma / (g (rho_L - rho_V))), Eq. 31."""
+    return math.sqrt(sigma / (g * drho))
+
+
+def taylor_wavelength(sigma: float, g: float, drho: float) -> float:
+    """Most dangerous Taylor wavelength, Eq. 29."""
+    return 2.0 * math.pi * math.sqrt(3.0 * sigma / (g * drho))
+
+
+def characteristic_time(sigma: float, g: float, drho: float) -> float:
+    """t0 = sqrt(l0 / g), Eq. 32."""
+    return math.sqrt(capillary_length(sigma, g, drho) / g)
+
+
+def berenson_h(sigma, g, rho_L, rho_V, h_fg, c_vV, lam_V, mu_V, dT):
+    """Film-boiling heat-transfer coefficient of Berenson, Eq. 33, with
+    h'_fg = h_fg + C_V,V dT / 2 (and lambda_V cubed, see the module note)."""
+    drho = rho_L - rho_V
+    hp = h_fg + 0.5 * c_vV * dT
+    return 0.425 * (lam_V ** 3 * g * rho_V * drho * hp / (mu_V * dT)) ** 0.25 * (sigma / (g * drho)) ** -0.125
+
+
+def berenson_nu(sigma, g, rho_L, rho_V, h_fg, c_vV, lam_V, mu_V, dT):
+    """Space-averaged Nusselt number of Berenson's correlation, Eq. 34."""
+    drho = rho_L - rho_V
+    hp = h_fg + 0.5 * c_vV * dT
+    return (0.425 * 2.0 * math.sqrt(3.0) * math.pi * (g * rho_V * drho * hp / (lam_V * mu_V * dT)) ** 0.25
+            * (sigma / (g * drho)) ** 0.375)
+
+
+def nu_lbm(q_mean, T_w, T_sat, lam_V, lambda_d):
+    """Eq. 35: Nu = lambda_d / (T_w - T_sat) / lambda_V * (space-averaged Q)."""
+    return lambda_d / (T_w - T_sat) / lam_V * q_mean
+
+
+# ---- Laplace test ---------------------------------------------------------------
+
+def laplace_config(n: int, precision: str = "fp64") -> W.RunConfig:
+    """Periodic n x n box at T_sat, no gravity, no walls (the drop's own
+    test case)."""
+    return W.periodic_box(n, n, liquid_rows=0, init_noise=0.0, precision=precision)
+
+
+def disc_density(cfg: W.RunConfig, radius: float, width: float = 4.0) -> np.ndarray:
+    y, x = np.mgrid[0:cfg.nf, 0:cfg.nx].astype(float)
+    r = np.hypot(x - (cfg.nx - 1) / 2.0, y - (cfg.nf - 1) / 2.0)
+    return cfg.rho_V + 0.5 * (cfg.rho_L - cfg.rho_V) * (1.0 - np.tanh(2.0 * (r - radius) / width))
+
+
+def laplace(radii, n: int = 128, steps: int = 20000, precision: str = "fp64") -> dict:
+    """Drops of the given radii stepped together; for each the equivalent
+    radius (from the liquid area, rho between the inner and the outer bulk
+    value) and the pressure jump p_EOS(rho_in) - p_EOS(rho_out); sigma is
+    the least-squares slope of dp against 1/R (with an intercept)."""
+    from . import lbm
+    cfg = laplace_config(n, precision)
+    tc = critical_temperature(cfg.a, cfg.b, cfg.R)
+    T = cfg.T_sat_over_Tc * tc
+    runs = []
+    for R0 in radii:
+        r = lbm.Run(cfg)
+        rho = disc_density(cfg, R0)
+        r.set_state(_WL[:, None, None] * rho[None], np.full((cfg.t_rows, cfg.nx), T), step=0)
+        runs.append(r)
+    batch = lbm.Batch(runs)
+    batch.step(steps)
+    batch.sync()
+    rows = []
+    c = (n - 1) // 2
+    for R0, r in zip(radii, runs):
+        rho = r.fields(("rho",))["rho"]
+        rin = float(rho[c - 1:c + 2, c - 1:c + 2].mean())
+        rout = float(np.mean([rho[0, 0], rho[0, -1], rho[-1, 0], rho[-1, -1]]))
+        area = float(np.sum((rho - rout) / (rin - rout)))
+        Req = math.sqrt(area / math.pi)
+        dp = float(pr_pressure(rin, T, cfg.a, cfg.b, cfg.R, cfg.omega) - pr_pressure(rout, T, cfg.a, cfg.b, cfg.R, cfg.omega))
+        rows.append({"R0": R0, "R": Req, "rho_in": rin, "rho_out": rout, "dp": dp})
+    batch.close()
+    inv = np.array([1.0 / q["R"] for q in rows])
+    dp = np.array([q["dp"] for q in rows])
+    A = np.column_stack([inv, np.ones_like(inv)])
+    (sigma, icpt), res, *_ = np.linalg.lstsq(A, dp, rcond=None)
+    fit = A @ np.array([sigma, icpt])
+    r2 = 1.0 - float(np.sum((dp - fit) ** 2) / np.sum((dp - dp.mean()) ** 2))
+    return {"sigma": float(sigma), "intercept": float(icpt), "r2": r2, "drops": rows,
+            "setting": f"{n}x{n} periodic box at T_sat, {steps} steps, {precision}"}
+
+
+# ---- film boiling (Sec. 3.2) ----------------------------------------------------
+
+def film_boiling_config(sigma: float, g: float = 5e-5, precision: str = "fp32", T_b_over_Tc: float = 1.27,
+                        seed: int = 7) -> W.RunConfig:
+    """Model B sized by lambda_d of Eq. 29: fluid 2 lambda_d x 1.5 lambda_d,
+    heater 0.15 lambda_d, liquid in the lower half of the fluid; constant
+    T_b with the sine of Sec. 3.2 (0.02 Tc, wavelength lambda_d) between
+    t* = 5 and t* = 24.98 (t* = t / t0, Eq. 32)."""
+    base = W.small_parity(precision=precision)
+    drho = base.rho_L - base.rho_V
+    ld = taylor_wavelength(sigma, g, drho)
+    t0 = characteristic_time(sigma, g, drho)
+    nx, nf, ns = int(round(2 * ld)), int(round(1.5 * ld)), max(3, int(round(0.15 * ld)))
+    return base.replace(nx=nx, nf=nf, ns=ns, liquid_rows=nf // 2, g=g, rho_mean=0.0, bc_mode="sine",
+                        spot_x=(), c_w_spot=(), T_b_over_Tc=T_b_over_Tc, sine_amp_over_Tc=0.02,
+                        sine_wavelength=ld, sine_t0=int(round(5.0 * t0)), sine_t1=int(round(24.98 * t0)),
+                        lambda_s=16.25, rho_c_s=3 * base.rho_L * base.c_v, seed=seed)
+
+
+def film_boiling(sigma: float, h_fg: float = 0.58, t_end_star: float = 60.0, g: float = 5e-5,
+                 precision: str = "fp32", sample_every: int = 100, T_b_over_Tc: float = 1.27,
+                 c_w: float | None = None) -> dict:
+    """Run the film-boiling case to t* = t_end_star and compare Eq. 35 with
+    Eq. 34.  T_w is the space- and time-averaged temperature of the heater's
+    top row and Q the space-averaged heat flux, both averaged over
+    t* > 41.63 (Sec. 3.2); Q is reported at the heater bottom (Eq. 36) and
+    through the heater surface."""
+    from . import lbm
+    cfg = film_boiling_config(sigma, g=g, precision=precision, T_b_over_Tc=T_b_over_Tc)
+    if c_w is not None:
+        cfg = cfg.replace(c_w_base=c_w)
+    drho = cfg.rho_L - cfg.rho_V
+    ld = taylor_wavelength(sigma, g, drho)
+    t0 = characteristic_time(sigma, g, drho)
+    n_end = int(round(t_end_star * t0))
+    n_avg = int(round(41.63 * t0))
+    tc = critical_temperature(cfg.a, cfg.b, cfg.R)
+    T_sat = cfg.T_sat_over_Tc * tc
+    r = lbm.Run(cfg, series_capacity=n_end + 8)
+    tw = []
+    done = 0
+    while done < n_end:
+        k = min(sample_every, n_end - done)
+        r.step(k)
+        done += k
+        if done > n_avg:
+            T = r.fields(("T",))["T"]
+            tw.append(float(T[cfg.ns - 1].mean()))
+    r.sync()
+    ser = r.series(0, n_end)
+    rho_wall = float(r.fields(("rho",))["rho"][0].mean())
+    lam_V = cfg.rho_V * cfg.cv_chi
+    mu_V = cfg.rho_V * cfg.nu_V
+    T_w = float(np.mean(tw))
+    q_b = float(ser[n_avg:, 0].mean())
+    q_s = float(ser[n_avg:, 1].mean())
+    dT = T_w - T_sat
+    nu_th = berenson_nu(sigma, g, cfg.rho_L, cfg.rho_V, h_fg, cfg.c_v, lam_V, mu_V, dT)
+    nu_b = nu_lbm(q_b, T_w, T_sat, lam_V, ld)
+    nu_s = nu_lbm(q_s, T_w, T_sat, lam_V, ld)
+    every = max(1, n_end // 600)
+    return {"sigma": sigma, "lambda_d": ld, "t0": t0, "steps": n_end, "domain": [cfg.nx, cfg.nf, cfg.ns],
+            "T_w_over_Tc": T_w / tc, "q_bottom": q_b, "q_surface": q_s,
+            "nu_berenson": nu_th, "nu_lbm_bottom": nu_b, "nu_lbm_surface": nu_s,
+            "rel_dev_bottom": nu_b / nu_th - 1.0, "rel_dev_surface": nu_s / nu_th - 1.0,
+            "vapour_fraction_end": float(ser[-1, 2]), "rho_first_fluid_row": rho_wall,
+            "c_w": cfg.c_w_base, "mass_drift": float(ser[-1, 3] / ser[0, 3] - 1.0),
+            "nu_series_surface": [round(nu_lbm(q, T_w, T_sat, lam_V, ld), 3) for q in ser[::every, 1]],
+            "precision": precision}
+
+
+# ---- storage-precision report ---------------------------------------------------
+
+def coexistence(precision: str, nx: int = 32, nf: int = 128, steps: int = 20000) -> dict:
+    """Flat interface in a periodic box at T_sat (liquid in the lower half):
+    bulk densities far from the two interfaces, to compare with the Maxwell
+    construction (6.5 / 0.38 at 0.86 Tc, Sec. 3.1)."""
+    from . import lbm
+    cfg = W.periodic_box(nx, nf, liquid_rows=nf // 2, precision=precision)
+    r = lbm.Run(cfg, series_capacity=steps + 8)
+    r.step(steps)
+    r.sync()
+    rho = r.fields(("rho",))["rho"]
+    mass = r.series(0, steps)[:, 3]
+    q = nf // 8
+    return {"rho_L": float(rho[nf // 4 - q // 2:nf // 4 + q // 2].mean()),
+            "rho_V": float(rho[3 * nf // 4 - q // 2:3 * nf // 4 + q // 2].mean()),
+            "mass_drift": float(mass[-1] / mass[0] - 1.0)}
+
+
+def precision_report(sigma: float) -> dict:
+    """FP64 / FP32 / FP16-storage runs of the coexistence and film-boiling
+    cases, each precision's values and its deviation from FP64."""
+    out = {}
+    for prec in ("fp64", "fp32", "fp16"):
+        co = coexistence(prec)
+        fb = film_boiling(sigma, precision=prec, c_w=-1.2)
+        out[prec] = {"rho_L": co["rho_L"], "rho_V": co["rho_V"], "coexistence_mass_drift": co["mass_drift"],
+                     "nu_lbm_surface": fb["nu_lbm_surface"], "T_w_over_Tc": fb["T_w_over_Tc"],
+                     "film_mass_drift": fb["mass_drift"]}
+    ref = out["fp64"]
+    for prec in ("fp32", "fp16"):
+        d = out[prec]
+        d["dev"] = {k: d[k] / ref[k] - 1.0 for k in ("rho_L", "rho_V", "nu_lbm_surface")}
+    return out
+
+
+if __name__ == "__main__":  # python -m paper_1911_10747_gb300.validation
+    import json
+    import sys
+    prec = sys.argv[1] if len(sys.argv) > 1 else "fp32"
+    lap = laplace([16, 20, 25, 30, 36], precision="fp64")
+    print(json.dumps({k: v for k, v in lap.items()}))
+    fb = film_boiling(lap["sigma"], precision=prec)
+    print(json.dumps({k: v for k, v in fb.items() if k != "nu_series_surface"}))
