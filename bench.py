@@ -42,7 +42,8 @@ ALG_FLOW_BYTES = {"fp32": 76, "fp64": 152, "fp16": 40}
 HEAT_FLOPS = 274
 # FP32 peak from unit counts and clock: 152 SMs x 128 FP32 lanes x 2 flops x clock
 FP32_LANES = 152 * 128
-PROFILE = os.path.join(ROOT, "profiles", "flow_kernel_2048x2048_fp32.md")
+PROFILES = {"flow": os.path.join(ROOT, "profiles", "flow_kernel_2048x2048_fp32.md"),
+            "heat": os.path.join(ROOT, "profiles", "heat_kernel_2048x2048_fp32.md")}
 
 
 def peaks():
@@ -74,16 +75,18 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def ncu_traffic():
-    """DRAM bytes per flow-kernel launch from the committed ncu summary, or
-    None when absent or taken on a different kernel source."""
+def ncu_traffic(kind: str, variant: str):
+    """DRAM bytes per launch of the flow or heat kernel from the committed ncu
+    summary, or None when absent, taken on a different kernel source, or on
+    another launch-shape variant than the one timed."""
     try:
-        text = open(PROFILE).read()
+        text = open(PROFILES[kind]).read()
     except OSError:
         return None
     m = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", text)
     t = re.search(r"dram_bytes_per_full_launch:\s*([0-9.eE+]+)", text)
-    if not m or not t or m.group(1) != kernel_source_hash():
+    v = re.search(r"profiled_variant:\s*(\S+)", text)
+    if not m or not t or not v or m.group(1) != kernel_source_hash() or v.group(1) != variant:
         return None
     return float(t.group(1))
 
@@ -455,16 +458,19 @@ def run_ours(args):
     kms, nl = run.kernel_times()
     run.set_timing(False)
     hbm, peak_kind = peaks()
+    vnames = (variants["flow"][variants["selected"][0]], variants["heat"][variants["selected"][1]])
     flow_bytes = ALG_FLOW_BYTES[args.precision] * sites
     flow_achieved = flow_bytes / (kms[0] / 1e3) / 1e9
     flow_roof = {"bound": "hbm", "achieved": flow_achieved, "peak": hbm, "unit": "GB/s",
                  "frac": flow_achieved / hbm, "kernel": "k_flow", "bytes_per_site": ALG_FLOW_BYTES[args.precision],
-                 "traffic": ncu_traffic() if args.precision == "fp32" else None, "peak_source": peak_kind}
+                 "traffic": ncu_traffic("flow", vnames[0]) if args.precision == "fp32" else None,
+                 "peak_source": peak_kind}
     fp32_peak = FP32_LANES * 2 * max_sm_mhz() * 1e6 / 1e12
     heat_achieved = HEAT_FLOPS * cfg.temperature_sites / (kms[1] / 1e3) / 1e12
     heat_roof = {"bound": "alu", "achieved": heat_achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                  "frac": heat_achieved / fp32_peak, "kernel": "k_heat", "flops_per_site": HEAT_FLOPS,
-                 "traffic": None, "peak_source": "152 SMs x 128 FP32 lanes x 2 x max SM clock"}
+                 "traffic": ncu_traffic("heat", vnames[1]) if args.precision == "fp32" else None,
+                 "peak_source": "152 SMs x 128 FP32 lanes x 2 x max SM clock"}
     step_ms = ms_max / args.steps
     step_achieved = ALG_STEP_BYTES[args.precision] * sites / (step_ms / 1e3) / 1e9
     dominant = flow_roof if kms[0] >= kms[1] else heat_roof
