@@ -55,7 +55,7 @@ def peaks():
         return 6800.0, "fallback"
 
 
-KERNEL_SOURCES = ("lbm_device.cuh", "lbm_fast.cuh")
+KERNEL_SOURCES = ("lbm_device.cuh", "lbm_fast.cuh", "lbm_tma.cuh")
 
 
 def max_sm_mhz() -> float:
@@ -77,16 +77,15 @@ def kernel_source_hash() -> str:
 
 def ncu_traffic(kind: str, variant: str):
     """DRAM bytes per launch of the flow or heat kernel from the committed ncu
-    summary, or None when absent, taken on a different kernel source, or on
-    another launch-shape variant than the one timed."""
+    summary, or None when absent, taken on a different kernel source, or not
+    taken on the launch-shape variant that was timed."""
     try:
         text = open(PROFILES[kind]).read()
     except OSError:
         return None
     m = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", text)
-    t = re.search(r"dram_bytes_per_full_launch:\s*([0-9.eE+]+)", text)
-    v = re.search(r"profiled_variant:\s*(\S+)", text)
-    if not m or not t or not v or m.group(1) != kernel_source_hash() or v.group(1) != variant:
+    t = re.search(r"dram_bytes_per_full_launch\[" + re.escape(variant) + r"\]:\s*([0-9.eE+]+)", text)
+    if not m or not t or m.group(1) != kernel_source_hash():
         return None
     return float(t.group(1))
 

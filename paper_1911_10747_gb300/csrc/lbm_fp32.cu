@@ -2,6 +2,7 @@
 // FP32 arithmetic; FP16 storage of g as a probe.  Several launch shapes of
 // the flow and heat kernels are compiled; lbm_autotune picks among them.
 #include "lbm_fast.cuh"
+#include "lbm_tma.cuh"
 
 namespace lbmgb {
 namespace {
@@ -15,15 +16,17 @@ cudaError_t diag(const DevParams &p, const StepBuffers &b, int nblk, cudaStream_
 #define FLOWP(P, BX, BY, RY, MB)                                                                  \
     {"flowpers_" #BX "x" #BY "x" #RY "_b" #MB, FlowPersShape<P, BX, BY, RY, MB>::launch,            \
      FlowPersShape<P, BX, BY, RY, MB>::blocks, FlowPersShape<P, BX, BY, RY, MB>::prepare}
+#define FLOWT(P, BY, RY, MB)                                                                      \
+    {"flowtma_64x" #BY "x" #RY "_b" #MB, FlowTmaShape<P, BY, RY, MB>::launch, FlowTmaShape<P, BY, RY, MB>::blocks, \
+     FlowTmaShape<P, BY, RY, MB>::prepare}
 #define HEATS(P, BW, BY, R, MB) \
     {"heatrows_" #BW "x" #BY "x" #R, HeatRowsShape<P, BW, BY, R, MB>::launch, HeatRowsShape<P, BW, BY, R, MB>::prepare}
 #define HEATV(P, TX, TY, BX, BY) \
     {"heat_" #TX "x" #TY "_t" #BX "x" #BY, HeatFastShape<P, TX, TY, BX, BY>::launch, HeatFastShape<P, TX, TY, BX, BY>::prepare}
 
 const FlowVariant flows32[] = {
-    FLOWP(PolicyF32, 32, 8, 2, 2), FLOWP(PolicyF32, 64, 4, 2, 2), FLOWP(PolicyF32, 32, 8, 1, 3),
-    FLOWV(PolicyF32, 32, 8, 2, 3), FLOWV(PolicyF32, 32, 8, 4, 2), FLOWV(PolicyF32, 32, 16, 2, 2),
-    FLOWV(PolicyF32, 64, 4, 2, 3), FLOWV(PolicyF32, 32, 8, 1, 4), FLOWV(PolicyF32, 64, 8, 2, 2),
+    FLOWT(PolicyF32, 4, 2, 3), FLOWP(PolicyF32, 64, 4, 2, 2), FLOWP(PolicyF32, 32, 8, 2, 2),
+    FLOWP(PolicyF32, 32, 8, 1, 3), FLOWV(PolicyF32, 32, 8, 2, 3), FLOWV(PolicyF32, 64, 4, 2, 3),
 };
 const HeatVariant heats32[] = {
     HEATS(PolicyF32, 64, 10, 3, 1), HEATS(PolicyF32, 64, 8, 4, 1), HEATS(PolicyF32, 64, 6, 5, 1),

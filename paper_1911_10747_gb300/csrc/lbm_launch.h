@@ -12,7 +12,7 @@ namespace lbmgb {
 enum { FLAG_PERIODIC_Y = 1, FLAG_ISOTHERMAL = 2, FLAG_FROZEN_FLOW = 4, FLAG_MODEL_A = 8 };
 enum { TOP_WALL = 0, TOP_OUTFLOW = 1 };
 enum { BCM_SPOTS = 0, BCM_NOISE = 1, BCM_SINE = 2 };
-enum { ERRW_PSI = 1, ERRW_NONFINITE_RHO = 2, ERRW_NONFINITE_T = 4 };
+enum { ERRW_PSI = 1, ERRW_NONFINITE_RHO = 2, ERRW_NONFINITE_T = 4, ERRW_TIMEOUT = 8 };
 enum { TAG_INIT_NOISE = 1, TAG_BOTTOM_NOISE = 2 };
 enum { SERIES_WIDTH = 4 };
 
@@ -38,6 +38,7 @@ struct DevParams {
     double init_noise;
     double vap_threshold;         // (rho_L + rho_V) / 2
     unsigned long long seed;
+    unsigned tx_pad;              // test hook: extra bytes the staged-copy waits expect (0)
 };
 
 // Device buffers of one run touched by a step (types erased; the kernel

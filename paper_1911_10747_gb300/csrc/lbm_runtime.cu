@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -196,6 +197,12 @@ static int fill_params(const lbm_domain_t *d, const lbm_heater_t *ht, const lbm_
     p.init_noise = d->init_noise;
     p.vap_threshold = 0.5 * (eo->rho_L + eo->rho_V);
     p.seed = d->seed;
+    // Test hook for the bounded waits of the staged-copy flow kernel: a
+    // positive LBM_TEST_TX_PAD makes its stages expect more bytes than the
+    // copies deliver, so every wait runs out and the step reports
+    // LBM_E_TIMEOUT.  Unset in normal use.
+    const char *pad = std::getenv("LBM_TEST_TX_PAD");
+    p.tx_pad = pad ? (unsigned)std::strtoul(pad, nullptr, 10) : 0u;
     return 1;
 }
 
@@ -213,6 +220,8 @@ static int check_err_word(lbm_run *h) {
     unsigned e = 0;
     CK(h, cudaMemcpyAsync(&e, h->err, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
+    if (e & ERRW_TIMEOUT)
+        return fail(h, LBM_E_TIMEOUT, "a kernel's wait for its staged data ran out (the step's results are invalid)");
     if (e) {
         std::string m = "numerical fault latched by the kernels:";
         if (e & ERRW_PSI) m += " negative pseudopotential radicand;";

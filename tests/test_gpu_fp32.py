@@ -135,3 +135,41 @@ def test_fp16_storage_rounds_without_bias():
     print("fp16 film", s16["mass_drift"], s16["nu_lbm_surface"], "fp32", s32["nu_lbm_surface"])
     assert abs(s16["mass_drift"]) < 2e-3
     assert s16["nu_lbm_surface"] == pytest.approx(s32["nu_lbm_surface"], rel=0.2)
+
+
+@pytest.mark.parametrize("kw", [
+    dict(nx=192, nf=45, ns=5, liquid_rows=15, spot_x=(3, 100, 191), spot_half_width=2),
+    dict(nx=128, nf=37, ns=4, liquid_rows=12, top_mode="outflow", bc_mode="noise", spot_x=(), c_w_spot=()),
+])
+def test_fp32_bulk_copy_flow_variants_against_the_oracle(kw):
+    """The flow kernels that stage tiles with bulk asynchronous copies (nx a
+    multiple of 64): several tiles across, the periodic x edges, a ragged top
+    tile and both top boundaries, against the oracle."""
+    cfg = W.small_parity(precision="fp32").replace(rho_mean=2.3, **kw)
+    names = lbm.Run(cfg).variants()["flow"]
+    tma = [i for i, n in enumerate(names) if n.startswith("flowtma_")]
+    assert tma
+    o = O.OracleRun(cfg)
+    o.step(60)
+    for fv in tma:
+        g = lbm.Run(cfg)
+        g.select_variants(fv, 0)
+        g.step(60)
+        g.sync()
+        errs = field_errors(g, o)
+        assert errs["rho"] < 1e-4 and errs["T"] < 1e-5, (names[fv], errs)
+
+
+def test_fp32_bulk_copy_flow_in_a_periodic_box():
+    """Periodic in y with a box lower than one tile plus its halo rows."""
+    cfg = W.periodic_box(64, 6, liquid_rows=3, init_noise=1e-3, precision="fp32")
+    names = lbm.Run(cfg).variants()["flow"]
+    o = O.OracleRun(cfg)
+    o.step(40)
+    for fv in [i for i, n in enumerate(names) if n.startswith("flowtma_")]:
+        g = lbm.Run(cfg)
+        g.select_variants(fv, 0)
+        g.step(40)
+        g.sync()
+        errs = field_errors(g, o)
+        assert errs["rho"] < 1e-4, (names[fv], errs)
