@@ -492,8 +492,8 @@ def run_ours(args):
         dt = time.perf_counter() - t0
         e2e = {"value": ws * sites * e2e_steps / dt / 1e6, "unit": "MLUPS",
                "h2d_bytes_per_step": (9 * nfl + ntl) * 8, "d2h_bytes_per_step": 16,
-               "note": "per step: lbm_set_state from pinned float64 host arrays, lbm_step(1), "
-                       "lbm_wall_heat_flux + lbm_vapour_fraction read-back"}
+               "note": "per step: lbm_set_state from pinned float64 host arrays (read by the import kernel "
+                       "over the host link), lbm_step(1), lbm_wall_heat_flux + lbm_vapour_fraction read-back"}
 
     # ---- FP64 path on the same workload ----
     fp64 = None

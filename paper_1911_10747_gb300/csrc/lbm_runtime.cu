@@ -206,6 +206,18 @@ static int fill_params(const lbm_domain_t *d, const lbm_heater_t *ht, const lbm_
     return 1;
 }
 
+// Device address of page-locked host memory mapped for the current device,
+// or nullptr (pageable memory, or not a host pointer).
+static const double *host_alias(const double *p) {
+    if (!p) return nullptr;
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return (a.type == cudaMemoryTypeHost && a.devicePointer) ? static_cast<const double *>(a.devicePointer) : nullptr;
+}
+
 static int ensure_stage(lbm_run *h, size_t elems) {
     if (h->stage_elems >= elems) return LBM_OK;
     cudaFree(h->stage);
@@ -529,14 +541,28 @@ int lbm_set_state(lbm_handle h, const double *f, const double *T, int64_t step, 
     const double *df = f, *dT = T;
     int rc;
     if (!src_is_device && (f || T)) {
-        if ((rc = ensure_stage(h, 9 * nfl + ntl)) != LBM_OK) return rc;
+        // Page-locked host memory the device can address is read by the
+        // import kernel itself (over NVLink-C2C on Grace: copy and conversion
+        // in one pass); other host memory is staged with an async copy.
+        const double *af = host_alias(f), *aT = host_alias(T);
+        if ((f && !af) || (T && !aT)) {
+            if ((rc = ensure_stage(h, 9 * nfl + ntl)) != LBM_OK) return rc;
+        }
         if (f) {
-            CK(h, cudaMemcpyAsync(h->stage, f, 9 * nfl * sizeof(double), cudaMemcpyHostToDevice, h->stream));
-            df = h->stage;
+            if (af) {
+                df = af;
+            } else {
+                CK(h, cudaMemcpyAsync(h->stage, f, 9 * nfl * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+                df = h->stage;
+            }
         }
         if (T) {
-            CK(h, cudaMemcpyAsync(h->stage + 9 * nfl, T, ntl * sizeof(double), cudaMemcpyHostToDevice, h->stream));
-            dT = h->stage + 9 * nfl;
+            if (aT) {
+                dT = aT;
+            } else {
+                CK(h, cudaMemcpyAsync(h->stage + 9 * nfl, T, ntl * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+                dT = h->stage + 9 * nfl;
+            }
         }
     }
     // write into the current state buffers

@@ -192,3 +192,24 @@ def test_staged_copy_wait_that_runs_out_is_reported_and_the_context_survives(mon
     ok.step(3)
     ok.sync()
     assert ok.step_count == 3
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_set_state_from_page_locked_memory_equals_the_staged_path(precision):
+    """lbm_set_state reads page-locked host arrays directly (import kernel
+    over the host link) and stages pageable ones: both give the same state."""
+    import torch
+    cfg = W.small_parity(precision=precision).replace(bc_mode="noise", spot_x=(), c_w_spot=(), rho_mean=2.42)
+    a = lbm.Run(cfg).step(7)
+    st = a.fields(("f", "T"))
+    pf = torch.from_numpy(st["f"].copy()).pin_memory()
+    pT = torch.from_numpy(st["T"].copy()).pin_memory()
+    b, c = lbm.Run(cfg), lbm.Run(cfg)
+    b.set_state(pf.data_ptr(), pT.data_ptr(), step=7)
+    c.set_state(st["f"], st["T"], step=7)
+    fb, fc = b.fields(("f", "T")), c.fields(("f", "T"))
+    for k in fb:
+        assert np.array_equal(fb[k], fc[k]), k
+    b.step(5)
+    c.step(5)
+    assert np.array_equal(b.fields(("rho",))["rho"], c.fields(("rho",))["rho"])
