@@ -60,6 +60,10 @@ def test_struct_layouts_match_header(tmp_path):
     (dict(s=(1.0, 0.8, 0.8, 1.0, 2.5, 1.0, 1.1, 1.0, 1.0)), "MRT"),
     (dict(periodic_y=True), "periodic"),
     (dict(rho_V=7.0), "rho_L > rho_V"),
+    (dict(nx=0), "domain.nx"),
+    (dict(ns=2), "ny_solid"),
+    (dict(liquid_rows=200), "liquid_rows"),
+    (dict(nx=1 << 20, nf=1 << 12), "too large"),  # 4.3e9 sites: rejected before any allocation
 ])
 def test_invalid_configuration_is_rejected_on_the_host(lib, change, field):
     cfg = W.small_parity().replace(**change)

@@ -213,3 +213,19 @@ def test_set_state_from_page_locked_memory_equals_the_staged_path(precision):
     b.step(5)
     c.step(5)
     assert np.array_equal(b.fields(("rho",))["rho"], c.fields(("rho",))["rho"])
+
+
+@pytest.mark.parametrize("kw", [
+    dict(nx=1, nf=12, ns=3, liquid_rows=4, spot_x=(), c_w_spot=()),              # one column
+    dict(nx=5, nf=2, ns=3, liquid_rows=1, spot_x=(), c_w_spot=()),               # two fluid rows
+    dict(nx=1, nf=3, ns=0, liquid_rows=1, spot_x=(), c_w_spot=(), bc_mode="noise"),  # model A, one column
+])
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_degenerate_domains(kw, precision):
+    """Smallest domains the ABI accepts: every neighbour wraps onto the site
+    itself or its column, the bottom and top walls touch."""
+    cfg = W.small_parity(precision=precision).replace(rho_mean=2.42, **kw)
+    g, o = run_both(cfg, 30)
+    errs = field_errors(g, o)
+    tol = TOL64 if precision == "fp64" else 1e-4
+    assert all(v <= tol for v in errs.values()), errs
