@@ -79,8 +79,20 @@ __device__ __forceinline__ float bottom_theta(const FParams &q, int x, long long
 }
 
 __device__ __forceinline__ float frcp(float x) { return __frcp_rn(x); }
-__device__ __forceinline__ float fast_rcp(float x) { return __fdividef(1.0f, x); }
-__device__ __forceinline__ float fast_sqrt(float x) { return x * rsqrtf(x); }  // x > 0
+// Single-instruction PTX approximations (documented maximum error 1 ulp for
+// the reciprocal, 2^-23 relative for the root), flushing subnormals: no
+// value of the FP32 path is subnormal, and this skips the special-range
+// handling the library intrinsics carry.
+__device__ __forceinline__ float fast_rcp(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float fast_sqrt(float x) {  // x >= 0
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
 
 // psi(rho, T) of Eq. 12-13 in FP32 with approximate reciprocals / roots.
 __device__ __forceinline__ float psi_fast(const FParams &q, float rho, float T, unsigned &errbits) {

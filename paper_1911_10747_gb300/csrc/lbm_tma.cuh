@@ -287,7 +287,7 @@ inline PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 // same tile instead.
 template <class P, int BY, int RY, int MINB>
 struct FlowTmaShape {
-    using Fallback = FlowPersShape<P, TMA_TX, BY, RY, MINB>;
+    using Fallback = FlowPersShape<P, TMA_TX, BY, RY, (MINB < 2 ? MINB : 2)>;  // its registers need <= 2 blocks / SM
     static constexpr int SR = BY * RY + 2;
     static constexpr size_t smem_bytes = 2 * sizeof(float) * (size_t)tma_stage_floats<BY, RY>() + 128;
     static int grid_blocks;
