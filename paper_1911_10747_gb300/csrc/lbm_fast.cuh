@@ -162,8 +162,10 @@ __device__ __forceinline__ void st_pop(__half *q, float v, PopDither &d) {
 // forcing (Eq. 3-10) and push streaming with halfway bounce-back (Eq. 8), FP32
 // path.  f: the site's shifted populations; sp: its psi in a tile of row
 // stride SW (neighbours at +-1, +-SW); k = y nx + x.  Writes the moments and
-// the nine post-collision populations to their destinations.
-template <class S>
+// the nine post-collision populations to their destinations.  EDGE = false
+// is for sites of tiles that touch no boundary (no wall row, no periodic
+// wrap): the wall terms and index wraps drop out at compile time.
+template <class S, bool EDGE = true>
 __device__ __forceinline__ void flow_site(const FParams &p, const float *f, float d, float rho, const float *sp,
                                           int SW, int x, int y, int k, bool py, bool outflow,
                                           const double *__restrict__ cw, S *const *oplane, float *__restrict__ rho_o,
@@ -176,14 +178,14 @@ __device__ __forceinline__ void flow_site(const FParams &p, const float *f, floa
     const float pE = sp[1], pW = sp[-1], pN = sp[SW], pS = sp[-SW];
     float pNE = sp[SW + 1], pNW = sp[SW - 1];
     const float pSW = sp[-SW - 1], pSE = sp[-SW + 1];
-    const bool bot = !py && y == 0, top = !py && y == nf - 1;
+    const bool bot = EDGE && !py && y == 0, top = EDGE && !py && y == nf - 1;
     float pNx = pN;
     if (top && outflow) { pNx = psi; pNE = pE; pNW = pW; }  // open top: zero normal gradient
     const float a = pNE - pSW, b = pSE - pNW;
     const float pre = mG * psi;
     const float sx = w1 * (pE - pW) + w2 * (a + b), sy = w1 * (pNx - pS) + w2 * (a - b);
     const float Fmx = pre * sx, Fmy = pre * sy;
-    const int xm = wrap1(x - 1, nx), xp = wrap1(x + 1, nx);
+    const int xm = EDGE ? wrap1(x - 1, nx) : x - 1, xp = EDGE ? wrap1(x + 1, nx) : x + 1;
     float Fax = 0.0f, Fay = 0.0f;
     if (bot) {  // Eq. 14 with the heater sites below (i = 4, 7, 8)
         const float cm = float(cw[xm]), c0 = float(cw[x]), cp = float(cw[xp]);
@@ -250,8 +252,8 @@ __device__ __forceinline__ void flow_site(const FParams &p, const float *f, floa
     // Eq. 8, push; halfway bounce-back at the heater and the top wall
     // (32-bit offsets from this site: east / west columns, rows above / below)
     const int dxp = xp - x, dxm = xm - x;
-    const int kn = (py && y == nf - 1) ? x : k + nx;      // row above
-    const int ks_ = (py && y == 0) ? (nf - 1) * nx + x : k - nx;  // row below
+    const int kn = (EDGE && py && y == nf - 1) ? x : k + nx;                // row above
+    const int ks_ = (EDGE && py && y == 0) ? (nf - 1) * nx + x : k - nx;    // row below
     st_pop(oplane[0] + k, fo0, dz);
     st_pop(oplane[1] + k + dxp, fo1, dz);
     st_pop(oplane[3] + k + dxm, fo3, dz);
@@ -357,17 +359,17 @@ k_flow_fast(const FParams p, const typename P::fst *__restrict__ fin, typename P
     __syncthreads();
 
     // ---- collide and push ----
-    const float w1 = 1.0f / 3.0f, w2 = 1.0f / 12.0f;
-    const float mG = p.mG;
-    const float inv_drho = p.inv_drho, dtau = p.dtau;
+    S *oplane[9];
+    #pragma unroll
+    for (int i = 0; i < 9; i++) oplane[i] = fout + i * plane;
     float mass = 0.0f, nvap = 0.0f;
     #pragma unroll
     for (int r = 0; r < RY; r++) {
         const int lx = threadIdx.x, ly = threadIdx.y + r * BY;
         const int x = x0 + lx, y = y0 + ly;
         if (x >= nx || y >= nf) continue;
-        const size_t k = (size_t)y * nx + x;
-        PopDither dz = pop_dither<S>(p, nstep, (int)k);
+        const int k = y * nx + x;
+        PopDither dz = pop_dither<S>(p, nstep, k);
         const float d = dd[r];
         const float rho = d + rho0;
         if (!(fabsf(rho) < 1e30f)) errbits |= ERRW_NONFINITE_RHO;
@@ -375,120 +377,14 @@ k_flow_fast(const FParams p, const typename P::fst *__restrict__ fin, typename P
         nvap += (rho < p.vap_threshold) ? 1.0f : 0.0f;
         if (frozen) {
             #pragma unroll
-            for (int i = 0; i < 9; i++) st_pop(fout + i * plane + k, g[r][i], dz);
+            for (int i = 0; i < 9; i++) st_pop(oplane[i] + k, g[r][i], dz);
             rho_o[k] = rho;
             ux_o[k] = 0.0f;
             uy_o[k] = 0.0f;
             continue;
         }
-        const float *sp = s_psi + (ly + 1) * SW + (lx + 1);
-        const float psi = sp[0];
-        const float pE = sp[1], pW = sp[-1], pN = sp[SW], pS = sp[-SW];
-        float pNE = sp[SW + 1], pNW = sp[SW - 1];
-        const float pSW = sp[-SW - 1], pSE = sp[-SW + 1];
-        const bool bot = !py && y == 0, top = !py && y == nf - 1;
-        float pNx = pN;
-        if (top && outflow) { pNx = psi; pNE = pE; pNW = pW; }  // open top: zero normal gradient
-        const float a = pNE - pSW, b = pSE - pNW;
-        const float pre = mG * psi;
-        const float sx = w1 * (pE - pW) + w2 * (a + b), sy = w1 * (pNx - pS) + w2 * (a - b);
-        const float Fmx = pre * sx, Fmy = pre * sy;
-        const int xm = wrap1(x - 1, nx), xp = wrap1(x + 1, nx);
-        float Fax = 0.0f, Fay = 0.0f;
-        if (bot) {  // Eq. 14 with the heater sites below (i = 4, 7, 8)
-            const float cm = float(cw[xm]), c0 = float(cw[x]), cp = float(cw[xp]);
-            Fax = -psi * (w2 * (cp - cm));
-            Fay = psi * (w1 * c0 + w2 * (cm + cp));
-        }
-        if (top && !outflow) Fay += -psi * ((w1 + 2.0f * w2) * p.c_w_top);
-        const float Fx = Fmx + Fax;
-        const float Fy = (Fmy + Fay) - (rho - p.rho_mean) * p.g;
-
-        const float *f = g[r];
-        // moments of g (Eq. 6 with the rho0 shift of m0..m2 folded into q0..q2)
-        const float s14 = (f[1] + f[2]) + (f[3] + f[4]);
-        const float s58 = (f[5] + f[6]) + (f[7] + f[8]);
-        const float m1 = -4.0f * f[0] - s14 + 2.0f * s58;
-        const float m2 = 4.0f * f[0] - 2.0f * s14 + s58;
-        const float f13 = f[1] - f[3], f24 = f[2] - f[4];
-        const float f57 = f[5] - f[7], f86 = f[8] - f[6];
-        const float m3 = f13 + (f57 + f86);
-        const float m4 = -2.0f * f13 + (f57 + f86);
-        const float m5 = f24 + (f57 - f86);
-        const float m6 = -2.0f * f24 + (f57 - f86);
-        const float m7 = (f[1] + f[3]) - (f[2] + f[4]);
-        const float m8 = (f[5] + f[7]) - (f[6] + f[8]);
-        const float irho = fast_rcp(rho);
-        const float ux = (m3 + 0.5f * Fx) * irho, uy = (m5 + 0.5f * Fy) * irho;
-        const float tau = p.tau_V + (rho - p.rho_V) * inv_drho * dtau;
-        const float s78 = fast_rcp(tau);
-        const float ru2 = rho * (ux * ux + uy * uy);
-        const float q1 = -2.0f * d + 3.0f * ru2, q2 = d - 3.0f * ru2;
-        const float q3 = rho * ux, q5 = rho * uy;
-        const float q7 = rho * (ux * ux - uy * uy), q8 = rho * (ux * uy);
-        const float uF = ux * Fx + uy * Fy;
-        const float eps = (psi > 0.0f) ? p.varpi12G2 * (sx * sx + sy * sy) : 0.0f;
-        const float S1 = 6.0f * uF + eps * p.inv_tauem;
-        const float S2 = -6.0f * uF + eps * p.sgn_over_taus;
-        // Eq. 7 (m0 unchanged; q4 = -q3, q6 = -q5)
-        const float z1 = m1 - p.s[1] * (m1 - q1) + p.hs[1] * S1;
-        const float z2 = m2 - p.s[2] * (m2 - q2) + p.hs[2] * S2;
-        const float z3 = m3 - p.s[3] * (m3 - q3) + p.hs[3] * Fx;
-        const float z4 = m4 - p.s[4] * (m4 + q3) - p.hs[4] * Fx;
-        const float z5 = m5 - p.s[5] * (m5 - q5) + p.hs[5] * Fy;
-        const float z6 = m6 - p.s[6] * (m6 + q5) - p.hs[6] * Fy;
-        const float h78 = 1.0f - 0.5f * s78;
-        const float z7 = m7 - s78 * (m7 - q7) + h78 * (2.0f * (ux * Fx - uy * Fy));
-        const float z8 = m8 - s78 * (m8 - q8) + h78 * (ux * Fy + uy * Fx);
-        const float e0 = d * (1.0f / 9.0f), e1 = z1 * (1.0f / 36.0f), e2 = z2 * (1.0f / 36.0f);
-        const float e3 = z3 * (1.0f / 6.0f), e4 = z4 * (1.0f / 12.0f), e5 = z5 * (1.0f / 6.0f);
-        const float e6 = z6 * (1.0f / 12.0f), e7 = z7 * 0.25f, e8 = z8 * 0.25f;
-        const float A0 = e0 - e1 - 2.0f * e2;       // axis-direction common part
-        const float B0 = e0 + 2.0f * e1 + e2;       // diagonal common part
-        const float fo0 = e0 - 4.0f * e1 + 4.0f * e2;
-        const float fo1 = A0 + (e3 - 2.0f * e4) + e7;
-        const float fo3 = A0 - (e3 - 2.0f * e4) + e7;
-        const float fo2 = A0 + (e5 - 2.0f * e6) - e7;
-        const float fo4 = A0 - (e5 - 2.0f * e6) - e7;
-        const float cxx = e3 + e4, cyy = e5 + e6;
-        const float fo5 = B0 + cxx + cyy + e8;
-        const float fo6 = B0 - cxx + cyy - e8;
-        const float fo7 = B0 - cxx - cyy + e8;
-        const float fo8 = B0 + cxx - cyy - e8;
-        rho_o[k] = rho;
-        ux_o[k] = ux;
-        uy_o[k] = uy;
-        // Eq. 8, push; halfway bounce-back at the heater and the top wall
-        S *o = fout;
-        const size_t ro = (size_t)y * nx;
-        st_pop(o + ro + x, fo0, dz);
-        st_pop(o + plane + ro + xp, fo1, dz);
-        st_pop(o + 3 * plane + ro + xm, fo3, dz);
-        const size_t ru = (size_t)(py && y == nf - 1 ? 0 : y + 1) * nx;
-        const size_t rd = (size_t)(py && y == 0 ? nf - 1 : y - 1) * nx;
-        if (!top) {
-            st_pop(o + 2 * plane + ru + x, fo2, dz);
-            st_pop(o + 5 * plane + ru + xp, fo5, dz);
-            st_pop(o + 6 * plane + ru + xm, fo6, dz);
-        } else if (!outflow) {
-            st_pop(o + 4 * plane + ro + x, fo2, dz);
-            st_pop(o + 7 * plane + ro + x, fo5, dz);
-            st_pop(o + 8 * plane + ro + x, fo6, dz);
-        }
-        if (!bot) {
-            st_pop(o + 4 * plane + rd + x, fo4, dz);
-            st_pop(o + 7 * plane + rd + xm, fo7, dz);
-            st_pop(o + 8 * plane + rd + xp, fo8, dz);
-        } else {
-            st_pop(o + 2 * plane + ro + x, fo4, dz);
-            st_pop(o + 5 * plane + ro + x, fo7, dz);
-            st_pop(o + 6 * plane + ro + x, fo8, dz);
-        }
-        if (top && outflow) {
-            st_pop(o + 4 * plane + ro + x, fo4, dz);
-            st_pop(o + 7 * plane + ro + xm, fo7, dz);
-            st_pop(o + 8 * plane + ro + xp, fo8, dz);
-        }
+        flow_site<S>(p, g[r], d, rho, s_psi + (ly + 1) * SW + (lx + 1), SW, x, y, k, py, outflow, cw, oplane, rho_o,
+                     ux_o, uy_o, dz);
     }
     // per-block mass and vapour count: FP32 inside the block, FP64 across blocks
     #pragma unroll
@@ -640,139 +536,35 @@ k_flow_pers(const FParams p, int tiles_x, int ntiles, const typename P::fst *__r
     if (tile + (int)gridDim.x < ntiles) fetch(nxt, nyt);
     __syncthreads();
 
-    // ---- collide and push ----
-    const float w1 = 1.0f / 3.0f, w2 = 1.0f / 12.0f;
-    const float mG = p.mG;
-    const float inv_drho = p.inv_drho, dtau = p.dtau;
-    #pragma unroll
-    for (int r = 0; r < RY; r++) {
-        const int lx = threadIdx.x, ly = threadIdx.y + r * BY;
-        const int x = x0 + lx, y = y0 + ly;
-        if (x >= nx || y >= nf) continue;
-        const int k = y * nx + x;
-        PopDither dz = pop_dither<S>(p, nstep, (int)k);
-        const float d = dd[r];
-        const float rho = d + rho0;
-        if (!(fabsf(rho) < 1e30f)) errbits |= ERRW_NONFINITE_RHO;
-        mass += rho;
-        nvap += (rho < p.vap_threshold) ? 1.0f : 0.0f;
-        if (frozen) {
-            #pragma unroll
-            for (int i = 0; i < 9; i++) st_pop(oplane[i] + k, g[r][i], dz);
-            rho_o[k] = rho;
-            ux_o[k] = 0.0f;
-            uy_o[k] = 0.0f;
-            continue;
+    // ---- collide and push (tiles that touch no boundary skip the wall terms) ----
+    auto collide = [&](auto edge_tag) {
+        constexpr bool E = decltype(edge_tag)::value;
+        #pragma unroll
+        for (int r = 0; r < RY; r++) {
+            const int lx = threadIdx.x, ly = threadIdx.y + r * BY;
+            const int x = x0 + lx, y = y0 + ly;
+            if (E && (x >= nx || y >= nf)) continue;
+            const int k = y * nx + x;
+            PopDither dz = pop_dither<S>(p, nstep, (int)k);
+            const float d = dd[r];
+            const float rho = d + rho0;
+            if (!(fabsf(rho) < 1e30f)) errbits |= ERRW_NONFINITE_RHO;
+            mass += rho;
+            nvap += (rho < p.vap_threshold) ? 1.0f : 0.0f;
+            if (frozen) {
+                #pragma unroll
+                for (int i = 0; i < 9; i++) st_pop(oplane[i] + k, g[r][i], dz);
+                rho_o[k] = rho;
+                ux_o[k] = 0.0f;
+                uy_o[k] = 0.0f;
+                continue;
+            }
+            flow_site<S, E>(p, g[r], d, rho, s_psi + (ly + 1) * SW + (lx + 1), SW, x, y, k, py, outflow, cw, oplane,
+                            rho_o, ux_o, uy_o, dz);
         }
-        const float *sp = s_psi + (ly + 1) * SW + (lx + 1);
-        const float psi = sp[0];
-        const float pE = sp[1], pW = sp[-1], pN = sp[SW], pS = sp[-SW];
-        float pNE = sp[SW + 1], pNW = sp[SW - 1];
-        const float pSW = sp[-SW - 1], pSE = sp[-SW + 1];
-        const bool bot = !py && y == 0, top = !py && y == nf - 1;
-        float pNx = pN;
-        if (top && outflow) { pNx = psi; pNE = pE; pNW = pW; }  // open top: zero normal gradient
-        const float a = pNE - pSW, b = pSE - pNW;
-        const float pre = mG * psi;
-        const float sx = w1 * (pE - pW) + w2 * (a + b), sy = w1 * (pNx - pS) + w2 * (a - b);
-        const float Fmx = pre * sx, Fmy = pre * sy;
-        const int xm = wrap1(x - 1, nx), xp = wrap1(x + 1, nx);
-        float Fax = 0.0f, Fay = 0.0f;
-        if (bot) {  // Eq. 14 with the heater sites below (i = 4, 7, 8)
-            const float cm = float(cw[xm]), c0 = float(cw[x]), cp = float(cw[xp]);
-            Fax = -psi * (w2 * (cp - cm));
-            Fay = psi * (w1 * c0 + w2 * (cm + cp));
-        }
-        if (top && !outflow) Fay += -psi * ((w1 + 2.0f * w2) * p.c_w_top);
-        const float Fx = Fmx + Fax;
-        const float Fy = (Fmy + Fay) - (rho - p.rho_mean) * p.g;
-
-        const float *f = g[r];
-        // moments of g (Eq. 6 with the rho0 shift of m0..m2 folded into q0..q2)
-        const float s14 = (f[1] + f[2]) + (f[3] + f[4]);
-        const float s58 = (f[5] + f[6]) + (f[7] + f[8]);
-        const float m1 = -4.0f * f[0] - s14 + 2.0f * s58;
-        const float m2 = 4.0f * f[0] - 2.0f * s14 + s58;
-        const float f13 = f[1] - f[3], f24 = f[2] - f[4];
-        const float f57 = f[5] - f[7], f86 = f[8] - f[6];
-        const float m3 = f13 + (f57 + f86);
-        const float m4 = -2.0f * f13 + (f57 + f86);
-        const float m5 = f24 + (f57 - f86);
-        const float m6 = -2.0f * f24 + (f57 - f86);
-        const float m7 = (f[1] + f[3]) - (f[2] + f[4]);
-        const float m8 = (f[5] + f[7]) - (f[6] + f[8]);
-        const float irho = fast_rcp(rho);
-        const float ux = (m3 + 0.5f * Fx) * irho, uy = (m5 + 0.5f * Fy) * irho;
-        const float tau = p.tau_V + (rho - p.rho_V) * inv_drho * dtau;
-        const float s78 = fast_rcp(tau);
-        const float ru2 = rho * (ux * ux + uy * uy);
-        const float q1 = -2.0f * d + 3.0f * ru2, q2 = d - 3.0f * ru2;
-        const float q3 = rho * ux, q5 = rho * uy;
-        const float q7 = rho * (ux * ux - uy * uy), q8 = rho * (ux * uy);
-        const float uF = ux * Fx + uy * Fy;
-        const float eps = (psi > 0.0f) ? p.varpi12G2 * (sx * sx + sy * sy) : 0.0f;
-        const float S1 = 6.0f * uF + eps * p.inv_tauem;
-        const float S2 = -6.0f * uF + eps * p.sgn_over_taus;
-        // Eq. 7 (m0 unchanged; q4 = -q3, q6 = -q5)
-        const float z1 = m1 - p.s[1] * (m1 - q1) + p.hs[1] * S1;
-        const float z2 = m2 - p.s[2] * (m2 - q2) + p.hs[2] * S2;
-        const float z3 = m3 - p.s[3] * (m3 - q3) + p.hs[3] * Fx;
-        const float z4 = m4 - p.s[4] * (m4 + q3) - p.hs[4] * Fx;
-        const float z5 = m5 - p.s[5] * (m5 - q5) + p.hs[5] * Fy;
-        const float z6 = m6 - p.s[6] * (m6 + q5) - p.hs[6] * Fy;
-        const float h78 = 1.0f - 0.5f * s78;
-        const float z7 = m7 - s78 * (m7 - q7) + h78 * (2.0f * (ux * Fx - uy * Fy));
-        const float z8 = m8 - s78 * (m8 - q8) + h78 * (ux * Fy + uy * Fx);
-        const float e0 = d * (1.0f / 9.0f), e1 = z1 * (1.0f / 36.0f), e2 = z2 * (1.0f / 36.0f);
-        const float e3 = z3 * (1.0f / 6.0f), e4 = z4 * (1.0f / 12.0f), e5 = z5 * (1.0f / 6.0f);
-        const float e6 = z6 * (1.0f / 12.0f), e7 = z7 * 0.25f, e8 = z8 * 0.25f;
-        const float A0 = e0 - e1 - 2.0f * e2;       // axis-direction common part
-        const float B0 = e0 + 2.0f * e1 + e2;       // diagonal common part
-        const float fo0 = e0 - 4.0f * e1 + 4.0f * e2;
-        const float fo1 = A0 + (e3 - 2.0f * e4) + e7;
-        const float fo3 = A0 - (e3 - 2.0f * e4) + e7;
-        const float fo2 = A0 + (e5 - 2.0f * e6) - e7;
-        const float fo4 = A0 - (e5 - 2.0f * e6) - e7;
-        const float cxx = e3 + e4, cyy = e5 + e6;
-        const float fo5 = B0 + cxx + cyy + e8;
-        const float fo6 = B0 - cxx + cyy - e8;
-        const float fo7 = B0 - cxx - cyy + e8;
-        const float fo8 = B0 + cxx - cyy - e8;
-        rho_o[k] = rho;
-        ux_o[k] = ux;
-        uy_o[k] = uy;
-        // Eq. 8, push; halfway bounce-back at the heater and the top wall
-        // (32-bit offsets from this site: east / west columns, rows above / below)
-        const int dxp = xp - x, dxm = xm - x;
-        const int kn = (py && y == nf - 1) ? x : k + nx;      // row above
-        const int ks_ = (py && y == 0) ? (nf - 1) * nx + x : k - nx;  // row below
-        st_pop(oplane[0] + k, fo0, dz);
-        st_pop(oplane[1] + k + dxp, fo1, dz);
-        st_pop(oplane[3] + k + dxm, fo3, dz);
-        if (!top) {
-            st_pop(oplane[2] + kn, fo2, dz);
-            st_pop(oplane[5] + kn + dxp, fo5, dz);
-            st_pop(oplane[6] + kn + dxm, fo6, dz);
-        } else if (!outflow) {
-            st_pop(oplane[4] + k, fo2, dz);
-            st_pop(oplane[7] + k, fo5, dz);
-            st_pop(oplane[8] + k, fo6, dz);
-        }
-        if (!bot) {
-            st_pop(oplane[4] + ks_, fo4, dz);
-            st_pop(oplane[7] + ks_ + dxm, fo7, dz);
-            st_pop(oplane[8] + ks_ + dxp, fo8, dz);
-        } else {
-            st_pop(oplane[2] + k, fo4, dz);
-            st_pop(oplane[5] + k, fo7, dz);
-            st_pop(oplane[6] + k, fo8, dz);
-        }
-        if (top && outflow) {
-            st_pop(oplane[4] + k, fo4, dz);
-            st_pop(oplane[7] + k + dxm, fo7, dz);
-            st_pop(oplane[8] + k + dxp, fo8, dz);
-        }
-    }
+    };
+    if (x0 == 0 || x0 + TX >= nx || y0 == 0 || y0 + TY >= nf) collide(std::true_type{});
+    else collide(std::false_type{});
     __syncthreads();  // s_psi is rewritten by the next tile
     cxt = nxt; cyt = nyt;
     }

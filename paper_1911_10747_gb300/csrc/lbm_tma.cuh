@@ -219,30 +219,35 @@ k_flow_tma(const __grid_constant__ CUtensorMap map_f, const __grid_constant__ CU
             break;
         }
 
-        // ---- collide and push ----
-        #pragma unroll
-        for (int r = 0; r < RY; r++) {
-            const int lx = threadIdx.x, ly = threadIdx.y + r * BY;
-            const int x = x0 + lx, y = y0 + ly;
-            if (y >= nf) continue;
-            const int ks = y * nx + x;
-            PopDither dz{1u};
-            const float d = dd[r];
-            const float rho = d + rho0;
-            if (!(fabsf(rho) < 1e30f)) errbits |= ERRW_NONFINITE_RHO;
-            mass += rho;
-            nvap += (rho < p.vap_threshold) ? 1.0f : 0.0f;
-            if (frozen) {
-                #pragma unroll
-                for (int i = 0; i < 9; i++) oplane[i][ks] = g[r][i];
-                rho_o[ks] = rho;
-                ux_o[ks] = 0.0f;
-                uy_o[ks] = 0.0f;
-                continue;
+        // ---- collide and push (tiles that touch no boundary skip the wall terms) ----
+        auto collide = [&](auto edge_tag) {
+            constexpr bool E = decltype(edge_tag)::value;
+            #pragma unroll
+            for (int r = 0; r < RY; r++) {
+                const int lx = threadIdx.x, ly = threadIdx.y + r * BY;
+                const int x = x0 + lx, y = y0 + ly;
+                if (E && y >= nf) continue;
+                const int ks = y * nx + x;
+                PopDither dz{1u};
+                const float d = dd[r];
+                const float rho = d + rho0;
+                if (!(fabsf(rho) < 1e30f)) errbits |= ERRW_NONFINITE_RHO;
+                mass += rho;
+                nvap += (rho < p.vap_threshold) ? 1.0f : 0.0f;
+                if (frozen) {
+                    #pragma unroll
+                    for (int i = 0; i < 9; i++) oplane[i][ks] = g[r][i];
+                    rho_o[ks] = rho;
+                    ux_o[ks] = 0.0f;
+                    uy_o[ks] = 0.0f;
+                    continue;
+                }
+                flow_site<float, E>(p, g[r], d, rho, s_psi + (ly + 1) * SW + (lx + 1), SW, x, y, ks, py, outflow, cw,
+                                    oplane, rho_o, ux_o, uy_o, dz);
             }
-            flow_site<float>(p, g[r], d, rho, s_psi + (ly + 1) * SW + (lx + 1), SW, x, y, ks, py, outflow, cw, oplane,
-                             rho_o, ux_o, uy_o, dz);
-        }
+        };
+        if (x0 == 0 || x0 + BX >= nx || y0 == 0 || y0 + TY >= nf) collide(std::true_type{});
+        else collide(std::false_type{});
         __syncthreads();  // s_psi and this stage are rewritten
         cxt = nxt; cyt = nyt;
     }
