@@ -895,7 +895,15 @@ k_heat_rows(const FParams p, int tiles_x, int ntiles, const typename P::tst *__r
     int pk = 0, px = 0;  // kinds of the staged cells (3 bits per cell) and their column
 
     const int gdx = (int)gridDim.x % tiles_x, gdy = (int)gridDim.x / tiles_x;
-    auto fetch = [&](int txt, int tyt) {
+    // a tile whose rows are all fluid rows (walled domains): every cell is
+    // HK_FLUID, so the kind logic drops out of its fetch, load and
+    // coefficient passes
+    auto interior = [&](int tyt) {
+        const int rlo = tyt * TYO - H;
+        return !py && rlo >= ns && rlo + SH <= nt;
+    };
+    auto fetch_tile = [&](int txt, int tyt, auto itag) {
+        constexpr bool I = decltype(itag)::value;
         const int x0 = txt * TXO, r0 = tyt * TYO;
         const int x = WIDE ? wrap1(x0 + tx - H, nx) : wrapi(x0 + tx - H, nx);
         px = x;
@@ -903,7 +911,8 @@ k_heat_rows(const FParams p, int tiles_x, int ntiles, const typename P::tst *__r
         #pragma unroll
         for (int c = 0; c < R; c++) {
             int row = r0 + y0 + c - H, k;
-            if (py) { row = WIDE ? wrap1(row, nt) : wrapi(row, nt); k = HK_FLUID; }
+            if (I) k = HK_FLUID;
+            else if (py) { row = WIDE ? wrap1(row, nt) : wrapi(row, nt); k = HK_FLUID; }
             else if (row < 0 || row > nt) k = HK_OUT;
             else if (row == 0) k = HK_BOTTOM;
             else if (row == nt) k = HK_GHOST;
@@ -919,6 +928,10 @@ k_heat_rows(const FParams p, int tiles_x, int ntiles, const typename P::tst *__r
             cp_async4(&gV[y0 + c][tx], uy_i + kf, fl);
         }
     };
+    auto fetch = [&](int txt, int tyt) {
+        if (interior(tyt)) fetch_tile(txt, tyt, std::true_type{});
+        else fetch_tile(txt, tyt, std::false_type{});
+    };
     const float w1 = 1.0f / 9.0f, w2 = 1.0f / 36.0f;
     int cxt = (int)blockIdx.x % tiles_x, cyt = (int)blockIdx.x / tiles_x;
     if ((int)blockIdx.x < ntiles) fetch(cxt, cyt);
@@ -926,6 +939,20 @@ k_heat_rows(const FParams p, int tiles_x, int ntiles, const typename P::tst *__r
         int nxt = cxt + gdx, nyt = cyt + gdy;
         if (nxt >= tiles_x) { nxt -= tiles_x; nyt += 1; }
         const bool more = tile + (int)gridDim.x < ntiles;
+        // neighbour columns and rows, clamped into the tile (edge cells compute
+        // values nobody reads from them)
+        const int xl = tx > 0 ? tx - 1 : 0, xr = tx < BW - 1 ? tx + 1 : BW - 1;
+        const int yb = y0 > 0 ? y0 - 1 : 0, yt = y0 + R < SH ? y0 + R : SH - 1;
+        // rows y0 - 1 .. y0 + R of column x - 1 / x + 1 (index j = row - y0 + 1)
+        auto column = [&](const float (*a)[BW], int x, float *v) {
+            v[0] = a[yb][x];
+            #pragma unroll
+            for (int j = 0; j < R; j++) v[j + 1] = a[y0 + j][x];
+            v[R + 1] = a[yt][x];
+        };
+        // ---- load and per-step coefficients (interior tiles: compile-time fluid) ----
+        auto prepare = [&](auto itag) {
+        constexpr bool I = decltype(itag)::value;
         int kd[R];
         float irc[R], rho[R], ux[R], uy[R], lam[R];
         cp_async_wait_all();
@@ -933,7 +960,7 @@ k_heat_rows(const FParams p, int tiles_x, int ntiles, const typename P::tst *__r
         for (int c = 0; c < R; c++) {
             const float Tr = sL[y0 + c][tx];
             rho[c] = sU[y0 + c][tx]; ux[c] = sV[y0 + c][tx]; uy[c] = gV[y0 + c][tx];
-            const int k = (pk >> (3 * c)) & 7;
+            const int k = I ? (int)HK_FLUID : (pk >> (3 * c)) & 7;
             kd[c] = k;
             float T = Tr, l = 0.0f, rc = 1.0f;
             if (k == HK_SOLID) { l = p.lambda_s; rc = p.rho_c_s; }
@@ -950,17 +977,6 @@ k_heat_rows(const FParams p, int tiles_x, int ntiles, const typename P::tst *__r
             sV[y0 + c][tx] = uy[c];
         }
         __syncthreads();
-        // neighbour columns and rows, clamped into the tile (edge cells compute
-        // values nobody reads from them)
-        const int xl = tx > 0 ? tx - 1 : 0, xr = tx < BW - 1 ? tx + 1 : BW - 1;
-        const int yb = y0 > 0 ? y0 - 1 : 0, yt = y0 + R < SH ? y0 + R : SH - 1;
-        // rows y0 - 1 .. y0 + R of column x - 1 / x + 1 (index j = row - y0 + 1)
-        auto column = [&](const float (*a)[BW], int x, float *v) {
-            v[0] = a[yb][x];
-            #pragma unroll
-            for (int j = 0; j < R; j++) v[j + 1] = a[y0 + j][x];
-            v[R + 1] = a[yt][x];
-        };
         // ---- per-step coefficients (neighbour order E, N, W, S, NE, NW, SW, SE) ----
         {
             // conduction: 6 w_a lambda_face / (rho c), lambda_face = 2 / (1/l0 + 1/la)
@@ -1043,6 +1059,9 @@ k_heat_rows(const FParams p, int tiles_x, int ntiles, const typename P::tst *__r
                 c2[c] = g0 * B;
             }
         }
+        };
+        if (interior(cyt)) prepare(std::true_type{});
+        else prepare(std::false_type{});
         // ---- four RK stages; stage s reads sT[s & 1], writes sT[(s + 1) & 1] ----
         if (!iso) {
             #pragma unroll
