@@ -29,8 +29,9 @@ const FlowVariant flows32[] = {
     FLOWP(PolicyF32, 32, 8, 1, 3), FLOWV(PolicyF32, 32, 8, 2, 3), FLOWV(PolicyF32, 64, 4, 2, 3),
 };
 const HeatVariant heats32[] = {
-    HEATS(PolicyF32, 64, 10, 3, 1), HEATS(PolicyF32, 64, 8, 4, 1), HEATS(PolicyF32, 64, 6, 5, 1),
-    HEATS(PolicyF32, 64, 7, 4, 1), HEATS(PolicyF32, 64, 9, 3, 1), HEATS(PolicyF32, 32, 8, 4, 2),
+    HEATS(PolicyF32, 64, 6, 5, 1), HEATS(PolicyF32, 64, 8, 4, 1), HEATS(PolicyF32, 64, 10, 3, 1),
+    HEATS(PolicyF32, 64, 6, 6, 1),
+    HEATS(PolicyF32, 32, 8, 4, 2),
     HEATV(PolicyF32, 32, 16, 32, 8), HEATV(PolicyF32, 64, 32, 32, 16),
 };
 const FlowVariant flows16[] = {FLOWP(PolicyF16, 32, 8, 2, 2), FLOWV(PolicyF16, 32, 8, 2, 3)};
