@@ -339,6 +339,51 @@ def measure_validation():
             "precision": prec, "seconds": time.perf_counter() - t0}
 
 
+def measure_paper_scale(lbm, W, steps):
+    """The paper-scale runs: 400 x 600 fluid over 30 heater rows, superheats
+    0.05 / 0.10 / 0.15 / 0.20 Tc, nucleate spots and the noisy bottom, each
+    in FP64 and FP32 (the 8 runs of a precision stepped together).  Reports
+    per run the time averages of the heater-bottom flux and the vapour
+    fraction over the second half and FP32's deviation from FP64."""
+    cases = [(d, m) for m in ("spots", "noise") for d in (0.05, 0.10, 0.15, 0.20)]
+    out = {"setting": f"400x600 fluid + 30 heater rows, {steps} steps, averages over the second half", "runs": []}
+    res = {}
+    for prec in ("fp64", "fp32"):
+        runs = [lbm.Run(W.paper_scale(d, m, precision=prec), series_capacity=steps + 8) for d, m in cases]
+        t0 = time.perf_counter()
+        b = lbm.Batch(runs)
+        b.step(steps)
+        try:
+            b.sync()
+        except lbm.LbmError:
+            pass
+        b.close()
+        dt = time.perf_counter() - t0
+        out[f"{prec}_seconds"] = dt
+        out[f"{prec}_mlups"] = len(runs) * 400 * 600 * steps / dt / 1e6
+        for (d, m), r in zip(cases, runs):
+            try:
+                r.sync()
+                ser = r.series(0, steps)
+                res[(d, m, prec)] = (float(ser[steps // 2:, 0].mean()), float(ser[steps // 2:, 2].mean()))
+            except lbm.LbmError as e:
+                res[(d, m, prec)] = str(e)
+            r.close()
+    worst = 0.0
+    for d, m in cases:
+        a, c = res[(d, m, "fp64")], res[(d, m, "fp32")]
+        row = {"superheat_over_Tc": d, "bc": m}
+        if isinstance(a, tuple) and isinstance(c, tuple):
+            row.update(q_fp64=a[0], q_fp32=c[0], vf_fp64=a[1], vf_fp32=c[1],
+                       q_rel_dev=c[0] / a[0] - 1.0, vf_rel_dev=c[1] / a[1] - 1.0)
+            worst = max(worst, abs(row["q_rel_dev"]), abs(row["vf_rel_dev"]))
+        else:
+            row.update(fault_fp64=None if isinstance(a, tuple) else a, fault_fp32=None if isinstance(c, tuple) else c)
+        out["runs"].append(row)
+    out["max_rel_dev"] = worst
+    return out
+
+
 def measure_chf(lbm, W, steps):
     """Boiling curve on a 256 x 384 domain over 16 heater rows (constant
     bottom with nucleate spots): time-averaged heater-bottom flux Q'' over
@@ -533,6 +578,10 @@ def run_ours(args):
     if rank == 0 and not args.no_validation:
         validation = measure_validation()
 
+    paper = None
+    if args.paper_scale and rank == 0:
+        paper = measure_paper_scale(lbm, W, args.paper_scale_steps)
+
     chf = None
     if args.chf:
         chf = measure_chf(lbm, W, args.chf_steps)
@@ -574,6 +623,7 @@ def run_ours(args):
             "serve": serve,
             "chf": chf,
             "wetting": wetting,
+            "paper_scale": paper,
             "validation": validation,
         }
         print(json.dumps(line), flush=True)
@@ -599,6 +649,8 @@ def main():
     ap.add_argument("--no-wetting", action="store_true", help="skip the contact-angle check of the c_w values")
     ap.add_argument("--no-validation", action="store_true", help="skip the Laplace / film-boiling / precision cases")
     ap.add_argument("--wetting-steps", type=int, default=30000)
+    ap.add_argument("--paper-scale", action="store_true", help="also run the 400x600 FP64 vs FP32 comparison")
+    ap.add_argument("--paper-scale-steps", type=int, default=100000)
     ap.add_argument("--chf", action="store_true", help="also measure the FP32 vs FP64 boiling curve")
     ap.add_argument("--chf-steps", type=int, default=20000)
     ap.add_argument("--serve", action="store_true", help="also measure the request loop")
