@@ -387,13 +387,13 @@ def measure_paper_scale(lbm, W, steps):
 def measure_chf(lbm, W, steps):
     """Boiling curve on a 256 x 384 domain over 16 heater rows (constant
     bottom with nucleate spots): time-averaged heater-bottom flux Q'' over
-    the second half of `steps` steps at 7 superheats, in FP32 and FP64 (all
-    14 runs in one batch).  CHF = max Q'' over the superheats."""
+    the second half of `steps` steps at 7 superheats, in FP32, FP64 and FP16
+    storage (all 21 runs in one batch).  CHF = max Q'' over the superheats."""
     base = W.sweep(1)[0].replace(nx=256, nf=384, ns=16, liquid_rows=128, bc_mode="spots",
                                  spot_x=W.scaled_spots(256), spot_half_width=3,
                                  c_w_spot=W.DEFAULT_CW_SPOTS, g=W.stable_gravity(384, 128), seed=21)
     dts = [0.04, 0.08, 0.12, 0.16, 0.20, 0.24, 0.28]
-    cfgs = [base.replace(T_b_over_Tc=0.86 + d, precision=p) for p in ("fp32", "fp64") for d in dts]
+    cfgs = [base.replace(T_b_over_Tc=0.86 + d, precision=p) for p in ("fp32", "fp64", "fp16") for d in dts]
     runs = [lbm.Run(c, series_capacity=steps + 8) for c in cfgs]
     alive = list(range(len(runs)))
     fault = [None] * len(runs)
@@ -426,17 +426,23 @@ def measure_chf(lbm, W, steps):
     for r in runs:
         r.close()
     n = len(dts)
-    q32, q64 = q[:n], q[n:]
+    q32, q64, q16 = q[:n], q[n:2 * n], q[2 * n:]
     both = [j for j in range(n) if q32[j] is not None and q64[j] is not None]
     c32 = max(q32[j] for j in both) if both else None
     c64 = max(q64[j] for j in both) if both else None
+    all3 = [j for j in both if q16[j] is not None]
+    c16 = max(q16[j] for j in all3) if all3 else None
+    c64b = max(q64[j] for j in all3) if all3 else None
     return {"domain": "256x384 fluid + 16 heater rows, spots", "steps": steps, "superheats_over_Tc": dts,
-            "q_fp32": q32, "q_fp64": q64, "fault_step_fp32": fault[:n], "fault_step_fp64": fault[n:],
-            "chf_fp32": c32, "chf_fp64": c64,
+            "q_fp32": q32, "q_fp64": q64, "q_fp16": q16, "fault_step_fp32": fault[:n],
+            "fault_step_fp64": fault[n:2 * n], "fault_step_fp16": fault[2 * n:],
+            "chf_fp32": c32, "chf_fp64": c64, "chf_fp16": c16,
             "chf_superheat_fp32": dts[q32.index(c32)] if both else None,
             "chf_superheat_fp64": dts[q64.index(c64)] if both else None,
             "chf_rel_error": abs(c32 - c64) / abs(c64) if both else None,
             "max_rel_error_curve": max(abs(q32[j] - q64[j]) / abs(q64[j]) for j in both) if both else None,
+            "chf_rel_error_fp16": abs(c16 - c64b) / abs(c64b) if all3 else None,
+            "max_rel_error_curve_fp16": max(abs(q16[j] - q64[j]) / abs(q64[j]) for j in all3) if all3 else None,
             "seconds": dt}
 
 
