@@ -67,11 +67,16 @@ def max_sm_mhz() -> float:
 
 
 def kernel_source_hash() -> str:
-    """Hash of the kernel sources; an ncu summary taken on other sources is stale."""
+    """Hash of the kernel sources' code (comments and white space removed):
+    an ncu summary taken on other code is stale, one taken before a comment
+    edit is not."""
     h = hashlib.sha256()
     for name in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, "paper_1911_10747_gb300", "csrc", name), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_1911_10747_gb300", "csrc", name)) as fh:
+            text = fh.read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        h.update("".join(text.split()).encode())
     return h.hexdigest()[:16]
 
 

@@ -26,7 +26,10 @@
  *     stream the library creates).  Numerical faults found by the kernels
  *     (negative pseudopotential radicand, non-finite density or temperature)
  *     are latched in a device word and reported as LBM_E_NUMERIC by the next
- *     call that synchronises (lbm_sync and every read-back).
+ *     call that synchronises (lbm_sync and every read-back); a staged-copy
+ *     wait that ran out is reported the same way as LBM_E_TIMEOUT.
+ *   - Page-locked host arrays given to lbm_set_state are read by the device
+ *     directly; pageable ones are staged through a device buffer.
  *   - A handle is not thread-safe; distinct handles are independent.
  *
  * Layouts (row-major, x fastest): populations f[9][NF][NX] in the order of
@@ -53,7 +56,8 @@ enum lbm_status {
     LBM_E_NOMEM = 2,   /* device or host allocation failed */
     LBM_E_CUDA = 3,    /* a CUDA runtime call failed (message has the CUDA error) */
     LBM_E_NUMERIC = 4, /* the kernels latched a numerical fault */
-    LBM_E_TIMEOUT = 5, /* reserved: a bounded device wait gave up */
+    LBM_E_TIMEOUT = 5, /* a kernel's bounded wait for its staged data ran out (100 ms);
+                          the step's results are invalid, the context stays usable */
     LBM_E_STATE = 6    /* call not valid in the handle's current state */
 };
 

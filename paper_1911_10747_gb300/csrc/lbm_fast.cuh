@@ -78,7 +78,6 @@ __device__ __forceinline__ float bottom_theta(const FParams &q, int x, long long
     return q.dTb;
 }
 
-__device__ __forceinline__ float frcp(float x) { return __frcp_rn(x); }
 // Single-instruction PTX approximations (documented maximum error 1 ulp for
 // the reciprocal, 2^-23 relative for the root), flushing subnormals: no
 // value of the FP32 path is subnormal, and this skips the special-range
@@ -111,13 +110,6 @@ __device__ __forceinline__ float psi_fast(const FParams &q, float rho, float T, 
     return fast_sqrt(arg);
 }
 
-// ============================================================================
-// Flow kernel, FP32 shifted populations.  Tile TX = BX columns x TY = BY * RY
-// rows; thread (tx, ty) owns rows ty + k BY.  psi tile with a one-site halo
-// in shared memory; the halo ring is recomputed from the neighbours'
-// populations (L2 hits).  Rows outside the fluid hold psi = 0 (walls add
-// their pull through F_ads) or, for an open top, the psi of the top row.
-// ============================================================================
 // Population stores.  FP32: plain.  FP16 storage rounds stochastically: a
 // dither drawn uniformly from the 13 float mantissa bits a half drops is
 // added to the magnitude, which is then truncated (Connolly, Higham and Mary,
@@ -282,6 +274,14 @@ __device__ __forceinline__ void flow_site(const FParams &p, const float *f, floa
     }
 }
 
+// ============================================================================
+// Flow kernel, FP32 shifted populations, one tile per block.  Tile TX = BX
+// columns x TY = BY * RY rows; thread (tx, ty) owns rows ty + k BY.  psi tile
+// with a one-site halo in shared memory; the halo ring is recomputed from the
+// neighbours' populations (L2 hits).  Rows outside the fluid hold psi = 0
+// (walls add their pull through F_ads) or, for an open top, the psi of the
+// top row.
+// ============================================================================
 template <class P, int BX, int BY, int RY, int MINB>
 __global__ void __launch_bounds__(BX *BY, MINB)
 k_flow_fast(const FParams p, const typename P::fst *__restrict__ fin, typename P::fst *__restrict__ fout,
@@ -405,6 +405,12 @@ k_flow_fast(const FParams p, const typename P::fst *__restrict__ fin, typename P
     if (errbits) atomicOr(err, errbits);
 }
 
+// Flow kernel, FP32, persistent: SMs x resident blocks, each looping over
+// TX x TY tiles (same per-site work as k_flow_fast, through flow_site).
+// While a tile is computed, the next tile's populations, T and psi-ring
+// sites are already loading into registers.  Tiles that touch no boundary
+// use flow_site's interior form.  WIDE (compile time) promises nx >= TX + 1
+// and, if periodic in y, nf >= TY + 2, so that index wraps are a compare.
 template <class P, int BX, int BY, int RY, int MINB, bool WIDE>
 __global__ void __launch_bounds__(BX *BY, MINB)
 k_flow_pers(const FParams p, int tiles_x, int ntiles, const typename P::fst *__restrict__ fin, typename P::fst *__restrict__ fout,
