@@ -229,3 +229,17 @@ def test_degenerate_domains(kw, precision):
     errs = field_errors(g, o)
     tol = TOL64 if precision == "fp64" else 1e-4
     assert all(v <= tol for v in errs.values()), errs
+
+
+@pytest.mark.parametrize("bc", ["spots", "noise"])
+def test_paper_scale_domain_against_oracle(bc):
+    """The 400 x 600 + 30 paper-scale domain, 20 steps: FP64 to 1e-12 per
+    site, FP32 within its rounding bound."""
+    cfg = W.paper_scale(0.1, bc, precision="fp64").replace(rho_mean=2.42)
+    g, o = run_both(cfg, 20)
+    errs = field_errors(g, o)
+    assert all(v <= TOL64 for v in errs.values()), errs
+    g32 = lbm.Run(cfg.replace(precision="fp32")).step(20)
+    g32.sync()
+    errs32 = field_errors(g32, o)
+    assert errs32["rho"] < 1e-5 and errs32["T"] < 1e-6, errs32
