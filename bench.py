@@ -179,6 +179,14 @@ def aggregate_over_ranks(ms: float, sites: int, steps: int, device=None):
     return ms_max, ws * sites * steps / (ms_max / 1e3) / 1e6
 
 
+def workload_config(nx: int, nf: int, ns: int, ws: int, precision: str = "fp32") -> dict:
+    """The `config` object of both arms' JSON lines: the workload they time."""
+    return {"workload": WORKLOAD if precision == "fp32" else WORKLOAD.replace("FP32 shifted", precision.upper()),
+            "nx": nx, "ny_fluid": nf, "ny_solid": ns,
+            "l2": "inputs larger than L2 (populations alone 2 x 151 MB in FP32)",
+            "parallelism": f"replicas x{ws}" if ws > 1 else "single run"}
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -188,13 +196,13 @@ def run_reference(args):
     for _ in range(args.warmup and 1):
         oracle_sample(cfg, 1)  # warm caches / page in once
     mlups, dt = oracle_sample(cfg, max(1, args.steps))
-    sample = f"{max(1, args.steps)} step(s) of the full 2048x2048+64 workload, FP64 oracle, 1 thread"
+    sample = (f"{max(1, args.steps)} step(s) of the full 2048x2048+64 workload by the FP64 CPU oracle, "
+              "1 thread (the same workload the GPU arm times in FP32)")
     line = {"impl": "reference", "metric": METRIC, "value": mlups, "unit": "MLUPS", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1000 / max(1, args.steps),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded initial density noise and bottom-temperature noise)",
-            "config": {"workload": WORKLOAD.replace("FP32 shifted populations", "FP64 CPU oracle"),
-                       "nx": cfg.nx, "ny_fluid": cfg.nf, "ny_solid": cfg.ns},
+            "config": workload_config(cfg.nx, cfg.nf, cfg.ns, 1),
             "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -614,10 +622,7 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": {"fp32": "f32", "fp64": "f64", "fp16": "f16-storage/f32"}[args.precision],
             "data": "synthetic (seeded initial density noise and bottom-temperature noise)",
-            "config": {"workload": WORKLOAD if args.precision == "fp32" else WORKLOAD.replace("FP32 shifted", args.precision.upper()),
-                       "nx": cfg.nx, "ny_fluid": cfg.nf, "ny_solid": cfg.ns,
-                       "l2": "inputs larger than L2 (populations alone 2 x 151 MB in FP32)",
-                       "parallelism": f"replicas x{ws}" if ws > 1 else "single run"},
+            "config": workload_config(cfg.nx, cfg.nf, cfg.ns, ws, args.precision),
             "roofline": dict(dominant, step={"bound": "hbm", "achieved": step_achieved, "peak": hbm,
                                              "frac": step_achieved / hbm,
                                              "bytes_per_site": ALG_STEP_BYTES[args.precision]}),
