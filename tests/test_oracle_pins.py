@@ -202,3 +202,17 @@ def test_isotropic_gradient_and_laplacian_closed_forms():
     gx, gy, _ = O.grad_lap(np.sin(k * x))
     np.testing.assert_allclose(gx, math.sin(k) * np.cos(k * x), atol=1e-13)
     np.testing.assert_allclose(gy, 0.0, atol=1e-13)
+
+
+@pytest.mark.parametrize("omega", [0.1, 0.2, 0.344, 0.5])
+def test_peng_robinson_reproduces_its_acentric_factor(omega):
+    """The kappa(omega) correlation of the PR EOS (Eq. 13) was fitted so that
+    the EOS returns the acentric factor it is given: omega = -log10(p_sat at
+    0.7 Tc / p_c) - 1, with p_c = 0.07780 R Tc / b the PR critical pressure.
+    The oracle's Maxwell construction at 0.7 Tc recovers omega to 0.01 over a
+    range of omega -- a check of kappa and of the PR form together."""
+    import math
+    a, b, R = 2.0 / 49.0, 2.0 / 21.0, 1.0
+    rl, rv, ps = O.maxwell(0.7, a=a, b=b, R=R, omega=omega)
+    pc = 0.07780 * R * O.Tc(a, b, R) / b
+    assert -math.log10(ps / pc) - 1.0 == pytest.approx(omega, abs=0.01)
