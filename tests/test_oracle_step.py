@@ -237,3 +237,39 @@ def test_laplace_law_for_drops_in_a_periodic_box():
     dpR = [R * dp for R, dp in out]
     assert out[0][1] > out[1][1] > out[2][1] > 0
     assert max(dpR) / min(dpR) - 1 < 0.06, out
+
+
+@pytest.mark.parametrize("liquid_rows", [0, 7, 20, 32])
+def test_vapour_fraction_counts_the_vapour_rows_of_a_layered_state(liquid_rows):
+    """Frozen flow keeps the initial layer exactly (liquid rho_L below, vapour
+    rho_V above, no noise): the vapour fraction (sites with rho below
+    (rho_L + rho_V) / 2) is the share of vapour rows, and the mass is the
+    sum of the layer densities."""
+    nx, nf = 8, 32
+    cfg = W.RunConfig(nx=nx, nf=nf, ns=4, liquid_rows=liquid_rows, frozen_flow=True, isothermal=True,
+                      init_noise=0.0, bc_mode="spots", g=0.0)
+    r = O.OracleRun(cfg)
+    r.step(2)
+    d = r.diagnostics()
+    assert d["vapour_fraction"] == (nf - liquid_rows) / nf
+    assert d["mass"] == pytest.approx(nx * (liquid_rows * cfg.rho_L + (nf - liquid_rows) * cfg.rho_V), rel=1e-14)
+
+
+def test_vapour_fraction_threshold_is_the_mean_coexistence_density():
+    """Sites just below (rho_L + rho_V) / 2 count as vapour, sites at or just
+    above it do not: a wrong threshold or comparison changes the count."""
+    nx, nf = 8, 16
+    cfg = W.RunConfig(nx=nx, nf=nf, ns=4, liquid_rows=8, frozen_flow=True, isothermal=True,
+                      init_noise=0.0, bc_mode="spots", g=0.0)
+    r = O.OracleRun(cfg)
+    thr = 0.5 * (cfg.rho_L + cfg.rho_V)
+    rng = np.random.default_rng(11)
+    pick = rng.integers(0, 3, size=(nf, nx))
+    rho = np.choose(pick, [thr * (1 - 1e-9), thr, thr * (1 + 1e-9)])
+    f = np.zeros((9, nf, nx))
+    f[0] = rho  # all mass at rest: the zeroth moment is rho without rounding
+    r.set_f(f)
+    r.step(1)
+    np.testing.assert_array_equal(r.rho, rho)
+    assert r.diagnostics()["vapour_fraction"] == np.count_nonzero(r.rho < thr) / (nx * nf)
+    assert r.diagnostics()["vapour_fraction"] == np.count_nonzero(pick == 0) / (nx * nf)
