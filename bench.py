@@ -43,7 +43,8 @@ HEAT_FLOPS = 274
 # FP32 peak from unit counts and clock: 152 SMs x 128 FP32 lanes x 2 flops x clock
 FP32_LANES = 152 * 128
 PROFILES = {"flow": os.path.join(ROOT, "profiles", "flow_kernel_2048x2048_fp32.md"),
-            "heat": os.path.join(ROOT, "profiles", "heat_kernel_2048x2048_fp32.md")}
+            "heat": os.path.join(ROOT, "profiles", "heat_kernel_2048x2048_fp32.md"),
+            "fp64": os.path.join(ROOT, "profiles", "fp64_kernels_1024x1024.md")}
 
 
 def peaks():
@@ -90,6 +91,21 @@ def ncu_traffic(kind: str, variant: str):
         return None
     m = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", text)
     t = re.search(r"dram_bytes_per_full_launch\[" + re.escape(variant) + r"\]:\s*([0-9.eE+]+)", text)
+    if not m or not t or m.group(1) != kernel_source_hash():
+        return None
+    return float(t.group(1))
+
+
+def ncu_fp64_flops(kind: str):
+    """FP64 flops per site (DADD + DMUL + 2 DFMA executed, from ncu) of the
+    FP64 flow or heat kernel in the committed summary, or None when absent
+    or taken on a different kernel source."""
+    try:
+        text = open(PROFILES["fp64"]).read()
+    except OSError:
+        return None
+    m = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", text)
+    t = re.search(r"fp64_flops_per_site\[" + re.escape(kind) + r"\]:\s*([0-9.eE+]+)", text)
     if not m or not t or m.group(1) != kernel_source_hash():
         return None
     return float(t.group(1))
@@ -534,6 +550,9 @@ def run_ours(args):
                  "frac": heat_achieved / fp32_peak, "kernel": "k_heat", "flops_per_site": HEAT_FLOPS,
                  "traffic": ncu_traffic("heat", vnames[1]) if args.precision == "fp32" else None,
                  "peak_source": "152 SMs x 128 FP32 lanes x 2 x max SM clock"}
+    # the same fraction against the FMA throughput measured on this GPU (context)
+    fma32 = lbm.peak_fma(32, device=local)
+    heat_roof.update(measured_fma_peak=fma32, frac_of_measured_fma=heat_achieved / fma32)
     step_ms = ms_max / args.steps
     step_achieved = ALG_STEP_BYTES[args.precision] * sites / (step_ms / 1e3) / 1e9
     dominant = flow_roof if kms[0] >= kms[1] else heat_roof
@@ -581,6 +600,19 @@ def run_ours(args):
         fp64 = {"value": sites / (ms64 / 1e3) / 1e6, "unit": "MLUPS", "ms_per_step": ms64,
                 "kernel_ms": {"flow": k64ms[0], "heat": k64ms[1], "diag": k64ms[2]},
                 "flow_hbm_frac": ALG_FLOW_BYTES["fp64"] * sites / (k64ms[0] / 1e3) / 1e9 / hbm}
+        # FP64 is arithmetic-bound: flops counted by ncu against the measured
+        # FP64 FMA throughput of this GPU
+        fma64 = lbm.peak_fma(64, iters=1024, device=local)
+        fl, fh = ncu_fp64_flops("flow"), ncu_fp64_flops("heat")
+        fp64["fma_peak_tflops"] = fma64
+        if fl is not None and fh is not None:
+            ach = (fl * sites / (k64ms[0] / 1e3) / 1e12, fh * cfg.temperature_sites / (k64ms[1] / 1e3) / 1e12)
+            fp64["alu_roofline"] = {
+                "flow": {"bound": "fp64_alu", "achieved": ach[0], "peak": fma64, "unit": "TFLOP/s",
+                         "frac": ach[0] / fma64, "flops_per_site": fl},
+                "heat": {"bound": "fp64_alu", "achieved": ach[1], "peak": fma64, "unit": "TFLOP/s",
+                         "frac": ach[1] / fma64, "flops_per_site": fh},
+                "peak_source": "lbm_peak_fma(64): FMA chains on every SM, measured in this run"}
     else:
         run.close()
 

@@ -304,6 +304,19 @@ int lbm_diagnostics_static(const double *rho, const double *T, int32_t nx, int32
                            int32_t ny_solid, double lambda_s, double cv_chi, double rho_L,
                            double rho_V, double *out, void *stream);
 
+/* Measured FMA throughput of one GPU, the peak against which the
+ * arithmetic-bound kernels report their fraction.  The paper has no
+ * counterpart (it reports no timings).  bits = 32 or 64 selects float or
+ * double; device = CUDA ordinal (-1: the current device; the caller's current
+ * device is restored).  Every thread of SMs x 8 blocks of 256 runs eight
+ * independent chains of `iters` fused multiply-adds; one untimed launch, then
+ * one launch timed with CUDA events on a private stream; *tflops receives
+ * 2 x 8 x iters x threads / time in TFLOP/s.  Synchronous.  Allocates and
+ * frees one small device buffer.  Errors: LBM_E_INVAL (bits not 32 / 64,
+ * iters outside 1 .. 2^24, tflops NULL), LBM_E_CUDA; message via
+ * lbm_last_error(NULL). */
+int lbm_peak_fma(int32_t device, int32_t bits, int32_t iters, double *tflops);
+
 /* Message of the last error on h (or of the last failed lbm_create when h is
  * NULL).  Valid until the next call on the same handle. */
 const char *lbm_last_error(lbm_handle h);

@@ -1,11 +1,12 @@
 """Build the CUDA library liblbm_gb300.so in-tree for sm_103a.
 
-Three translation units compiled in parallel by nvcc, then linked:
+Six translation units compiled in parallel by nvcc, then linked:
   csrc/lbm_fp64.cu     FP64 kernels, -fmad=false (plain rounding of each op)
   csrc/lbm_fp32.cu     FP32 / FP16-storage kernels
   csrc/lbm_runtime.cu  host runtime and the C ABI of include/lbm.h
   csrc/lbm_static_diag.cu  the allocation-free diagnostics entry point
   csrc/lbm_server.cu   continuous-batching request loop (host code)
+  csrc/lbm_peak.cu     FMA-throughput probe (the arithmetic rooflines' peak)
 Host code is compiled with -ffp-contract=off so the FP64 constants derived
 on the host round the same way on x86-64 and AArch64.
 """
@@ -23,7 +24,7 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "liblbm_gb300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 UNITS = {"lbm_fp64.cu": ["-fmad=false"], "lbm_fp32.cu": [], "lbm_runtime.cu": [],
-         "lbm_static_diag.cu": ["-fmad=false"], "lbm_server.cu": []}
+         "lbm_static_diag.cu": ["-fmad=false"], "lbm_server.cu": [], "lbm_peak.cu": []}
 
 
 def nvcc() -> str:

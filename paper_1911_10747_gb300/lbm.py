@@ -33,7 +33,7 @@ EXPORTS = ("lbm_create", "lbm_destroy", "lbm_step", "lbm_sync", "lbm_step_count"
            "lbm_batch_create", "lbm_batch_step", "lbm_batch_sync", "lbm_batch_destroy",
            "lbm_batch_last_error", "lbm_device_bytes", "lbm_server_create", "lbm_server_submit",
            "lbm_server_tick", "lbm_server_status", "lbm_server_result", "lbm_server_counts",
-           "lbm_server_destroy", "lbm_server_last_error",
+           "lbm_server_destroy", "lbm_server_last_error", "lbm_peak_fma",
            "lbm_last_error",
            "lbm_status_string")
 
@@ -140,6 +140,7 @@ def load(path: str = LIB_PATH):
     L.lbm_diagnostics_static.argtypes = [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_int32,
                                          C.c_double, C.c_double, C.c_double, C.c_double, C.c_void_p,
                                          C.c_void_p]
+    L.lbm_peak_fma.argtypes = [C.c_int32, C.c_int32, C.c_int32, _D]
     L.lbm_last_error.argtypes = [C.c_void_p]
     L.lbm_last_error.restype = C.c_char_p
     L.lbm_status_string.argtypes = [C.c_int]
@@ -346,6 +347,15 @@ def diagnostics_static(rho_ptr: int, T_ptr: int, cfg, out_ptr: int, stream=None)
     rc = load().lbm_diagnostics_static(rho_ptr, T_ptr, cfg.nx, cfg.nf, cfg.ns, cfg.lambda_s, cfg.cv_chi,
                                        cfg.rho_L, cfg.rho_V, out_ptr, stream)
     _check(rc, None, "lbm_diagnostics_static")
+
+
+def peak_fma(bits: int, iters: int = 4096, device: int = -1) -> float:
+    """Measured FMA throughput (TFLOP/s) in float (bits = 32) or double
+    (bits = 64): lbm_peak_fma in include/lbm.h."""
+    v = C.c_double()
+    rc = load().lbm_peak_fma(device, bits, iters, C.byref(v))
+    _check(rc, None, "lbm_peak_fma")
+    return v.value
 
 
 class Batch:

@@ -84,3 +84,12 @@ def test_null_arguments(lib):
     assert lib.lbm_destroy(None) == lbm.LBM_OK
     assert lib.lbm_step(None, 1) == lbm.LBM_E_INVAL
     assert lib.lbm_step_count(None) == -1
+
+
+@pytest.mark.parametrize("bits, iters", [(16, 64), (64, 0), (32, (1 << 24) + 1)])
+def test_fma_probe_rejects_bad_arguments_on_the_host(lib, bits, iters):
+    v = C.c_double(-1.0)
+    assert lib.lbm_peak_fma(-1, bits, iters, C.byref(v)) == lbm.LBM_E_INVAL
+    assert "lbm_peak_fma" in lib.lbm_last_error(None).decode()
+    assert v.value == -1.0
+    assert lib.lbm_peak_fma(-1, 32, 64, None) == lbm.LBM_E_INVAL
