@@ -57,6 +57,7 @@ def peaks():
 
 
 KERNEL_SOURCES = ("lbm_device.cuh", "lbm_fast.cuh", "lbm_tma.cuh")
+FP64_SOURCES = ("lbm_device.cuh", "lbm_fp64.cu")  # the FP64 kernels and their launch shapes
 
 
 def max_sm_mhz() -> float:
@@ -67,12 +68,12 @@ def max_sm_mhz() -> float:
         return 2070.0
 
 
-def kernel_source_hash() -> str:
+def kernel_source_hash(names=KERNEL_SOURCES) -> str:
     """Hash of the kernel sources' code (comments and white space removed):
     an ncu summary taken on other code is stale, one taken before a comment
     edit is not."""
     h = hashlib.sha256()
-    for name in KERNEL_SOURCES:
+    for name in names:
         with open(os.path.join(ROOT, "paper_1911_10747_gb300", "csrc", name)) as fh:
             text = fh.read()
         text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
@@ -104,9 +105,9 @@ def ncu_fp64_flops(kind: str):
         text = open(PROFILES["fp64"]).read()
     except OSError:
         return None
-    m = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", text)
+    m = re.search(r"fp64_source_sha256_16:\s*([0-9a-f]+)", text)
     t = re.search(r"fp64_flops_per_site\[" + re.escape(kind) + r"\]:\s*([0-9.eE+]+)", text)
-    if not m or not t or m.group(1) != kernel_source_hash():
+    if not m or not t or m.group(1) != kernel_source_hash(FP64_SOURCES):
         return None
     return float(t.group(1))
 
@@ -512,7 +513,7 @@ def run_ours(args):
         hv = variants["heat"].index(args.heat_variant) if args.heat_variant else variants["selected"][1]
         run.select_variants(fv, hv)
     else:
-        run.autotune(5)
+        run.autotune(20)
     variants = run.variants()
     run.step(max(args.warmup, 3))
     run.sync()

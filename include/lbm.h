@@ -215,11 +215,13 @@ int lbm_variants(lbm_handle h, int kind, int *count, int *selected);
 const char *lbm_variant_name(lbm_handle h, int kind, int index);
 int lbm_select_variants(lbm_handle h, int flow, int heat);
 
-/* Autotuner: time `iters` launches of every flow variant and every heat
- * variant on the run's current state and keep the fastest pair.  The state,
- * the step counter and the diagnostics are left unchanged (the kernels write
- * only buffers that the next step overwrites).  best_ms (nullable, [2])
- * receives the winning average milliseconds per launch.  Synchronises. */
+/* Autotuner: on the run's current state, time `iters` flow + heat launch
+ * pairs for every flow variant (with the heat variant in use), keep the
+ * fastest, then the same for every heat variant, and keep that pair.  The
+ * state, the step counter and the diagnostics are left unchanged (the
+ * kernels write only buffers that the next step overwrites).  best_ms
+ * (nullable, [2]) receives the winning average milliseconds per flow + heat
+ * pair of each search.  Synchronises. */
 int lbm_autotune(lbm_handle h, int iters, double *best_ms);
 
 /* Batches of independent runs (the boiling-curve sweep, served requests).

@@ -93,6 +93,15 @@ __device__ __forceinline__ float fast_sqrt(float x) {  // x >= 0
     return r;
 }
 
+// Packed FP32 pairs (sm_100 and later): one instruction updates both halves
+// of a float2, each rounded as the scalar operation would be.
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, f2(-1.0f), a); }  // exact a - b
+__device__ __forceinline__ float2 rcp2(float2 a) { return make_float2(fast_rcp(a.x), fast_rcp(a.y)); }
+
 // psi(rho, T) of Eq. 12-13 in FP32 with approximate reciprocals / roots.
 __device__ __forceinline__ float psi_fast(const FParams &q, float rho, float T, unsigned &errbits) {
     const float t1 = fast_sqrt(T * q.inv_Tc);
@@ -468,7 +477,7 @@ k_flow_pers(const FParams p, int tiles_x, int ntiles, const typename P::fst *__r
         if (py) y = wy(y);
         return py || (y >= 0 && y < nf);
     };
-    auto fetch = [&](int txt, int tyt) {
+    auto fetch_ring = [&](int txt, int tyt) {
         const int x0 = txt * TX, y0 = tyt * TY;
         if (tid < RING && !frozen) {
             int hx, hy, x, y;
@@ -481,6 +490,9 @@ k_flow_pers(const FParams p, int tiles_x, int ntiles, const typename P::fst *__r
                 rT = ld_as<float>(Tfl + kk);
             }
         }
+    };
+    auto fetch_main = [&](int txt, int tyt) {
+        const int x0 = txt * TX, y0 = tyt * TY;
         #pragma unroll
         for (int r = 0; r < RY; r++) {
             const int lx = threadIdx.x, ly = threadIdx.y + r * BY;
@@ -502,7 +514,7 @@ k_flow_pers(const FParams p, int tiles_x, int ntiles, const typename P::fst *__r
     };
     float mass = 0.0f, nvap = 0.0f;
     int cxt = (int)blockIdx.x % tiles_x, cyt = (int)blockIdx.x / tiles_x;  // current tile
-    if ((int)blockIdx.x < ntiles) fetch(cxt, cyt);
+    if ((int)blockIdx.x < ntiles) { fetch_ring(cxt, cyt); fetch_main(cxt, cyt); }
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int x0 = cxt * TX, y0 = cyt * TY;
     int nxt = cxt + gdx, nyt = cyt + gdy;  // next tile of this block
@@ -513,6 +525,10 @@ k_flow_pers(const FParams p, int tiles_x, int ntiles, const typename P::fst *__r
         for (int i = 0; i < 9; i++) g[r][i] = pg[r][i];
         gT[r] = pTv[r];
     }
+    const bool more = tile + (int)gridDim.x < ntiles;
+    // the next tile's own sites load from here on, under this tile's psi and
+    // collision work; its ring sites once this tile's ring psi is done
+    if (more) fetch_main(nxt, nyt);
 
     // ---- own sites: density, psi ----
     #pragma unroll
@@ -538,8 +554,7 @@ k_flow_pers(const FParams p, int tiles_x, int ntiles, const typename P::fst *__r
         }
         s_psi[rslot] = psi;
     }
-    // the next tile's loads (own sites and ring) fly during this tile's collisions
-    if (tile + (int)gridDim.x < ntiles) fetch(nxt, nyt);
+    if (more) fetch_ring(nxt, nyt);
     __syncthreads();
 
     // ---- collide and push (tiles that touch no boundary skip the wall terms) ----
@@ -1151,6 +1166,337 @@ struct HeatRowsShape {
 };
 template <class P, int BW, int BY, int R, int MINB>
 int HeatRowsShape<P, BW, BY, R, MINB>::grid_blocks = 152;
+
+// ============================================================================
+// Heat kernel, FP32, paired columns.  The tiles, halo, strips and per-cell
+// algebra of k_heat_rows (64-column tiles, R-row strips per thread), but each
+// thread owns two columns of its strip, x and x + 32, and keeps every
+// per-cell value as a float2 (column x in .x, x + 32 in .y).  The arithmetic
+// then runs as packed FP32 instructions (one issue slot for two cells;
+// reciprocals and roots stay scalar), and shared memory holds the tile as
+// pairs (T[x], T[x + 32]) in slot x, so that a neighbour read is one 64-bit
+// load.  The west pair of lane x is slot x - 1 and its east pair slot x + 1,
+// taken modulo 32: lane 0 reads slot 31 and moves its .x (column 31, the
+// west neighbour of column 32) into .y; lane 31 reads slot 0 and moves its
+// .y (column 32, the east neighbour of column 31) into .x.  The other half of
+// those two pairs stands for columns -1 and 64, outside the tile, and is
+// read only by halo cells.
+// ============================================================================
+
+template <class P, int BY, int R, int MINB, bool WIDE>
+__global__ void __launch_bounds__(32 * BY, MINB)
+k_heat_pair(const FParams p, int tiles_x, int ntiles, const typename P::tst *__restrict__ Tin,
+            typename P::tst *__restrict__ Tout, const float *__restrict__ rho_i, const float *__restrict__ ux_i,
+            const float *__restrict__ uy_i, const long long *__restrict__ stepp, unsigned *__restrict__ err) {
+    constexpr int HW = 32, BW = 2 * HW, NSL = HW, H = 4, SH = R * BY, TXO = BW - 2 * H, TYO = SH - 2 * H;
+    __shared__ float2 sT[2][SH][NSL];
+    // 1/lambda, u_x, u_y of the tile for the coefficient pass; afterwards the
+    // same arrays (and gV) stage the next tile's raw T, rho, u_x, u_y, each
+    // slot written and read by its owning thread only
+    __shared__ float2 sL[SH][NSL], sU[SH][NSL], sV[SH][NSL], gV[SH][NSL];
+    const int tx = threadIdx.x, ty = threadIdx.y, y0 = R * ty;
+    const int so = tx, sl = (tx + HW - 1) & (HW - 1), sr = (tx + 1) & (HW - 1);  // own, west, east slots
+    const bool wrap_w = tx == 0, wrap_e = tx == HW - 1;  // lanes whose west / east pair is the wrapped one
+    const int nx = p.nx, nt = p.nt, ns = p.ns;
+    const bool py = (p.flags & FLAG_PERIODIC_Y) != 0;
+    const bool model_a = (p.flags & FLAG_MODEL_A) != 0;
+    const bool iso = (p.flags & FLAG_ISOTHERMAL) != 0;
+    const float tsat = p.T_sat;
+    unsigned errbits = 0;
+
+    float2 Tn[R], Tc[R], acc[R], kk[R][8], nks[R], c0[R], c2[R];
+    int pk = 0, pxa = 0, pxb = 0;  // kinds of the staged rows (3 bits per row) and their columns
+
+    const int gdx = (int)gridDim.x % tiles_x, gdy = (int)gridDim.x / tiles_x;
+    auto interior = [&](int tyt) {
+        const int rlo = tyt * TYO - H;
+        return !py && rlo >= ns && rlo + SH <= nt;
+    };
+    auto fetch_tile = [&](int txt, int tyt, auto itag) {
+        constexpr bool I = decltype(itag)::value;
+        const int x0 = txt * TXO, r0 = tyt * TYO;
+        const int xa = WIDE ? wrap1(x0 + tx - H, nx) : wrapi(x0 + tx - H, nx);
+        const int xb = WIDE ? wrap1(x0 + tx + HW - H, nx) : wrapi(x0 + tx + HW - H, nx);
+        pxa = xa;
+        pxb = xb;
+        pk = 0;
+        #pragma unroll
+        for (int c = 0; c < R; c++) {
+            int row = r0 + y0 + c - H, k;
+            if (I) k = HK_FLUID;
+            else if (py) { row = WIDE ? wrap1(row, nt) : wrapi(row, nt); k = HK_FLUID; }
+            else if (row < 0 || row > nt) k = HK_OUT;
+            else if (row == 0) k = HK_BOTTOM;
+            else if (row == nt) k = HK_GHOST;
+            else k = (row < ns) ? HK_SOLID : HK_FLUID;
+            pk |= k << (3 * c);
+            const bool inT = k == HK_SOLID || k == HK_FLUID, fl = k == HK_FLUID, gh = k == HK_GHOST;
+            const bool wa = k == HK_BOTTOM && model_a;  // Model A wall row: rho of the first fluid row
+            const int kta = inT ? row * nx + xa : 0, ktb = inT ? row * nx + xb : 0;
+            const int kfa = fl ? kta - ns * nx : (gh ? (nt - ns - 1) * nx + xa : (wa ? xa : 0));
+            const int kfb = fl ? ktb - ns * nx : (gh ? (nt - ns - 1) * nx + xb : (wa ? xb : 0));
+            float *dL = &sL[y0 + c][so].x, *dU = &sU[y0 + c][so].x, *dV = &sV[y0 + c][so].x, *dW = &gV[y0 + c][so].x;
+            cp_async4(dL, Tin + kta, inT);
+            cp_async4(dL + 1, Tin + ktb, inT);
+            cp_async4(dU, rho_i + kfa, fl || gh || wa);
+            cp_async4(dU + 1, rho_i + kfb, fl || gh || wa);
+            cp_async4(dV, ux_i + kfa, fl);
+            cp_async4(dV + 1, ux_i + kfb, fl);
+            cp_async4(dW, uy_i + kfa, fl);
+            cp_async4(dW + 1, uy_i + kfb, fl);
+        }
+    };
+    auto fetch = [&](int txt, int tyt) {
+        if (interior(tyt)) fetch_tile(txt, tyt, std::true_type{});
+        else fetch_tile(txt, tyt, std::false_type{});
+    };
+    const float w1 = 1.0f / 9.0f, w2 = 1.0f / 36.0f;
+    int cxt = (int)blockIdx.x % tiles_x, cyt = (int)blockIdx.x / tiles_x;
+    if ((int)blockIdx.x < ntiles) fetch(cxt, cyt);
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        int nxt = cxt + gdx, nyt = cyt + gdy;
+        if (nxt >= tiles_x) { nxt -= tiles_x; nyt += 1; }
+        const bool more = tile + (int)gridDim.x < ntiles;
+        // neighbour rows, clamped into the tile (edge cells compute values
+        // nobody reads from them)
+        const int yb = y0 > 0 ? y0 - 1 : 0, yt = y0 + R < SH ? y0 + R : SH - 1;
+        // rows y0 - 1 .. y0 + R of the west / east neighbour pairs (index
+        // j = row - y0 + 1), the wrapped halves moved into place
+        auto west = [&](const float2 (*a)[NSL], float2 *v) {
+            v[0] = a[yb][sl];
+            #pragma unroll
+            for (int j = 0; j < R; j++) v[j + 1] = a[y0 + j][sl];
+            v[R + 1] = a[yt][sl];
+            #pragma unroll
+            for (int j = 0; j < R + 2; j++) v[j].y = wrap_w ? v[j].x : v[j].y;
+        };
+        auto east = [&](const float2 (*a)[NSL], float2 *v) {
+            v[0] = a[yb][sr];
+            #pragma unroll
+            for (int j = 0; j < R; j++) v[j + 1] = a[y0 + j][sr];
+            v[R + 1] = a[yt][sr];
+            #pragma unroll
+            for (int j = 0; j < R + 2; j++) v[j].x = wrap_e ? v[j].y : v[j].x;
+        };
+        // ---- load and per-step coefficients (interior tiles: compile-time fluid) ----
+        auto prepare = [&](auto itag) {
+        constexpr bool I = decltype(itag)::value;
+        int kd[R];
+        float2 irc[R], rho[R], ux[R], uy[R], lam[R];
+        cp_async_wait_all();
+        #pragma unroll
+        for (int c = 0; c < R; c++) {
+            const float2 Tr = sL[y0 + c][so];
+            rho[c] = sU[y0 + c][so]; ux[c] = sV[y0 + c][so]; uy[c] = gV[y0 + c][so];
+            const int k = I ? (int)HK_FLUID : (pk >> (3 * c)) & 7;
+            kd[c] = k;
+            float2 T = Tr, l = f2(0.0f), rc = f2(1.0f);
+            if (k == HK_SOLID) { l = f2(p.lambda_s); rc = f2(p.rho_c_s); }
+            else if (k == HK_FLUID) { l = mul2(f2(p.cv_chi), rho[c]); rc = mul2(rho[c], f2(p.c_v)); }
+            else if (k == HK_BOTTOM) {
+                const long long n = *stepp;
+                T = make_float2(bottom_theta(p, pxa, n), bottom_theta(p, pxb, n));
+                l = model_a ? mul2(f2(p.cv_chi), rho[c]) : f2(p.lambda_s);
+            }
+            else if (k == HK_GHOST) l = mul2(f2(p.cv_chi), rho[c]);
+            Tn[c] = T; Tc[c] = T; irc[c] = rcp2(rc);
+            // 1/lambda: the harmonic mean of a link is 2 / (1/l0 + 1/la)
+            lam[c] = make_float2(l.x > 0.0f ? fast_rcp(l.x) : 1e30f, l.y > 0.0f ? fast_rcp(l.y) : 1e30f);
+        }
+        #pragma unroll
+        for (int c = 0; c < R; c++) {
+            sT[0][y0 + c][so] = Tn[c];
+            sT[1][y0 + c][so] = Tn[c];
+            sL[y0 + c][so] = lam[c];
+            sU[y0 + c][so] = ux[c];
+            sV[y0 + c][so] = uy[c];
+        }
+        __syncthreads();
+        // ---- per-step coefficients (neighbour order E, N, W, S, NE, NW, SW, SE) ----
+        {
+            // conduction: 6 w_a lambda_face / (rho c), lambda_face = 2 / (1/l0 + 1/la)
+            float2 Ll[R + 2], Lr[R + 2];
+            west(sL, Ll);
+            east(sL, Lr);
+            const float2 Lb = sL[yb][so], Lt = sL[yt][so];
+            #pragma unroll
+            for (int c = 0; c < R; c++) {
+                const float2 l0 = lam[c];
+                const float2 lN = c + 1 < R ? lam[c + 1] : Lt, lS = c > 0 ? lam[c - 1] : Lb;
+                const int k = kd[c];
+                const bool moves = (k == HK_SOLID || k == HK_FLUID) && !iso;
+                const float2 f12 = moves ? mul2(f2(12.0f), irc[c]) : f2(0.0f);
+                const float2 cax = mul2(f2(w1), f12), cdg = mul2(f2(w2), f12);
+                kk[c][0] = mul2(cax, rcp2(add2(l0, Lr[c + 1])));
+                kk[c][1] = mul2(cax, rcp2(add2(l0, lN)));
+                kk[c][2] = mul2(cax, rcp2(add2(l0, Ll[c + 1])));
+                kk[c][3] = mul2(cax, rcp2(add2(l0, lS)));
+                kk[c][4] = mul2(cdg, rcp2(add2(l0, Lr[c + 2])));
+                kk[c][5] = mul2(cdg, rcp2(add2(l0, Ll[c + 2])));
+                kk[c][6] = mul2(cdg, rcp2(add2(l0, Ll[c])));
+                kk[c][7] = mul2(cdg, rcp2(add2(l0, Lr[c])));
+                const float2 ks = add2(add2(add2(kk[c][0], kk[c][1]), add2(kk[c][2], kk[c][3])),
+                                       add2(add2(kk[c][4], kk[c][5]), add2(kk[c][6], kk[c][7])));
+                nks[c] = mul2(ks, f2(-1.0f));
+                c0[c] = f2(0.0f);
+                c2[c] = f2(0.0f);
+                acc[c] = f2(0.0f);
+            }
+        }
+        bool any_fluid = false;
+        #pragma unroll
+        for (int c = 0; c < R; c++) any_fluid |= kd[c] == HK_FLUID;
+        if (!iso && any_fluid) {
+            // advection (-u . grad T = sum_a adv_a T_a, adv_a = -3 w_a (e_a . u))
+            // and the (dp/dT)_rho div u source of Eq. 24, with the Eq. 27 gradient
+            float2 dd[R];
+            {
+                float2 Ul[R + 2], Ur[R + 2];
+                west(sU, Ul);
+                east(sU, Ur);
+                #pragma unroll
+                for (int c = 0; c < R; c++)
+                    dd[c] = fma2(f2(w1), sub2(Ur[c + 1], Ul[c + 1]),
+                                 mul2(f2(w2), add2(sub2(Ur[c + 2], Ul[c]), sub2(Ur[c], Ul[c + 2]))));
+            }
+            {
+                float2 Vl[R + 2], Vr[R + 2];
+                west(sV, Vl);
+                east(sV, Vr);
+                const float2 Vb = sV[yb][so], Vt = sV[yt][so];
+                #pragma unroll
+                for (int c = 0; c < R; c++) {
+                    const float2 vN = c + 1 < R ? uy[c + 1] : Vt, vS = c > 0 ? uy[c - 1] : Vb;
+                    dd[c] = add2(dd[c], fma2(f2(w1), sub2(vN, vS),
+                                             mul2(f2(w2), sub2(sub2(Vr[c + 2], Vl[c]), sub2(Vr[c], Vl[c + 2])))));
+                }
+            }
+            #pragma unroll
+            for (int c = 0; c < R; c++) {
+                if (kd[c] != HK_FLUID) continue;
+                const float2 vx = mul2(f2(-3.0f), ux[c]), vy = mul2(f2(-3.0f), uy[c]);
+                kk[c][0] = fma2(f2(w1), vx, kk[c][0]);            // e = ( 1,  0)
+                kk[c][1] = fma2(f2(w1), vy, kk[c][1]);            // e = ( 0,  1)
+                kk[c][2] = fma2(f2(-w1), vx, kk[c][2]);           // e = (-1,  0)
+                kk[c][3] = fma2(f2(-w1), vy, kk[c][3]);           // e = ( 0, -1)
+                kk[c][4] = fma2(f2(w2), add2(vx, vy), kk[c][4]);  // e = ( 1,  1)
+                kk[c][5] = fma2(f2(w2), sub2(vy, vx), kk[c][5]);  // e = (-1,  1)
+                kk[c][6] = fma2(f2(-w2), add2(vx, vy), kk[c][6]); // e = (-1, -1)
+                kk[c][7] = fma2(f2(w2), sub2(vx, vy), kk[c][7]);  // e = ( 1, -1)
+                const float2 r = rho[c];
+                const float2 br = mul2(f2(p.b), r);
+                const float2 omb = sub2(f2(1.0f), br), den = fma2(br, sub2(f2(2.0f), br), f2(1.0f));
+                const float2 iod = rcp2(mul2(omb, den));
+                const float2 pa = mul2(mul2(f2(p.a_kappa), mul2(r, r)), mul2(omb, iod));
+                const float2 A = fma2(pa, f2(-p.kappa_over_Tc), mul2(mul2(r, f2(p.R)), mul2(den, iod)));
+                const float2 B = mul2(pa, f2(p.B_coef));
+                const float2 g0 = mul2(mul2(f2(-3.0f), dd[c]), irc[c]);  // -div u / (rho c)
+                const float2 C1 = mul2(g0, A);
+                nks[c] = add2(nks[c], C1);
+                c0[c] = mul2(C1, f2(tsat));
+                c2[c] = mul2(g0, B);
+            }
+        }
+        };
+        if (interior(cyt)) prepare(std::true_type{});
+        else prepare(std::false_type{});
+        // ---- four RK stages; stage s reads sT[s & 1], writes sT[(s + 1) & 1] ----
+        if (!iso) {
+            #pragma unroll
+            for (int st = 0; st < 4; st++) {
+                const int m = st + 1;
+                const int rb = st & 1, wb = rb ^ 1;
+                if (st > 0) __syncthreads();  // the previous stage's writes are visible
+                // the coefficient arrays are no longer read: stage the next tile
+                if (st == 1 && more) fetch(nxt, nyt);
+                if (y0 + R - 1 < m || y0 >= SH - m) continue;  // whole warp outside the region
+                float2 Tl[R + 2], Tr[R + 2];
+                west(sT[rb], Tl);
+                east(sT[rb], Tr);
+                const float2 Tb = sT[rb][yb][so], Tt = sT[rb][yt][so];
+                float2 h[R];
+                #pragma unroll
+                for (int c = 0; c < R; c++) {
+                    const float2 t0 = Tc[c];
+                    const float2 tN = c + 1 < R ? Tc[c + 1] : Tt, tS = c > 0 ? Tc[c - 1] : Tb;
+                    // T_0 + T_sat > 0 in every cell whose value is used
+                    const float2 u = add2(t0, f2(tsat));
+                    float2 v = fma2(c2[c], make_float2(fast_sqrt(u.x), fast_sqrt(u.y)), c0[c]);
+                    v = fma2(kk[c][0], Tr[c + 1], v);
+                    v = fma2(kk[c][1], tN, v);
+                    v = fma2(kk[c][2], Tl[c + 1], v);
+                    v = fma2(kk[c][3], tS, v);
+                    v = fma2(kk[c][4], Tr[c + 2], v);
+                    v = fma2(kk[c][5], Tl[c + 2], v);
+                    v = fma2(kk[c][6], Tl[c], v);
+                    v = fma2(kk[c][7], Tr[c], v);
+                    h[c] = fma2(nks[c], t0, v);
+                }
+                #pragma unroll
+                for (int c = 0; c < R; c++) {
+                    if (st == 0) { acc[c] = h[c]; Tc[c] = fma2(f2(0.5f), h[c], Tn[c]); }
+                    else if (st == 1) { acc[c] = fma2(f2(2.0f), h[c], acc[c]); Tc[c] = fma2(f2(0.5f), h[c], Tn[c]); }
+                    else if (st == 2) { acc[c] = fma2(f2(2.0f), h[c], acc[c]); Tc[c] = add2(Tn[c], h[c]); }
+                    else acc[c] = add2(acc[c], h[c]);
+                    if (st < 3) sT[wb][y0 + c][so] = Tc[c];
+                }
+            }
+        } else if (more) {
+            __syncthreads();  // the coefficient arrays are staged into next
+            fetch(nxt, nyt);
+        }
+        // ---- write the tile (fixed cells have acc = 0) ----
+        const int x0 = cxt * TXO, r0 = cyt * TYO;
+        const int xa = x0 + tx - H, xb = x0 + tx + HW - H;
+        #pragma unroll
+        for (int c = 0; c < R; c++) {
+            const int hy = y0 + c;
+            const int row = r0 + hy - H;
+            if (hy >= H && hy < SH - H && row < nt) {
+                const float2 v = fma2(acc[c], f2(1.0f / 6.0f), Tn[c]);
+                if (tx >= H && xa < nx) {
+                    if (!(fabsf(v.x) < 1e30f)) errbits |= ERRW_NONFINITE_T;
+                    Tout[row * nx + xa] = v.x;
+                }
+                if (tx + HW < BW - H && xb < nx) {
+                    if (!(fabsf(v.y) < 1e30f)) errbits |= ERRW_NONFINITE_T;
+                    Tout[row * nx + xb] = v.y;
+                }
+            }
+        }
+        __syncthreads();  // shared tiles are rewritten by the next tile
+        cxt = nxt; cyt = nyt;
+    }
+    if (errbits) atomicOr(err, errbits);
+}
+
+template <class P, int BY, int R, int MINB>
+struct HeatPairShape {
+    static int grid_blocks;
+    static cudaError_t prepare() {
+        int dev = 0, sms = 0, per = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_heat_pair<P, BY, R, MINB, true>, 32 * BY, 0);
+        if (e != cudaSuccess) return e;
+        grid_blocks = sms * (per > 0 ? per : 1);
+        return cudaSuccess;
+    }
+    static cudaError_t launch(const DevParams &p, const StepBuffers &b, cudaStream_t s) {
+        constexpr int TXO = 64 - 8, TYO = R * BY - 8;
+        const int tx = (p.nx + TXO - 1) / TXO, ty = (p.nt + TYO - 1) / TYO;
+        const int ntiles = tx * ty;
+        const int g = ntiles < grid_blocks ? ntiles : grid_blocks;
+        const bool wide = p.nx >= 64 && (!(p.flags & FLAG_PERIODIC_Y) || p.nt >= R * BY);
+        auto k = wide ? k_heat_pair<P, BY, R, MINB, true> : k_heat_pair<P, BY, R, MINB, false>;
+        k<<<g, dim3(32, BY), 0, s>>>(
+            make_fparams(p), tx, ntiles, (const typename P::tst *)b.T_in, (typename P::tst *)b.T_out,
+            (const float *)b.rho, (const float *)b.ux, (const float *)b.uy, b.step, b.err);
+        return cudaGetLastError();
+    }
+};
+template <class P, int BY, int R, int MINB>
+int HeatPairShape<P, BY, R, MINB>::grid_blocks = 152;
 
 }  // namespace lbmgb
 

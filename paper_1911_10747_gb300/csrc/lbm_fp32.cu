@@ -21,6 +21,8 @@ cudaError_t diag(const DevParams &p, const StepBuffers &b, int nblk, cudaStream_
      FlowTmaShape<P, BY, RY, MB>::prepare}
 #define HEATS(P, BW, BY, R, MB) \
     {"heatrows_" #BW "x" #BY "x" #R, HeatRowsShape<P, BW, BY, R, MB>::launch, HeatRowsShape<P, BW, BY, R, MB>::prepare}
+#define HEATP(P, BY, R, MB) \
+    {"heatpair_64x" #BY "x" #R, HeatPairShape<P, BY, R, MB>::launch, HeatPairShape<P, BY, R, MB>::prepare}
 #define HEATV(P, TX, TY, BX, BY) \
     {"heat_" #TX "x" #TY "_t" #BX "x" #BY, HeatFastShape<P, TX, TY, BX, BY>::launch, HeatFastShape<P, TX, TY, BX, BY>::prepare}
 
@@ -32,6 +34,7 @@ const HeatVariant heats32[] = {
     HEATS(PolicyF32, 64, 6, 5, 1), HEATS(PolicyF32, 64, 8, 4, 1), HEATS(PolicyF32, 64, 10, 3, 1),
     HEATS(PolicyF32, 64, 6, 6, 1),
     HEATS(PolicyF32, 32, 8, 4, 2),
+    HEATP(PolicyF32, 8, 4, 1),
     HEATV(PolicyF32, 32, 16, 32, 8), HEATV(PolicyF32, 64, 32, 32, 16),
 };
 const FlowVariant flows16[] = {FLOWP(PolicyF16, 32, 8, 2, 2), FLOWV(PolicyF16, 32, 8, 2, 3)};

@@ -173,3 +173,29 @@ def test_fp32_bulk_copy_flow_in_a_periodic_box():
         g.sync()
         errs = field_errors(g, o)
         assert errs["rho"] < 1e-4, (names[fv], errs)
+
+
+@pytest.mark.parametrize("kw", [
+    dict(nx=150, nf=45, ns=5, liquid_rows=15, spot_x=(3, 80, 149), spot_half_width=2),
+    dict(nx=40, nf=33, ns=4, liquid_rows=11, top_mode="outflow", bc_mode="noise", spot_x=(), c_w_spot=()),
+    dict(nx=96, nf=40, ns=0, liquid_rows=13, bc_mode="sine", spot_x=(), c_w_spot=()),
+])
+def test_fp32_paired_column_heat_variants_against_the_oracle(kw):
+    """The heat kernels that hold two columns per thread as packed pairs:
+    several tiles across with a ragged last tile, a domain narrower than one
+    tile (columns wrap inside the tile), model A, each bottom mode."""
+    cfg = W.small_parity(precision="fp32").replace(rho_mean=2.3, **kw)
+    if cfg.bc_mode == "sine":
+        cfg = cfg.replace(sine_t0=5, sine_t1=50, sine_wavelength=48.0)
+    names = lbm.Run(cfg).variants()["heat"]
+    pair = [i for i, n in enumerate(names) if n.startswith("heatpair_")]
+    assert pair
+    o = O.OracleRun(cfg)
+    o.step(60)
+    for hv in pair:
+        g = lbm.Run(cfg)
+        g.select_variants(0, hv)
+        g.step(60)
+        g.sync()
+        errs = field_errors(g, o)
+        assert errs["rho"] < 1e-4 and errs["T"] < 1e-5, (names[hv], errs)
