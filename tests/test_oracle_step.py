@@ -273,3 +273,31 @@ def test_vapour_fraction_threshold_is_the_mean_coexistence_density():
     np.testing.assert_array_equal(r.rho, rho)
     assert r.diagnostics()["vapour_fraction"] == np.count_nonzero(r.rho < thr) / (nx * nf)
     assert r.diagnostics()["vapour_fraction"] == np.count_nonzero(pick == 0) / (nx * nf)
+
+
+def test_sine_bottom_condition_phase_amplitude_and_window():
+    """Sec. 3.2's fluctuating wall: T_b + 0.02 Tc sin(2 pi (x - lambda/4) /
+    lambda) strictly inside t0 < n < t1, the plain T_b outside.  With
+    lambda = 24 the minimum sits on column 0, the zero crossing on column 6,
+    the maximum on column 12, and two whole wavelengths average to T_b."""
+    nx, lam = 48, 24.0
+    cfg = W.RunConfig(nx=nx, nf=8, ns=4, liquid_rows=4, frozen_flow=True, isothermal=True,
+                      bc_mode="sine", init_noise=0.0, T_b_over_Tc=1.1, g=0.0,
+                      sine_amp_over_Tc=0.02, sine_wavelength=lam, sine_t0=1, sine_t1=4)
+    r = O.OracleRun(cfg)
+    tc = r.Tc
+    tb = 1.1 * tc
+    seen = {}
+    for n in range(5):  # step n -> n + 1 imposes T_b(x, n) on row 0
+        r.step(1)
+        seen[n] = r.T[0].copy()
+    for n in (0, 1, 4):
+        np.testing.assert_array_equal(seen[n], np.full(nx, tb))
+    x = np.arange(nx)
+    want = tb + 0.02 * tc * np.sin(2 * np.pi * (x - lam / 4) / lam)
+    for n in (2, 3):
+        np.testing.assert_allclose(seen[n], want, rtol=1e-14)
+        assert seen[n][0] == pytest.approx(tb - 0.02 * tc, rel=1e-14)
+        assert seen[n][12] == pytest.approx(tb + 0.02 * tc, rel=1e-14)
+        assert seen[n][6] == pytest.approx(tb, rel=1e-14)
+        assert seen[n].mean() == pytest.approx(tb, rel=1e-14)
