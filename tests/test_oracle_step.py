@@ -301,3 +301,32 @@ def test_sine_bottom_condition_phase_amplitude_and_window():
         assert seen[n][12] == pytest.approx(tb + 0.02 * tc, rel=1e-14)
         assert seen[n][6] == pytest.approx(tb, rel=1e-14)
         assert seen[n].mean() == pytest.approx(tb, rel=1e-14)
+
+
+@pytest.mark.parametrize("top_mode", ["outflow", "wall"])
+def test_open_top_keeps_a_uniform_flow_uniform(top_mode):
+    """A uniform horizontal flow at uniform density (equilibrium populations,
+    no gravity, no wall adhesion) is a steady state of the interior.  With
+    the open top (psi continued with zero normal gradient, the unknown
+    downward populations taken from the top row itself) the rows above the
+    disturbance climbing from the bottom wall -- two rows per step, one
+    through the psi stencil and one through streaming -- stay exactly
+    uniform after three steps; a top wall (bounce-back, no psi above)
+    changes the top row at once."""
+    nx, nf, U = 12, 16, 0.02
+    cfg = W.RunConfig(nx=nx, nf=nf, ns=4, liquid_rows=nf, top_mode=top_mode, isothermal=True,
+                      init_noise=0.0, g=0.0, bc_mode="spots", spot_x=(), c_w_spot=(), c_w_base=0.0)
+    r = O.OracleRun(cfg)
+    feq = O.inverse_moments(O.meq(cfg.rho_L, U, 0.0))
+    f0 = np.broadcast_to(feq[:, None, None], (9, nf, nx)).copy()
+    r.set_f(f0)
+    r.step(3)
+    f = r.f
+    if top_mode == "outflow":
+        np.testing.assert_allclose(f[:, 8:, :], f0[:, 8:, :], rtol=1e-13, atol=0)
+        np.testing.assert_allclose(r.ux[8:], U, rtol=1e-12)
+        np.testing.assert_allclose(r.uy[8:], 0.0, atol=1e-16)
+    else:
+        assert np.max(np.abs(f[:, -1, :] - f0[:, -1, :])) > 1e-6
+    # the bottom wall disturbs only the rows it has reached
+    assert np.max(np.abs(f[:, 0, :] - f0[:, 0, :])) > 1e-6
