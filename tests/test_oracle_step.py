@@ -330,3 +330,34 @@ def test_open_top_keeps_a_uniform_flow_uniform(top_mode):
         assert np.max(np.abs(f[:, -1, :] - f0[:, -1, :])) > 1e-6
     # the bottom wall disturbs only the rows it has reached
     assert np.max(np.abs(f[:, 0, :] - f0[:, 0, :])) > 1e-6
+
+
+def test_momentum_changes_by_the_total_force_in_a_periodic_box():
+    """Doubly periodic, no walls: the psi-psi force of Eq. 11 sums to zero
+    over the box (each pair of sites pulls equally and oppositely) and
+    streaming moves populations without changing their sums, so one step
+    changes the population momentum by the sum of Eq. 15 alone,
+    -g (M - N rho_bar) in y and nothing in x -- exactly, given the
+    half-force velocity of Eq. 10 and the forcing moments of Eq. 7 / 9.
+    rho_bar is set away from the true mean so that the sum is not zero."""
+    nx, ny, g = 24, 20, 3e-4
+    cfg = W.periodic_box(nx, ny, liquid_rows=8, init_noise=1e-2).replace(g=g)
+    r = O.OracleRun(cfg)
+    r.step(5)  # interfaces move: the psi force is far from zero site by site
+    ex = np.array([0, 1, 0, -1, 0, 1, -1, -1, 1], dtype=float)
+    ey = np.array([0, 0, 1, 0, -1, 1, 1, -1, -1], dtype=float)
+    f = r.f
+    M = f.sum()
+    rho_bar = M / (nx * ny) + 0.05
+    r.set_rho_bar(rho_bar)
+    jx0, jy0 = np.tensordot(ex, f, 1).sum(), np.tensordot(ey, f, 1).sum()
+    r.step(1)
+    f1 = r.f
+    jx1, jy1 = np.tensordot(ex, f1, 1).sum(), np.tensordot(ey, f1, 1).sum()
+    want = -g * (M - nx * ny * rho_bar)
+    assert abs(want) > 1e-3
+    assert jy1 - jy0 == pytest.approx(want, rel=1e-10)
+    assert abs(jx1 - jx0) < 1e-12 * M
+    assert f1.sum() == pytest.approx(M, rel=1e-14)
+    # the box is not at rest: the forces cancel in the sum, not site by site
+    assert np.max(r.rho * np.hypot(r.ux, r.uy)) > 1e-4
