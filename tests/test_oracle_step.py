@@ -361,3 +361,37 @@ def test_momentum_changes_by_the_total_force_in_a_periodic_box():
     assert f1.sum() == pytest.approx(M, rel=1e-14)
     # the box is not at rest: the forces cancel in the sum, not site by site
     assert np.max(r.rho * np.hypot(r.ux, r.uy)) > 1e-4
+
+
+@pytest.mark.parametrize("scale", [1.0, 1.2, 0.0])
+def test_neutral_wall_adhesion_cancels_the_missing_psi_neighbours(scale):
+    """Uniform liquid at rest over the heater, open top, no gravity.  On the
+    fluid row next to the wall the psi force of Eq. 11 lacks its three solid
+    neighbours: F_y = -G psi^2 (1/3 + 2/12) = psi^2 / 2 with G = -1.  The
+    adhesion of Eq. 14 from those neighbours, -psi sum w c_w e, adds
+    psi c_w / 2.  With c_w = -psi(rho_L, T_sat) the two cancel: without the
+    varpi term of Eq. 9 the fluid stays exactly at rest; with it (it uses
+    |F_m|^2, not zero on the wall row) one step keeps u = 0 everywhere and
+    changes the populations of the two rows next to the wall only.  Any
+    other c_w sets the wall row in motion at once."""
+    nx, nf = 12, 10
+    probe = W.RunConfig(nx=nx, nf=nf, ns=4, liquid_rows=nf)
+    r0 = O.OracleRun(probe)
+    psi_l, bad = O.psi(probe.rho_L, probe.T_sat_over_Tc * r0.Tc)
+    assert not bad and psi_l > 0
+    base = probe.replace(top_mode="outflow", isothermal=True, g=0.0, init_noise=0.0,
+                         bc_mode="spots", spot_x=(), c_w_spot=(), c_w_base=-scale * psi_l)
+    r = O.OracleRun(base)
+    f0 = r.f
+    r.step(1)
+    umax = np.max(np.hypot(r.ux, r.uy))
+    if scale != 1.0:
+        assert np.max(np.abs(r.uy[0])) > 1e-5 and np.max(np.abs(r.uy[1:])) == 0.0
+        return
+    assert umax < 1e-16
+    np.testing.assert_allclose(r.f[:, 2:, :], f0[:, 2:, :], rtol=1e-14, atol=0)
+    assert np.max(np.abs(r.f[:, 0, :] - f0[:, 0, :])) > 1e-3
+    r = O.OracleRun(base.replace(varpi=0.0))
+    r.step(5)
+    np.testing.assert_allclose(r.f, f0, rtol=1e-13, atol=0)
+    assert np.max(np.hypot(r.ux, r.uy)) < 1e-15
