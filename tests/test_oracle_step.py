@@ -395,3 +395,36 @@ def test_neutral_wall_adhesion_cancels_the_missing_psi_neighbours(scale):
     r.step(5)
     np.testing.assert_allclose(r.f, f0, rtol=1e-13, atol=0)
     assert np.max(np.hypot(r.ux, r.uy)) < 1e-15
+
+
+@pytest.mark.parametrize("phase", ["liquid", "vapour"])
+def test_shear_wave_decays_at_the_phase_viscosity(phase):
+    """Eq. 4-5: s7 = s8 = 1 / tau(rho), tau = tau_V + (rho - rho_V) / (rho_L -
+    rho_V) (tau_L - tau_V), tau = 3 nu + 1/2.  A shear wave u_x = U sin(k y) in
+    a uniform periodic box (no psi force: the density is uniform) decays as
+    exp(-nu k^2 t); its measured rate gives nu_L = 0.1 in the liquid and
+    nu_V = 1/6 in the vapour to within the lattice's O(k^2) error."""
+    nx, ny, U = 4, 64, 1e-3
+    cfg = W.periodic_box(nx, ny, liquid_rows=ny if phase == "liquid" else 0, init_noise=0.0)
+    rho = cfg.rho_L if phase == "liquid" else cfg.rho_V
+    nu = cfg.nu_L if phase == "liquid" else cfg.nu_V
+    r = O.OracleRun(cfg)
+    k = 2 * np.pi / ny
+    y = np.arange(ny)
+    f = np.zeros((9, ny, nx))
+    for j in range(ny):
+        f[:, j, :] = O.inverse_moments(O.meq(rho, U * np.sin(k * y[j]), 0.0))[:, None]
+    r.set_f(f)
+
+    def amplitude():
+        return 2.0 / ny * float(np.sum(r.ux.mean(axis=1) * np.sin(k * y)))
+
+    r.step(20)
+    a0 = amplitude()
+    n = 300
+    r.step(n)
+    a1 = amplitude()
+    rate = -np.log(a1 / a0) / (n * k * k)
+    assert rate == pytest.approx(nu, rel=5e-3)
+    # a shear wave still: u_y and the density ripple are second order in U
+    assert np.abs(r.uy).max() < 1e-6 * U and np.abs(r.rho - rho).max() < U * U * rho
