@@ -617,6 +617,34 @@ def run_ours(args):
     else:
         run.close()
 
+    # ---- FP16-storage probe on the same workload (populations stored as
+    # half, arithmetic in FP32) ----
+    fp16 = None
+    if not args.no_fp16 and args.precision == "fp32":
+        torch.cuda.empty_cache()
+        r16 = lbm.Run(W.large(precision="fp16", seed=3 + rank), stream=stream.cuda_stream, device=local)
+        r16.autotune(20)
+        r16.step(max(args.warmup, 3))
+        r16.sync()
+        k16 = max(20, min(1000, args.steps // 2))
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        r16.step(k16)
+        a1.record(stream)
+        a1.synchronize()
+        ms16 = a0.elapsed_time(a1) / k16
+        r16.set_timing(True)
+        r16.step(min(k16, 200))
+        k16ms, _ = r16.kernel_times()
+        v16 = r16.variants()
+        r16.close()
+        fl16 = ALG_FLOW_BYTES["fp16"] * sites / (k16ms[0] / 1e3) / 1e9
+        fp16 = {"value": sites / (ms16 / 1e3) / 1e6, "unit": "MLUPS", "ms_per_step": ms16, "steps": k16,
+                "kernel_ms": {"flow": k16ms[0], "heat": k16ms[1], "diag": k16ms[2]},
+                "variants": {"flow": v16["flow"][v16["selected"][0]], "heat": v16["heat"][v16["selected"][1]]},
+                "flow_roofline": {"bound": "hbm", "achieved": fl16, "peak": hbm, "unit": "GB/s", "frac": fl16 / hbm,
+                                  "bytes_per_site": ALG_FLOW_BYTES["fp16"]}}
+
     # ---- boiling-curve sweep: 48 runs batched (FP32, one concurrent graph)
     # versus the same runs one after another in FP64 ----
     sweep = None
@@ -668,6 +696,7 @@ def run_ours(args):
             "e2e": e2e,
             "cpu_baseline": cpu,
             "fp64": fp64,
+            "fp16": fp16,
             "sweep": sweep,
             "serve": serve,
             "chf": chf,
@@ -689,6 +718,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "fp16"])
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-fp16", action="store_true", help="skip the FP16-storage throughput block")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-sweep", action="store_true")

@@ -119,40 +119,55 @@ __device__ __forceinline__ float psi_fast(const FParams &q, float rho, float T, 
     return fast_sqrt(arg);
 }
 
+// stored population -> float
+__device__ __forceinline__ float to_f(float v) { return v; }
+__device__ __forceinline__ float to_f(__half v) { return __half2float(v); }
+
 // Population stores.  FP32: plain.  FP16 storage rounds stochastically: a
 // dither drawn uniformly from the 13 float mantissa bits a half drops is
 // added to the magnitude, which is then truncated (Connolly, Higham and Mary,
 // SIAM J. Sci. Comput. 43 (2021), "Stochastic rounding and its probabilistic
 // backward error analysis").  Expected stored value = exact value, so the
-// per-step rounding errors no longer add up to a drift of the mass; the
-// dither comes from an xorshift32 stream seeded per site and step (values
-// in the half-subnormal range keep round-to-nearest).
+// per-step rounding errors no longer add up to a drift of the mass (values
+// in the half-subnormal range keep round-to-nearest).  The dither: a 32-bit
+// key per launch from the seed and the step, one 32-bit hash of key and site
+// per site (C. Wellons' two-round multiply-xorshift mixer), then a linear
+// congruential step per store (Knuth / Numerical Recipes constants) whose
+// top 13 bits are the dither.
+__device__ __forceinline__ uint32_t mix32(uint32_t x) {
+    x ^= x >> 16;
+    x *= 0x7feb352du;
+    x ^= x >> 15;
+    x *= 0x846ca68bu;
+    x ^= x >> 16;
+    return x;
+}
 struct PopDither {
     uint32_t s;
-    __device__ __forceinline__ uint32_t next() {
-        s ^= s << 13;
-        s ^= s >> 17;
-        s ^= s << 5;
-        return s;
+    __device__ __forceinline__ uint32_t next() {  // 13 uniform bits
+        s = s * 1664525u + 1013904223u;
+        return s >> 19;
     }
 };
+// per-launch key of the dither (0 for FP32 storage, which draws nothing)
 template <class S>
-__device__ __forceinline__ PopDither pop_dither(const FParams &p, long long n, int k) {
+__device__ __forceinline__ uint32_t dither_key(const FParams &p, long long n) {
+    if constexpr (sizeof(S) == 2)
+        return mix32((uint32_t)p.seed ^ mix32((uint32_t)(p.seed >> 32) ^ 0x5bd1e995u) ^
+                     mix32((uint32_t)n * 0x9e3779b9u + 0x7f4a7c15u));
+    return 0u;
+}
+template <class S>
+__device__ __forceinline__ PopDither pop_dither(uint32_t key, int k) {
     PopDither d{1u};
-    if constexpr (sizeof(S) == 2) {
-        const uint64_t gam = 0x9E3779B97F4A7C15ULL;
-        uint64_t h = smix((p.seed ^ 0x5bd1e995ULL) + gam);
-        h = smix((h ^ (uint64_t)n) + gam);
-        h = smix((h ^ (uint64_t)(unsigned)k) + gam);
-        d.s = (uint32_t)(h >> 32) | 1u;
-    }
+    if constexpr (sizeof(S) == 2) d.s = mix32(key ^ (uint32_t)k);
     return d;
 }
 __device__ __forceinline__ void st_pop(float *q, float v, PopDither &) { *q = v; }
 __device__ __forceinline__ void st_pop(__half *q, float v, PopDither &d) {
     const uint32_t b = __float_as_uint(v), e = (b >> 23) & 0xffu;
     if (e >= 113u && e < 142u) {  // |v| in the normal half range [2^-14, 2^15)
-        const uint32_t m = ((b & 0x7fffffffu) + (d.next() & 0x1fffu)) & ~0x1fffu;
+        const uint32_t m = ((b & 0x7fffffffu) + d.next()) & ~0x1fffu;
         *q = __float2half_rz(__uint_as_float((b & 0x80000000u) | m));  // exact
     } else {
         *q = __float2half_rn(v);
@@ -303,7 +318,7 @@ k_flow_fast(const FParams p, const typename P::fst *__restrict__ fin, typename P
     __shared__ float s_red[2][NT / 32];
 
     const int nx = p.nx, nf = p.nf;
-    const long long nstep = sizeof(S) == 2 ? *stepp : 0;  // keys the FP16 store dither
+    const uint32_t dkey = sizeof(S) == 2 ? dither_key<S>(p, *stepp) : 0u;  // keys the FP16 store dither
     const size_t plane = (size_t)nf * nx;
     const bool py = (p.flags & FLAG_PERIODIC_Y) != 0;
     const bool frozen = (p.flags & FLAG_FROZEN_FLOW) != 0;
@@ -378,7 +393,7 @@ k_flow_fast(const FParams p, const typename P::fst *__restrict__ fin, typename P
         const int x = x0 + lx, y = y0 + ly;
         if (x >= nx || y >= nf) continue;
         const int k = y * nx + x;
-        PopDither dz = pop_dither<S>(p, nstep, k);
+        PopDither dz = pop_dither<S>(dkey, k);
         const float d = dd[r];
         const float rho = d + rho0;
         if (!(fabsf(rho) < 1e30f)) errbits |= ERRW_NONFINITE_RHO;
@@ -432,7 +447,7 @@ k_flow_pers(const FParams p, int tiles_x, int ntiles, const typename P::fst *__r
     __shared__ float s_red[2][NT / 32];
 
     const int nx = p.nx, nf = p.nf;
-    const long long nstep = sizeof(S) == 2 ? *stepp : 0;  // keys the FP16 store dither
+    const uint32_t dkey = sizeof(S) == 2 ? dither_key<S>(p, *stepp) : 0u;  // keys the FP16 store dither
     const size_t plane = (size_t)nf * nx;
     // per-plane base pointers (uniform); site offsets below are 32-bit (the
     // runtime rejects domains of more than 2e9 sites, so one plane indexes in 31 bits)
@@ -458,13 +473,16 @@ k_flow_pers(const FParams p, int tiles_x, int ntiles, const typename P::fst *__r
     auto wy = [&](int v) { return WIDE ? wrap1(v, nf) : wrapi(v, nf); };
     // tile coordinates advance by gridDim.x tiles per iteration without a division
     const int gdx = (int)gridDim.x % tiles_x, gdy = (int)gridDim.x / tiles_x;
-    // populations and temperature of the next tile, loaded during this tile
-    float pg[RY][9];
+    // populations (as stored: converted only when the tile starts, so that
+    // no instruction waits on the loads before then) and temperature of the
+    // next tile, loaded during this tile
+    S pg[RY][9];
     float pTv[RY];
     // one halo-ring site per thread (threads 0 .. ring-1): its density and T
     constexpr int RING = 2 * SW + 2 * TY;
     static_assert(RING <= NT, "one ring site per thread");
-    float rg[9], rT = 0.0f;
+    S rg[9];
+    float rT = 0.0f;
     bool rvalid = false;
     int rslot = 0;  // shared-memory slot of this thread's ring site (set by fetch)
     auto ring_site = [&](int k, int x0, int y0, int &hx, int &hy, int &x, int &y) {
@@ -486,7 +504,7 @@ k_flow_pers(const FParams p, int tiles_x, int ntiles, const typename P::fst *__r
             if (rvalid) {
                 const int kk = y * nx + x;
                 #pragma unroll
-                for (int i = 0; i < 9; i++) rg[i] = ld_as<float>(fplane[i] + kk);
+                for (int i = 0; i < 9; i++) rg[i] = __ldg(fplane[i] + kk);
                 rT = ld_as<float>(Tfl + kk);
             }
         }
@@ -503,11 +521,11 @@ k_flow_pers(const FParams p, int tiles_x, int ntiles, const typename P::fst *__r
             if (has) {
                 const int k = y * nx + x;
                 #pragma unroll
-                for (int i = 0; i < 9; i++) pg[r][i] = ld_as<float>(fplane[i] + k);
+                for (int i = 0; i < 9; i++) pg[r][i] = __ldg(fplane[i] + k);
                 pTv[r] = ld_as<float>(Tfl + k);
             } else {
                 #pragma unroll
-                for (int i = 0; i < 9; i++) pg[r][i] = 0.0f;
+                for (int i = 0; i < 9; i++) pg[r][i] = S(0.0f);
                 pTv[r] = 0.0f;
             }
         }
@@ -522,7 +540,7 @@ k_flow_pers(const FParams p, int tiles_x, int ntiles, const typename P::fst *__r
     #pragma unroll
     for (int r = 0; r < RY; r++) {
         #pragma unroll
-        for (int i = 0; i < 9; i++) g[r][i] = pg[r][i];
+        for (int i = 0; i < 9; i++) g[r][i] = to_f(pg[r][i]);
         gT[r] = pTv[r];
     }
     const bool more = tile + (int)gridDim.x < ntiles;
@@ -549,7 +567,10 @@ k_flow_pers(const FParams p, int tiles_x, int ntiles, const typename P::fst *__r
     if (!frozen && tid < RING) {
         float psi = 0.0f;
         if (rvalid) {
-            const float d = ((rg[0] + rg[1]) + (rg[2] + rg[3])) + ((rg[4] + rg[5]) + (rg[6] + rg[7])) + rg[8];
+            float f[9];
+            #pragma unroll
+            for (int i = 0; i < 9; i++) f[i] = to_f(rg[i]);
+            const float d = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
             psi = psi_fast(p, d + rho0, rT + tsat, errbits);
         }
         s_psi[rslot] = psi;
@@ -566,7 +587,7 @@ k_flow_pers(const FParams p, int tiles_x, int ntiles, const typename P::fst *__r
             const int x = x0 + lx, y = y0 + ly;
             if (E && (x >= nx || y >= nf)) continue;
             const int k = y * nx + x;
-            PopDither dz = pop_dither<S>(p, nstep, (int)k);
+            PopDither dz = pop_dither<S>(dkey, (int)k);
             const float d = dd[r];
             const float rho = d + rho0;
             if (!(fabsf(rho) < 1e30f)) errbits |= ERRW_NONFINITE_RHO;
