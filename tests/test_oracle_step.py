@@ -428,3 +428,27 @@ def test_shear_wave_decays_at_the_phase_viscosity(phase):
     assert rate == pytest.approx(nu, rel=5e-3)
     # a shear wave still: u_y and the density ripple are second order in U
     assert np.abs(r.uy).max() < 1e-6 * U and np.abs(r.rho - rho).max() < U * U * rho
+
+
+def test_phase_change_source_responds_to_the_velocity_divergence():
+    """Eq. 24's source -T / (rho C_V) (dp/dT)_rho div u, alone: uniform
+    density and temperature (no psi force, no gradient of T) under a
+    compressive wave u_x = U sin(k x).  The Eq. 27 divergence of that field is
+    U sin(k) cos(k x), so one step changes T by
+    -T0 (dp/dT)_rho(rho, T0) / (rho C_V) U sin(k) cos(k x), up to terms of
+    second order in U."""
+    nx, ny, U = 16, 4, 1e-4
+    cfg = W.periodic_box(nx, ny, liquid_rows=ny, isothermal=False, init_noise=0.0)
+    r = O.OracleRun(cfg)
+    rho, T0 = cfg.rho_L, r.T[0, 0]
+    k = 2 * np.pi / nx
+    x = np.arange(nx)
+    f = np.zeros((9, ny, nx))
+    for i in range(nx):
+        f[:, :, i] = O.inverse_moments(O.meq(rho, U * np.sin(k * x[i]), 0.0))[:, None]
+    r.set_f(f)
+    r.step(1)
+    dT = r.T - T0
+    want = -T0 * O.dpdT(rho, T0) / (rho * cfg.c_v) * U * np.sin(k) * np.cos(k * x)
+    np.testing.assert_allclose(dT, np.broadcast_to(want, (ny, nx)), rtol=1e-3, atol=1e-3 * np.abs(want).max())
+    assert np.abs(want).max() > 1e-7
