@@ -452,3 +452,26 @@ def test_phase_change_source_responds_to_the_velocity_divergence():
     want = -T0 * O.dpdT(rho, T0) / (rho * cfg.c_v) * U * np.sin(k) * np.cos(k * x)
     np.testing.assert_allclose(dT, np.broadcast_to(want, (ny, nx)), rtol=1e-3, atol=1e-3 * np.abs(want).max())
     assert np.abs(want).max() > 1e-7
+
+
+def test_advection_moves_a_temperature_wave_downstream():
+    """Eq. 24's -u . grad T with the Eq. 27 gradient: a uniform flow U along
+    x over T = T0 + eps sin(k x) (long wave, 64 columns).  The gradient of the
+    wave is eps sin(k) cos(k x), so one step adds -eps U sin(k) cos(k x): the
+    wave moves downstream.  Conduction and the psi-mediated source act in
+    phase with sin(k x) (they change the amplitude, not the phase) and enter
+    the cos(k x) part only at second order."""
+    nx, ny, U = 64, 4, 0.02
+    cfg = W.periodic_box(nx, ny, liquid_rows=ny, isothermal=False, init_noise=0.0)
+    r = O.OracleRun(cfg)
+    rho, T0 = cfg.rho_L, r.T[0, 0]
+    eps = 1e-4 * T0
+    k = 2 * np.pi / nx
+    x = np.arange(nx)
+    feq = O.inverse_moments(O.meq(rho, U, 0.0))
+    r.set_f(np.broadcast_to(feq[:, None, None], (9, ny, nx)).copy())
+    r.set_T(np.broadcast_to(T0 + eps * np.sin(k * x), (ny, nx)))
+    r.step(1)
+    dT = (r.T - T0).mean(axis=0)
+    cos_part = 2.0 / nx * np.sum(dT * np.cos(k * x))
+    assert cos_part == pytest.approx(-eps * U * np.sin(k), rel=2e-3)
