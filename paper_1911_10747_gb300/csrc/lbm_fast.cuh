@@ -129,7 +129,7 @@ __device__ __forceinline__ float to_f(__half v) { return __half2float(v); }
 // SIAM J. Sci. Comput. 43 (2021), "Stochastic rounding and its probabilistic
 // backward error analysis").  Expected stored value = exact value, so the
 // per-step rounding errors no longer add up to a drift of the mass (values
-// in the half-subnormal range keep round-to-nearest).  The dither: a 32-bit
+// in the half-subnormal range are rounded to nearest after the dither).  The dither: a 32-bit
 // key per launch from the seed and the step, one 32-bit hash of key and site
 // per site (C. Wellons' two-round multiply-xorshift mixer), then a linear
 // congruential step per store (Knuth / Numerical Recipes constants) whose
@@ -165,13 +165,12 @@ __device__ __forceinline__ PopDither pop_dither(uint32_t key, int k) {
 }
 __device__ __forceinline__ void st_pop(float *q, float v, PopDither &) { *q = v; }
 __device__ __forceinline__ void st_pop(__half *q, float v, PopDither &d) {
-    const uint32_t b = __float_as_uint(v), e = (b >> 23) & 0xffu;
-    if (e >= 113u && e < 142u) {  // |v| in the normal half range [2^-14, 2^15)
-        const uint32_t m = ((b & 0x7fffffffu) + d.next()) & ~0x1fffu;
-        *q = __float2half_rz(__uint_as_float((b & 0x80000000u) | m));  // exact
-    } else {
-        *q = __float2half_rn(v);
-    }
+    // the dither goes into the magnitude bits (a carry moves into the
+    // exponent, never into the sign for |v| < 2^15); with the 13 low bits
+    // cleared the value is a half exactly when |v| is in the normal half
+    // range [2^-14, 2^15), and the conversion rounds the rest to nearest
+    const uint32_t m = (__float_as_uint(v) + d.next()) & ~0x1fffu;
+    *q = __float2half_rn(__uint_as_float(m));
 }
 
 // One fluid site's forces (Eq. 11, 14, 15), MRT collision with the improved
