@@ -233,3 +233,26 @@ def test_fp32_paired_column_heat_variants_against_the_oracle(kw):
         g.sync()
         errs = field_errors(g, o)
         assert errs["rho"] < 1e-4 and errs["T"] < 1e-5, (names[hv], errs)
+
+
+def test_fp16_storage_heat_variants_agree():
+    """The heat kernels read float T, rho and u whatever the population
+    storage: with FP16 storage every heat variant follows the same run (the
+    flow kernel's stochastic rounding is keyed by site and step, so it draws
+    the same dither in every run; values that land next to a rounding step
+    can still differ by one half ulp)."""
+    cfg = W.small_parity(precision="fp16").replace(nx=70, nf=45, ns=5, liquid_rows=15, rho_mean=2.3,
+                                                   spot_x=(3, 40, 69), spot_half_width=2)
+    names = lbm.Run(cfg).variants()["heat"]
+
+    def run(hv):
+        r = lbm.Run(cfg)
+        r.select_variants(0, hv)
+        r.step(8)
+        return r.fields(("rho", "T"))
+
+    want = run(0)
+    for hv in range(1, len(names)):
+        got = run(hv)
+        for k in want:
+            assert np.max(np.abs(got[k] - want[k])) <= 1e-2 * np.abs(want[k]).max(), (names[hv], k)
