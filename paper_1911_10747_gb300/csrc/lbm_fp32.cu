@@ -34,11 +34,11 @@ const HeatVariant heats32[] = {
     HEATS(PolicyF32, 64, 6, 5, 1), HEATS(PolicyF32, 64, 8, 4, 1), HEATS(PolicyF32, 64, 10, 3, 1),
     HEATS(PolicyF32, 64, 6, 6, 1),
     HEATS(PolicyF32, 32, 8, 4, 2),
-    HEATP(PolicyF32, 8, 4, 1),
+    HEATP(PolicyF32, 12, 4, 1), HEATP(PolicyF32, 8, 4, 1),
     HEATV(PolicyF32, 32, 16, 32, 8), HEATV(PolicyF32, 64, 32, 32, 16),
 };
 const FlowVariant flows16[] = {FLOWP(PolicyF16, 32, 8, 2, 2), FLOWV(PolicyF16, 32, 8, 2, 3)};
-const HeatVariant heats16[] = {HEATS(PolicyF16, 64, 10, 3, 1), HEATS(PolicyF16, 64, 8, 4, 1), HEATP(PolicyF16, 8, 4, 1),
+const HeatVariant heats16[] = {HEATS(PolicyF16, 64, 10, 3, 1), HEATS(PolicyF16, 64, 8, 4, 1), HEATP(PolicyF16, 12, 4, 1),
                                HEATV(PolicyF16, 32, 32, 32, 16)};
 
 const KernelSet ks32 = {"fp32", sizeof(float), sizeof(float), sizeof(float),
