@@ -256,3 +256,21 @@ def test_fp16_storage_heat_variants_agree():
         got = run(hv)
         for k in want:
             assert np.max(np.abs(got[k] - want[k])) <= 1e-2 * np.abs(want[k]).max(), (names[hv], k)
+
+
+@pytest.mark.parametrize("ny", [40, 100])
+def test_fp32_heat_variants_in_a_periodic_box_with_heat(ny):
+    """Doubly periodic box with the energy equation on: rows wrap inside the
+    heat tiles (40 rows: fewer than the tallest tile holds; 100 rows: several
+    tiles), for every heat variant, against the oracle."""
+    cfg = W.periodic_box(64, ny, liquid_rows=ny // 3, init_noise=1e-3, isothermal=False, precision="fp32")
+    names = lbm.Run(cfg).variants()["heat"]
+    o = O.OracleRun(cfg)
+    o.step(40)
+    for hv, name in enumerate(names):
+        g = lbm.Run(cfg)
+        g.select_variants(0, hv)
+        g.step(40)
+        g.sync()
+        errs = field_errors(g, o)
+        assert errs["rho"] < 1e-4 and errs["T"] < 1e-5, (name, errs)
