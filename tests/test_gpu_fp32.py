@@ -48,9 +48,9 @@ def test_fp32_full_size_in_the_benchmarked_launch_configuration():
     """The bench's workload (2048 x 2048 fluid + 64 heater rows, seed 3) as
     the bench runs it: on a stream of its own, autotuned with the bench's
     call, stepped through the captured CUDA graphs; two steps against the
-    oracle.  Then every heat variant with the chosen flow variant, so that
-    whichever the autotuner picks on a given GPU has met the oracle at full
-    size."""
+    oracle.  Then every heat variant with the chosen flow variant and every
+    flow variant with the chosen heat variant, so that whichever the
+    autotuner picks on a given GPU has met the oracle at full size."""
     import torch
     cfg = W.large(precision="fp32", seed=3)
     o = O.OracleRun(cfg)
@@ -66,16 +66,16 @@ def test_fp32_full_size_in_the_benchmarked_launch_configuration():
     print("benchmarked pair", v["flow"][fv], v["heat"][hv0], errs)
     assert errs["rho"] < 1e-5 and errs["T"] < 1e-6, errs
     g.close()
-    for hv, name in enumerate(v["heat"]):
-        if hv == hv0:
-            continue
+    pairs = [(fv, hv) for hv in range(len(v["heat"])) if hv != hv0]
+    pairs += [(f, hv0) for f in range(len(v["flow"])) if f != fv]
+    for f, hv in pairs:
         g = lbm.Run(cfg, stream=stream.cuda_stream)
-        g.select_variants(fv, hv)
+        g.select_variants(f, hv)
         g.step(2)
         g.sync()
         errs = field_errors(g, o)
         g.close()
-        assert errs["rho"] < 1e-5 and errs["T"] < 1e-6, (name, errs)
+        assert errs["rho"] < 1e-5 and errs["T"] < 1e-6, (v["flow"][f], v["heat"][hv], errs)
 
 
 def test_fp32_variants_agree_are_deterministic_and_autotune_keeps_state():
