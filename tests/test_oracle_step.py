@@ -475,3 +475,27 @@ def test_advection_moves_a_temperature_wave_downstream():
     dT = (r.T - T0).mean(axis=0)
     cos_part = 2.0 / nx * np.sum(dT * np.cos(k * x))
     assert cos_part == pytest.approx(-eps * U * np.sin(k), rel=2e-3)
+
+
+def test_initial_state_layers_noise_rest_and_saturation():
+    """Sec. 3.1's start: liquid below, vapour above, at rest, T = T_sat in
+    fluid and heater.  Each site's density carries the relative noise
+    A (2U - 1), U the counter-based draw of (seed, tag 1, step 0, site); the
+    populations are the rest equilibrium w_i rho; rho_bar is the fluid mean."""
+    nx, nf, lr, A = 24, 30, 11, 1e-3
+    cfg = W.RunConfig(nx=nx, nf=nf, ns=5, liquid_rows=lr, init_noise=A, seed=17)
+    r = O.OracleRun(cfg)
+    rho, f = r.rho, r.f
+    base = np.where(np.arange(nf)[:, None] < lr, cfg.rho_L, cfg.rho_V) * np.ones((1, nx))
+    U = np.array([[O.uniform(17, 1, 0, y * nx + x) for x in range(nx)] for y in range(nf)])
+    np.testing.assert_allclose(rho / base - 1.0, A * (2 * U - 1), rtol=0, atol=1e-15)
+    assert np.all(np.abs(rho / base - 1.0) <= A)
+    np.testing.assert_allclose(f.sum(axis=0), rho, rtol=1e-15)
+    w = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+    np.testing.assert_allclose(f, w[:, None, None] * rho[None], rtol=1e-15)
+    ex = np.array([0, 1, 0, -1, 0, 1, -1, -1, 1])
+    ey = np.array([0, 0, 1, 0, -1, 1, 1, -1, -1])
+    assert np.abs(np.tensordot(ex, f, 1)).max() < 1e-15 and np.abs(np.tensordot(ey, f, 1)).max() < 1e-15
+    np.testing.assert_allclose(r.T, 0.86 * r.Tc, rtol=1e-15)
+    assert r.T.shape == (nf + 5, nx)
+    assert r.rho_bar == pytest.approx(rho.mean(), rel=1e-14)
