@@ -97,6 +97,32 @@ def ncu_traffic(kind: str, variant: str):
     return float(t.group(1))
 
 
+def ncu_instructions(kind: str, variant: str):
+    """Executed instructions per site (warp instructions x 32 / sites, ncu)
+    of the flow or heat variant in the committed summary, or None when absent
+    or taken on a different kernel source."""
+    try:
+        text = open(PROFILES[kind]).read()
+    except OSError:
+        return None
+    m = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", text)
+    t = re.search(r"instructions_per_site\[" + re.escape(variant) + r"\]:\s*([0-9.eE+]+)", text)
+    if not m or not t or m.group(1) != kernel_source_hash():
+        return None
+    return float(t.group(1))
+
+
+def issue_roofline(inst_per_site, sites, ms):
+    """Warp-instruction issue rate against the issue peak (152 SMs x 4
+    schedulers x 1 instruction per clock at the maximum SM clock)."""
+    if inst_per_site is None:
+        return None
+    peak = 152 * 4 * max_sm_mhz() * 1e6 / 1e12
+    achieved = inst_per_site / 32.0 * sites / (ms / 1e3) / 1e12
+    return {"achieved": achieved, "peak": peak, "unit": "T warp-instructions/s", "frac": achieved / peak,
+            "instructions_per_site": inst_per_site}
+
+
 def ncu_fp64_flops(kind: str):
     """FP64 flops per site (DADD + DMUL + 2 DFMA executed, from ncu) of the
     FP64 flow or heat kernel in the committed summary, or None when absent
@@ -554,6 +580,11 @@ def run_ours(args):
     # the same fraction against the FMA throughput measured on this GPU (context)
     fma32 = lbm.peak_fma(32, device=local)
     heat_roof.update(measured_fma_peak=fma32, frac_of_measured_fma=heat_achieved / fma32)
+    # instruction issue (context: both kernels spend their time issuing or
+    # waiting, not moving bytes or doing flops at the pipes' rates)
+    if args.precision == "fp32":
+        flow_roof["issue"] = issue_roofline(ncu_instructions("flow", vnames[0]), sites, kms[0])
+        heat_roof["issue"] = issue_roofline(ncu_instructions("heat", vnames[1]), cfg.temperature_sites, kms[1])
     step_ms = ms_max / args.steps
     step_achieved = ALG_STEP_BYTES[args.precision] * sites / (step_ms / 1e3) / 1e9
     dominant = flow_roof if kms[0] >= kms[1] else heat_roof
