@@ -499,3 +499,26 @@ def test_initial_state_layers_noise_rest_and_saturation():
     np.testing.assert_allclose(r.T, 0.86 * r.Tc, rtol=1e-15)
     assert r.T.shape == (nf + 5, nx)
     assert r.rho_bar == pytest.approx(rho.mean(), rel=1e-14)
+
+
+@pytest.mark.parametrize("scale", [1.0, 0.0])
+def test_neutral_top_wall_keeps_saturated_vapour_at_rest(scale):
+    """The lid's adhesion c_w_top (Eq. 14 on the top wall): uniform vapour at
+    T_sat between the two walls, no gravity, no varpi term.  With
+    c_w_top = c_w = -psi(rho_V, T_sat) both wall rows feel no net force and the
+    vapour stays exactly at rest; without the lid's adhesion the top row
+    moves."""
+    nx, nf = 12, 10
+    probe = W.RunConfig(nx=nx, nf=nf, ns=4, liquid_rows=0)
+    psi_v, bad = O.psi(probe.rho_V, probe.T_sat_over_Tc * O.OracleRun(probe).Tc)
+    assert not bad and psi_v > 0
+    cfg = probe.replace(isothermal=True, g=0.0, init_noise=0.0, varpi=0.0, bc_mode="spots", spot_x=(),
+                        c_w_spot=(), c_w_base=-psi_v, c_w_top=-scale * psi_v)
+    r = O.OracleRun(cfg)
+    f0 = r.f
+    r.step(3)
+    if scale == 1.0:
+        np.testing.assert_allclose(r.f, f0, rtol=1e-13, atol=0)
+        assert np.max(np.hypot(r.ux, r.uy)) < 1e-16
+    else:
+        assert np.max(np.abs(r.uy[-1])) > 1e-5 and np.max(np.abs(r.uy[0])) < 1e-16
