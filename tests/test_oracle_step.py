@@ -522,3 +522,32 @@ def test_neutral_top_wall_keeps_saturated_vapour_at_rest(scale):
         assert np.max(np.hypot(r.ux, r.uy)) < 1e-16
     else:
         assert np.max(np.abs(r.uy[-1])) > 1e-5 and np.max(np.abs(r.uy[0])) < 1e-16
+
+
+def test_nucleate_spot_layout_and_adhesion_stencil():
+    """One spot on column 0 with half width 1 (columns 23, 0, 1 of 24: it
+    wraps), the rest of the wall neutral for the liquid (c_w = -psi(rho_L)).
+    Eq. 14 reads c_w from the three solid neighbours x - 1, x, x + 1, so after
+    one step the wall row moves vertically on columns 22 .. 2 only, and
+    horizontally on 22, 23, 1, 2 with u_x mirror-antisymmetric about column
+    0, where it vanishes; no other row moves yet."""
+    nx, nf = 24, 8
+    probe = W.RunConfig(nx=nx, nf=nf, ns=4, liquid_rows=nf)
+    psi_l, _ = O.psi(probe.rho_L, probe.T_sat_over_Tc * O.OracleRun(probe).Tc)
+    cfg = probe.replace(isothermal=True, g=0.0, init_noise=0.0, varpi=0.0, top_mode="outflow",
+                        bc_mode="spots", spot_x=(0,), spot_half_width=1, c_w_spot=(-0.5 * psi_l,),
+                        c_w_base=-psi_l)
+    r = O.OracleRun(cfg)
+    r.step(1)
+    uy0, ux0 = r.uy[0], r.ux[0]
+    moving = {22, 23, 0, 1, 2}
+    for x in range(nx):
+        if x in moving:
+            assert abs(uy0[x]) > 1e-6, x
+        else:
+            assert uy0[x] == 0.0, x
+    assert ux0[0] == 0.0
+    assert abs(ux0[23]) > 1e-7 and ux0[1] == pytest.approx(-ux0[23], rel=1e-12)
+    assert abs(ux0[22]) > 1e-7 and ux0[2] == pytest.approx(-ux0[22], rel=1e-12)
+    assert all(ux0[x] == 0.0 for x in range(3, 22))
+    assert np.abs(r.uy[1:]).max() == 0.0 and np.abs(r.ux[1:]).max() == 0.0
