@@ -143,6 +143,23 @@ typedef struct {
     double rho_shift;       /* reference density of the shifted populations; <= 0: rho_mean */
     int32_t series_capacity;/* per-step diagnostics ring length (0: 4096) */
     int32_t device;         /* CUDA device ordinal */
+    /* Optional device allocator for the run's buffers (a framework's caching
+     * allocator plugs in here).  Both NULL: cudaMalloc / cudaFree.  Both set:
+     * dev_alloc(bytes, alloc_ctx) returns device memory of `device`, aligned to
+     * 256 bytes, or NULL (then LBM_E_NOMEM); dev_free(ptr, alloc_ctx) releases
+     * it.  The run synchronises its streams before it hands memory back, so a
+     * stream-ordered allocator may reuse it at once.  One set, one NULL:
+     * LBM_E_INVAL.  Called from the thread that calls lbm_create,
+     * lbm_set_state (staging growth) and lbm_destroy. */
+    void *(*dev_alloc)(size_t bytes, void *alloc_ctx);
+    void (*dev_free)(void *ptr, void *alloc_ctx);
+    void *alloc_ctx;
+    int32_t bounds_check;   /* 1: debugging mode -- lbm_step runs its steps one at a
+                               time and after each waits for the GPU and checks the
+                               CUDA status and the device error word (numerical
+                               faults, wait time-outs), so a fault is reported by
+                               the call, at the step that caused it; no graphs */
+    int32_t pad1;
 } lbm_opts_t;
 
 /* Create a run, allocate its device state and initialise it (Sec. 3.1):

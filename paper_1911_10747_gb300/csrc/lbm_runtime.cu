@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdint>
 #include <cstdlib>
 #include <cmath>
 #include <cstdio>
@@ -59,6 +60,11 @@ struct lbm_run {
     std::vector<EventPair> ev[3];
     double t_ms[3] = {0, 0, 0};
     int64_t t_count = 0;
+    // optional device allocator (lbm_opts_t.dev_alloc / dev_free)
+    void *(*dev_alloc)(size_t, void *) = nullptr;
+    void (*dev_free)(void *, void *) = nullptr;
+    void *alloc_ctx = nullptr;
+    bool bounds_check = false;
     std::string msg;
 };
 
@@ -109,21 +115,47 @@ static StepBuffers state_as_in(lbm_run *h) {
     return b;
 }
 
+// Device memory of a run: cudaMalloc / cudaFree, or the caller's allocator.
+static cudaError_t dalloc(lbm_run *h, void **p, size_t bytes) {
+    if (!h->dev_alloc) return cudaMalloc(p, bytes);
+    *p = h->dev_alloc(bytes, h->alloc_ctx);
+    if (!*p) return cudaErrorMemoryAllocation;
+    if ((reinterpret_cast<uintptr_t>(*p) & 255u) != 0) {  // TMA and vector loads need aligned bases
+        h->dev_free(*p, h->alloc_ctx);
+        *p = nullptr;
+        return cudaErrorMisalignedAddress;
+    }
+    return cudaSuccess;
+}
+static void dfree(lbm_run *h, void *p) {
+    if (!p) return;
+    if (h->dev_free) h->dev_free(p, h->alloc_ctx);
+    else cudaFree(p);
+}
+// cudaFree waits for the device; a caller's allocator may not, so the run's
+// queued work is finished first
+static void quiesce(lbm_run *h) {
+    if (!h->dev_free) return;
+    if (h->dstream) cudaStreamSynchronize(h->dstream);
+    if (h->stream) cudaStreamSynchronize(h->stream);
+}
+
 static void free_all(lbm_run *h) {
     if (h->graph) cudaGraphExecDestroy(h->graph);
     if (h->graph8) cudaGraphExecDestroy(h->graph8);
+    quiesce(h);
     for (int k = 0; k < 2; k++) {
-        cudaFree(h->f[k]);
-        cudaFree(h->T[k]);
+        dfree(h, h->f[k]);
+        dfree(h, h->T[k]);
     }
     for (int k = 0; k < 2; k++) {
-        cudaFree(h->rho[k]); cudaFree(h->ux[k]); cudaFree(h->uy[k]); cudaFree(h->part[k]);
+        dfree(h, h->rho[k]); dfree(h, h->ux[k]); dfree(h, h->uy[k]); dfree(h, h->part[k]);
     }
-    cudaFree(h->cw); cudaFree(h->series); cudaFree(h->q_top); cudaFree(h->last);
+    dfree(h, h->cw); dfree(h, h->series); dfree(h, h->q_top); dfree(h, h->last);
     for (cudaEvent_t ev : {h->ev_heat, h->ev_diag, h->cev_heat, h->cev_diag})
         if (ev) cudaEventDestroy(ev);
     if (h->dstream) cudaStreamDestroy(h->dstream);
-    cudaFree(h->scratch); cudaFree(h->stage); cudaFree(h->err); cudaFree(h->dstep);
+    dfree(h, h->scratch); dfree(h, h->stage); dfree(h, h->err); dfree(h, h->dstep);
     for (auto &v : h->ev)
         for (auto &e : v) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
@@ -220,10 +252,12 @@ static const double *host_alias(const double *p) {
 
 static int ensure_stage(lbm_run *h, size_t elems) {
     if (h->stage_elems >= elems) return LBM_OK;
-    cudaFree(h->stage);
+    quiesce(h);
+    dfree(h, h->stage);
     h->stage = nullptr;
     h->stage_elems = 0;
-    if (cudaMalloc(&h->stage, elems * sizeof(double)) != cudaSuccess) return fail(h, LBM_E_NOMEM, "staging allocation failed");
+    if (dalloc(h, (void **)&h->stage, elems * sizeof(double)) != cudaSuccess)
+        return fail(h, LBM_E_NOMEM, "staging allocation failed");
     h->stage_elems = elems;
     return LBM_OK;
 }
@@ -279,6 +313,14 @@ int lbm_create(const lbm_domain_t *domain, const lbm_heater_t *heater, const lbm
         case LBM_FP16: h->ks = kernels_fp16(); break;
         default: delete h; return fail(nullptr, LBM_E_INVAL, "opts.precision invalid");
     }
+    if ((opts->dev_alloc == nullptr) != (opts->dev_free == nullptr)) {
+        delete h;
+        return fail(nullptr, LBM_E_INVAL, "opts.dev_alloc and opts.dev_free must be set together");
+    }
+    h->dev_alloc = opts->dev_alloc;
+    h->dev_free = opts->dev_free;
+    h->alloc_ctx = opts->alloc_ctx;
+    h->bounds_check = opts->bounds_check != 0;
     h->device = opts->device;
     h->use_graphs = opts->use_graphs != 0;
     if (opts->series_capacity < 0) { delete h; return fail(nullptr, LBM_E_INVAL, "opts.series_capacity negative"); }
@@ -325,9 +367,11 @@ int lbm_create(const lbm_domain_t *domain, const lbm_heater_t *heater, const lbm
         {(void **)&h->dstep, sizeof(long long)},
     };
     for (auto &a : allocs) {
-        e = cudaMalloc(a.ptr, a.bytes);
+        e = dalloc(h, a.ptr, a.bytes);
         if (e != cudaSuccess) {
-            fail(h, LBM_E_NOMEM, std::string("device allocation of ") + std::to_string(a.bytes) + " bytes failed: " + cudaGetErrorString(e));
+            fail(h, LBM_E_NOMEM, std::string("device allocation of ") + std::to_string(a.bytes) + " bytes failed: " +
+                                     (e == cudaErrorMisalignedAddress ? "opts.dev_alloc returned memory not aligned to 256 bytes"
+                                                                      : cudaGetErrorString(e)));
             return bad(LBM_E_NOMEM);
         }
     }
@@ -454,6 +498,19 @@ int lbm_step(lbm_handle h, int64_t n) {
     if (n < 0) return fail(h, LBM_E_INVAL, "negative step count");
     CK(h, cudaSetDevice(h->device));
     int rc;
+    if (h->bounds_check) {  // one step at a time, each waited for and checked
+        while (n > 0) {
+            if ((rc = launch_step(h, h->timing)) != LBM_OK) return rc;
+            n -= 1;
+            h->steps += 1;
+            CK(h, join_diag(h));
+            CK(h, cudaStreamSynchronize(h->dstream));
+            CK(h, cudaStreamSynchronize(h->stream));
+            CK(h, cudaGetLastError());
+            if ((rc = check_err_word(h)) != LBM_OK) return rc;
+        }
+        return LBM_OK;
+    }
     const bool graphs = h->use_graphs && !h->timing && h->stream != nullptr;
     while (n > 0) {
         if (graphs && n >= 8 && h->parity == 0) {

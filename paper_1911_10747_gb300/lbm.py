@@ -66,9 +66,34 @@ class lbm_bc_t(C.Structure):
                 ("c_w_base", C.c_double), ("c_w_spot", C.c_double * 8), ("c_w_top", C.c_double)]
 
 
+#: lbm_opts_t.dev_alloc / dev_free
+DEV_ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+DEV_FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+
 class lbm_opts_t(C.Structure):
     _fields_ = [("precision", C.c_int32), ("use_graphs", C.c_int32), ("stream", C.c_void_p),
-                ("rho_shift", C.c_double), ("series_capacity", C.c_int32), ("device", C.c_int32)]
+                ("rho_shift", C.c_double), ("series_capacity", C.c_int32), ("device", C.c_int32),
+                ("dev_alloc", DEV_ALLOC_FN), ("dev_free", DEV_FREE_FN), ("alloc_ctx", C.c_void_p),
+                ("bounds_check", C.c_int32), ("pad1", C.c_int32)]
+
+
+def torch_allocator(device: int = 0):
+    """(dev_alloc, dev_free) callbacks that take the run's device memory from
+    PyTorch's caching allocator on `device` (keep them referenced while the
+    run lives: lbm.Run does)."""
+    import torch
+
+    def alloc(nbytes, ctx):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), device)
+        except RuntimeError:
+            return None  # -> LBM_E_NOMEM
+
+    def free(ptr, ctx):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    return DEV_ALLOC_FN(alloc), DEV_FREE_FN(free)
 
 
 _lib = None
@@ -155,8 +180,10 @@ def _check(rc: int, h, where: str):
         raise LbmError(rc, where, msg.decode() if msg else "")
 
 
-def structs_from_config(cfg, stream=None, use_graphs=True, series_capacity=0, device=0):
-    """Fill the five ABI structs from a RunConfig."""
+def structs_from_config(cfg, stream=None, use_graphs=True, series_capacity=0, device=0, allocator=None,
+                        bounds_check=False):
+    """Fill the five ABI structs from a RunConfig.  allocator: None
+    (cudaMalloc) or a (dev_alloc, dev_free) pair of ctypes callbacks."""
     d = lbm_domain_t()
     d.nx, d.ny_fluid, d.liquid_rows = cfg.nx, cfg.nf, cfg.liquid_rows
     d.top_mode = {"wall": LBM_TOP_WALL, "outflow": LBM_TOP_OUTFLOW}[cfg.top_mode]
@@ -189,16 +216,27 @@ def structs_from_config(cfg, stream=None, use_graphs=True, series_capacity=0, de
     op.rho_shift = cfg.rho_shift
     op.series_capacity = series_capacity
     op.device = device
+    if allocator is not None:
+        op.dev_alloc, op.dev_free = allocator
+    op.bounds_check = 1 if bounds_check else 0
     return d, ht, eo, bc, op
 
 
 class Run:
     """One boiling run on the GPU (a handle of the C library)."""
 
-    def __init__(self, cfg, stream=None, use_graphs=True, series_capacity=0, device=0):
+    def __init__(self, cfg, stream=None, use_graphs=True, series_capacity=0, device=0, allocator=None,
+                 bounds_check=False):
+        """allocator: None (the library's cudaMalloc), "torch" (PyTorch's
+        caching allocator) or a (dev_alloc, dev_free) pair of callbacks;
+        bounds_check: step one step at a time and report faults at once."""
         L = load()
         self.cfg = cfg
-        self._structs = structs_from_config(cfg, stream, use_graphs, series_capacity, device)
+        if allocator == "torch":
+            allocator = torch_allocator(device)
+        self._allocator = allocator  # the callbacks must outlive the handle
+        self._structs = structs_from_config(cfg, stream, use_graphs, series_capacity, device, allocator,
+                                            bounds_check)
         h = C.c_void_p()
         rc = L.lbm_create(*[C.byref(s) for s in self._structs], C.byref(h))
         _check(rc, None, "lbm_create")

@@ -93,3 +93,20 @@ def test_fma_probe_rejects_bad_arguments_on_the_host(lib, bits, iters):
     assert "lbm_peak_fma" in lib.lbm_last_error(None).decode()
     assert v.value == -1.0
     assert lib.lbm_peak_fma(-1, 32, 64, None) == lbm.LBM_E_INVAL
+
+
+def test_allocator_callbacks_must_come_in_pairs(lib):
+    """opts.dev_alloc without opts.dev_free (or the reverse) is rejected on
+    the host, before any device work."""
+    cfg = W.small_parity()
+    for half in ("dev_alloc", "dev_free"):
+        structs = lbm.structs_from_config(cfg)
+        op = structs[4]
+        if half == "dev_alloc":
+            op.dev_alloc = lbm.DEV_ALLOC_FN(lambda n, ctx: None)
+        else:
+            op.dev_free = lbm.DEV_FREE_FN(lambda p, ctx: None)
+        h = C.c_void_p()
+        assert lib.lbm_create(*[C.byref(s) for s in structs], C.byref(h)) == lbm.LBM_E_INVAL
+        assert not h.value
+        assert "dev_alloc" in lib.lbm_last_error(None).decode()
