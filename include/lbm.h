@@ -193,6 +193,14 @@ int lbm_fields(lbm_handle h, unsigned mask, double *const *dst, int dst_is_devic
 int lbm_set_state(lbm_handle h, const double *f, const double *T, int64_t step,
                   int src_is_device);
 
+/* Checkpoint: the state lbm_set_state takes back -- post-stream populations
+ * f (9*NF*NX) and temperature T (NT*NX) as float64, and the step counter.
+ * Any of f, T, step may be NULL to skip it; dst_is_device as in lbm_fields.
+ * Synchronises when f or T is requested.  lbm_set_state(h, f, T, step, ...)
+ * on a run of the same configuration continues bit for bit (FP64 path;
+ * reduced-precision storage converts through float64 both ways). */
+int lbm_get_state(lbm_handle h, double *f, double *T, int64_t *step, int dst_is_device);
+
 /* Heat flux of the last step: mean over x of -lambda_s dT/dy at the heater
  * bottom (Eq. 36 with rows 0-2, Eq. 39 without its scale factor) and, if
  * q_top_local is not NULL, the NX local fluxes -lambda_face dT/dy across the

@@ -548,6 +548,18 @@ int lbm_sync(lbm_handle h) {
 
 int64_t lbm_step_count(lbm_handle h) { return h ? h->steps : -1; }
 
+int lbm_get_state(lbm_handle h, double *f, double *T, int64_t *step, int dst_is_device) {
+    if (!h) return LBM_E_INVAL;
+    double *dst[2] = {nullptr, nullptr};
+    unsigned mask = 0;
+    int j = 0;
+    if (T) { mask |= LBM_FIELD_T; dst[j++] = T; }  // lbm_fields takes T before F
+    if (f) { mask |= LBM_FIELD_F; dst[j++] = f; }
+    const int rc = mask ? lbm_fields(h, mask, dst, dst_is_device) : LBM_OK;
+    if (rc == LBM_OK && step) *step = h->steps;
+    return rc;
+}
+
 int lbm_fields(lbm_handle h, unsigned mask, double *const *dst, int dst_is_device) {
     if (!h) return LBM_E_INVAL;
     if (mask & ~31u) return fail(h, LBM_E_INVAL, "unknown field bits");

@@ -27,7 +27,7 @@ LBM_FIELD_RHO, LBM_FIELD_UX, LBM_FIELD_UY, LBM_FIELD_T, LBM_FIELD_F = 1, 2, 4, 8
 
 #: every entry point declared in include/lbm.h
 EXPORTS = ("lbm_create", "lbm_destroy", "lbm_step", "lbm_sync", "lbm_step_count", "lbm_fields",
-           "lbm_set_state", "lbm_wall_heat_flux", "lbm_vapour_fraction", "lbm_mass", "lbm_series",
+           "lbm_set_state", "lbm_get_state", "lbm_wall_heat_flux", "lbm_vapour_fraction", "lbm_mass", "lbm_series",
            "lbm_set_timing", "lbm_kernel_times", "lbm_kernels_per_step", "lbm_variants",
            "lbm_variant_name", "lbm_select_variants", "lbm_autotune", "lbm_diagnostics_static",
            "lbm_batch_create", "lbm_batch_step", "lbm_batch_sync", "lbm_batch_destroy",
@@ -130,6 +130,7 @@ def load(path: str = LIB_PATH):
     L.lbm_step_count.restype = C.c_int64
     L.lbm_fields.argtypes = [C.c_void_p, C.c_uint, C.POINTER(C.c_void_p), C.c_int]
     L.lbm_set_state.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int]
+    L.lbm_get_state.argtypes = [C.c_void_p, _D, _D, C.POINTER(C.c_int64), C.c_int]
     L.lbm_wall_heat_flux.argtypes = [C.c_void_p, _D, _D]
     L.lbm_vapour_fraction.argtypes = [C.c_void_p, _D]
     L.lbm_mass.argtypes = [C.c_void_p, _D]
@@ -321,6 +322,15 @@ class Run:
         _check(load().lbm_set_state(self._h, fp, tp, int(step), 1 if src_is_device else 0), self._h,
                "lbm_set_state")
         del keep
+
+    def get_state(self):
+        """Checkpoint (lbm_get_state): (f [9, nf, nx], T [nt, nx], step), float64."""
+        f = np.empty((9, self.nf, self.nx))
+        T = np.empty((self.nt, self.nx))
+        step = C.c_int64()
+        _check(load().lbm_get_state(self._h, f.ctypes.data_as(_D), T.ctypes.data_as(_D), C.byref(step), 0),
+               self._h, "lbm_get_state")
+        return f, T, int(step.value)
 
     def wall_heat_flux(self, local: bool = False):
         qb = C.c_double()

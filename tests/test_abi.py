@@ -110,3 +110,9 @@ def test_allocator_callbacks_must_come_in_pairs(lib):
         assert lib.lbm_create(*[C.byref(s) for s in structs], C.byref(h)) == lbm.LBM_E_INVAL
         assert not h.value
         assert "dev_alloc" in lib.lbm_last_error(None).decode()
+
+
+def test_get_state_without_a_run_is_rejected(lib):
+    step = C.c_int64(-7)
+    assert lib.lbm_get_state(None, None, None, C.byref(step), 0) == lbm.LBM_E_INVAL
+    assert step.value == -7

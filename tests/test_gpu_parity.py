@@ -126,6 +126,25 @@ def test_set_state_round_trip_and_restart_is_exact():
         assert np.array_equal(fa[k], fb[k]), k
 
 
+def test_get_state_checkpoint_restarts_bit_for_bit():
+    """lbm_get_state returns what lbm_set_state takes back: a run restarted
+    from the checkpoint (populations, temperature, step counter that keys
+    the noisy bottom) continues exactly as the original."""
+    cfg = W.small_parity().replace(bc_mode="noise", spot_x=(), c_w_spot=(), rho_mean=2.42)
+    a = lbm.Run(cfg).step(13)
+    f, T, step = a.get_state()
+    assert step == 13 and f.shape == (9, cfg.nf, cfg.nx) and T.shape == (cfg.t_rows, cfg.nx)
+    st = a.fields(("f", "T"))
+    assert np.array_equal(st["f"], f) and np.array_equal(st["T"], T)
+    a.step(11)
+    b = lbm.Run(cfg)
+    b.set_state(f, T, step=step)
+    b.step(11)
+    fa, fb = a.fields(("rho", "T", "f")), b.fields(("rho", "T", "f"))
+    for k in fa:
+        assert np.array_equal(fa[k], fb[k]), k
+
+
 def test_full_size_domain_fp64_against_oracle():
     """The 2048 x 2048 + 64 domain of the throughput run, two steps, FP64."""
     cfg = W.large(precision="fp64").replace(rho_mean=2.41)
