@@ -116,3 +116,15 @@ def test_get_state_without_a_run_is_rejected(lib):
     step = C.c_int64(-7)
     assert lib.lbm_get_state(None, None, None, C.byref(step), 0) == lbm.LBM_E_INVAL
     assert step.value == -7
+
+
+def test_missing_library_fails_loudly(tmp_path, monkeypatch):
+    """No CPU fallback: without the CUDA library the binding raises instead
+    of computing anything, for a direct load and for a run."""
+    missing = str(tmp_path / "liblbm_gb300.so")
+    monkeypatch.setattr(lbm, "_lib", None)
+    with pytest.raises(ImportError, match="no CPU path"):
+        lbm.load(missing)
+    monkeypatch.setattr(lbm.load, "__defaults__", (missing,))
+    with pytest.raises(ImportError, match="no CPU path"):
+        lbm.Run(W.small_parity())
