@@ -15,6 +15,22 @@
  * Every function names the passage it follows.  Readings of passages the
  * paper leaves open are marked "reading:".
  *
+ * Pinned, without a GPU, by tests/test_oracle_pins.py and
+ * tests/test_oracle_step.py against what the paper and the mathematics fix:
+ * the transfer matrix and velocities (Eq. 2, 6, printed), moments of the
+ * textbook equilibrium and of Guo's force, the BGK limit, the PR EOS (Tc,
+ * critical point, acentric factor, Maxwell densities and latent heat against
+ * printed values), psi reproducing p_EOS, the counter-based draws, the
+ * Eq. 27-28 stencils, RK4 amplification, steady conduction through the
+ * heater, Eq. 36 on quadratics, mass conservation, symmetries, the phase
+ * viscosities (shear-wave decay), momentum balance, neutral wall adhesion
+ * at the heater and at the lid, the nucleate-spot layout, the open top,
+ * the sine and noisy bottoms, advection and the phase-change source of
+ * Eq. 24, the vapour fraction, flat-interface coexistence, the Laplace law
+ * and the initial state.
+ * Parity unpinned: the full coupled step as a whole (no closed form exists);
+ * the CUDA path is compared with this file, part by part pinned as above.
+ *
  * Layout: populations f[i][y][x] (i = 0..8, y = fluid row 0..nf-1, x =
  * 0..nx-1); temperature T[r][x] for rows r = 0..nt-1, nt = ns + nf, where
  * rows 0..ns-1 are the solid heater (row 0 = heater bottom, Dirichlet) and
