@@ -19,8 +19,9 @@
  *   - Return value: LBM_OK (0) or an lbm_status error code; the message of
  *     the last error on a handle is returned by lbm_last_error.
  *   - All structs passed in are copied; the caller keeps ownership.
- *   - The handle owns every device allocation it makes; lbm_destroy frees
- *     them.  Pointers passed as "host" buffers must stay valid for the call
+ *   - The handle owns every device allocation it makes (by cudaMalloc, or by
+ *     lbm_opts_t.dev_alloc when given); lbm_destroy frees them.  Pointers
+ *     passed as "host" buffers must stay valid for the call
  *     only (calls that read back synchronise the handle's stream first).
  *   - Work is queued on the handle's CUDA stream (lbm_opts_t.stream, or a
  *     stream the library creates).  Numerical faults found by the kernels
