@@ -268,7 +268,11 @@ int lbm_batch_sync(lbm_batch b);
 int lbm_batch_destroy(lbm_batch b);
 const char *lbm_batch_last_error(lbm_batch b);
 
-/* Device memory (bytes, upper estimate) a run of this configuration holds. */
+/* Device memory (bytes, upper estimate) a run of this configuration holds
+ * from lbm_create on.  Not included: the float64 staging buffer that the
+ * first read-back into host memory (lbm_fields, lbm_get_state) or import
+ * from pageable memory (lbm_set_state) allocates, 8 bytes per value moved
+ * (at most 9 NF NX + NT NX values), kept until lbm_destroy. */
 int lbm_device_bytes(const lbm_domain_t *domain, const lbm_heater_t *heater, const lbm_opts_t *opts,
                      uint64_t *bytes);
 

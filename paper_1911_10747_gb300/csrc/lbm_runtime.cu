@@ -904,10 +904,11 @@ int lbm_device_bytes(const lbm_domain_t *domain, const lbm_heater_t *heater, con
     const bool model_a = heater->ny_solid == 0 && !(domain->flags & LBM_PERIODIC_Y);
     const uint64_t ntl = (uint64_t)domain->nx * (domain->ny_fluid + (model_a ? 1 : heater->ny_solid));
     const uint64_t cap = opts->series_capacity > 0 ? (uint64_t)opts->series_capacity : 4096;
-    // populations x2, temperature x2, moments x3, per-column arrays, per-block
-    // partials (at most one block per 32 sites), series ring, small words
-    *bytes = 2 * 9 * nfl * ks->f_elem + 2 * ntl * ks->T_elem + 3 * nfl * ks->m_elem + 2 * 8 * (uint64_t)domain->nx +
-             2 * 8 * (nfl / 32 + 1) + cap * SERIES_WIDTH * 8 + 1024 * 8 + 4096;
+    // populations x2, temperature x2, moments x3 for each step parity,
+    // per-column arrays, per-block partials for each parity (at most one
+    // block per 32 sites), series ring, small words
+    *bytes = 2 * 9 * nfl * ks->f_elem + 2 * ntl * ks->T_elem + 6 * nfl * ks->m_elem + 2 * 8 * (uint64_t)domain->nx +
+             2 * 2 * 8 * (nfl / 32 + 1) + cap * SERIES_WIDTH * 8 + 1024 * 8 + 4096;
     return LBM_OK;
 }
 
