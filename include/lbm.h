@@ -289,7 +289,8 @@ int lbm_device_bytes(const lbm_domain_t *domain, const lbm_heater_t *heater, con
  * state 0 queued, 1 running, 2 done, 3 failed, and the submit / start /
  * finish times in seconds since the server was created.
  * lbm_server_result copies the final diagnostics (4 values, as one row of
- * lbm_series) and the kept fields.  Not thread-safe. */
+ * lbm_series) and the kept fields (rho: NF*NX, T: NT*NX values, NT as in
+ * lbm_fields).  Not thread-safe. */
 typedef struct lbm_server_s *lbm_server;
 int lbm_server_create(uint64_t hbm_budget_bytes, int32_t max_active, int32_t chunk_steps, int32_t device,
                       lbm_server *out);

@@ -185,7 +185,11 @@ int lbm_server_tick(lbm_server s, int32_t *finished) {
         src = lbm_series(r.h, r.steps - 1, 1, row);
         if (src == LBM_OK) std::memcpy(r.diag, row, sizeof(row));
         if (src == LBM_OK && r.keep) {
-            const size_t nfl = (size_t)r.d.nx * r.d.ny_fluid, ntl = (size_t)r.d.nx * (r.d.ny_fluid + r.ht.ny_solid);
+            // T rows: the heater's and the fluid's, or for model A (no heater,
+            // walls) the heated wall's Dirichlet row and the fluid's
+            const bool model_a = r.ht.ny_solid == 0 && !(r.d.flags & LBM_PERIODIC_Y);
+            const size_t nfl = (size_t)r.d.nx * r.d.ny_fluid,
+                         ntl = (size_t)r.d.nx * (r.d.ny_fluid + (model_a ? 1 : r.ht.ny_solid));
             r.rho.resize(nfl);
             r.T.resize(ntl);
             double *dst[2] = {r.rho.data(), r.T.data()};

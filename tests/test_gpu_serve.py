@@ -66,3 +66,22 @@ def test_requests_give_the_same_results_alone_and_in_the_mix():
         st, (ts, t1, t2) = srv.status(i)
         assert ts <= t1 <= t2
     srv.close()
+
+
+def test_model_a_request_keeps_its_whole_temperature_field():
+    """Model A (no heater): T has the heated wall's row and the fluid rows,
+    NF + 1 of them; the kept fields of a served request are those of the
+    same run stepped alone."""
+    cfg = W.small_parity().replace(precision="fp32", ns=0)
+    srv = lbm.Server(hbm_budget_bytes=4 * lbm.device_bytes(cfg), max_active=2, chunk_steps=5)
+    rid = srv.submit(cfg, 12, keep_fields=True)
+    for _ in range(50):
+        srv.tick()
+        if srv.status(rid)[0] >= 2:
+            break
+    diag, rho, T = srv.result(rid, fields=True)
+    d0, rho0, T0 = alone(cfg, 12)
+    assert T.shape == (cfg.nf + 1, cfg.nx)
+    assert np.array_equal(rho, rho0) and np.array_equal(T, T0)
+    assert np.array_equal(diag, d0)
+    srv.close()
