@@ -159,7 +159,8 @@ typedef struct {
                                time and after each waits for the GPU and checks the
                                CUDA status and the device error word (numerical
                                faults, wait time-outs), so a fault is reported by
-                               the call, at the step that caused it; no graphs */
+                               the call, at the step that caused it; no graphs.
+                               lbm_batch_step does not check step by step */
     int32_t pad1;
 } lbm_opts_t;
 
