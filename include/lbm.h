@@ -49,7 +49,7 @@
 extern "C" {
 #endif
 
-#define LBM_ABI_VERSION 1
+#define LBM_ABI_VERSION 2
 
 enum lbm_status {
     LBM_OK = 0,
@@ -191,7 +191,11 @@ int lbm_fields(lbm_handle h, unsigned mask, double *const *dst, int dst_is_devic
 
 /* Replace the state: post-stream populations f (9*NF*NX) and temperature T
  * (NT*NX), float64, host or device; either may be NULL to keep it.
- * Sets the step counter to `step` (the counter keys the noisy bottom). */
+ * Sets the step counter to `step` (the counter keys the noisy bottom) and
+ * starts a new trajectory there: lbm_series serves only steps >= `step`,
+ * and lbm_wall_heat_flux, lbm_vapour_fraction and lbm_mass return
+ * LBM_E_STATE until a step of the new state has run (their values would
+ * describe the state before the import). */
 int lbm_set_state(lbm_handle h, const double *f, const double *T, int64_t step,
                   int src_is_device);
 
@@ -313,13 +317,19 @@ const char *lbm_server_last_error(lbm_server s);
  * synchronisation of those calls.
  *
  * Inputs (device pointers, float64, row-major as in lbm_fields): rho
- * [ny_fluid][nx] and T [ny_solid + ny_fluid][nx].  Output: out, a device
- * pointer to 4 doubles receiving the same values as one row of lbm_series:
- * mean heater-bottom flux (Eq. 36 with lambda_s, 0 if ny_solid < 3), mean
- * heater-surface face flux (harmonic-mean conductance, cv_chi * rho in the
- * fluid), vapour fraction (rho < (rho_L + rho_V) / 2) and mass.  Work is
- * queued on `stream` (a cudaStream_t; NULL = legacy default stream) and the
- * call returns without waiting.
+ * [ny_fluid][nx] and T [NT][nx], NT as in lbm_fields: ny_solid + ny_fluid
+ * with a heater (ny_solid >= 3), 1 + ny_fluid for model A (ny_solid = 0,
+ * row 0 the wall's Dirichlet row), ny_fluid for a domain periodic in y
+ * (ny_solid = 0 and LBM_PERIODIC_Y in flags; T is then not read).  Output:
+ * out, a device pointer to 4 doubles receiving the same values as one row
+ * of lbm_series for that configuration: mean heater-bottom flux (Eq. 36
+ * with lambda_s), mean heater-surface face flux (harmonic-mean conductance,
+ * cv_chi * rho in the fluid), vapour fraction (rho < (rho_L + rho_V) / 2)
+ * and mass.  Model A reports its wall flux -cv_chi rho (T(row 1) - T_b) in
+ * both flux slots; a domain periodic in y has no wall and reports 0 for
+ * both.  flags: the lbm_flags of the run (only LBM_PERIODIC_Y is used).
+ * Work is queued on `stream` (a cudaStream_t; NULL = legacy default
+ * stream) and the call returns without waiting.
  *
  * Scratch: per-block partial sums go to a file-scope device array of
  * 16384 x 4 doubles (512 KiB) that every GPU loading the library keeps until
@@ -331,11 +341,12 @@ const char *lbm_server_last_error(lbm_server s);
  * All calls share the array and leave their partials in it (each call writes
  * every slot it reads, so nothing needs clearing): calls that overlap on the
  * GPU race, so serialise them (one stream, or events).
- * Errors: LBM_E_INVAL (NULL pointer, bad size, over capacity), LBM_E_CUDA (no
- * current device, symbol lookup or launch failed); the message is returned
- * by lbm_last_error(NULL). */
+ * Errors: LBM_E_INVAL (NULL pointer, bad size, ny_solid of 1 or 2, a
+ * periodic domain with ny_solid != 0, over capacity), LBM_E_CUDA (no current
+ * device, symbol lookup or launch failed); the message is returned by
+ * lbm_last_error(NULL). */
 int lbm_diagnostics_static(const double *rho, const double *T, int32_t nx, int32_t ny_fluid,
-                           int32_t ny_solid, double lambda_s, double cv_chi, double rho_L,
+                           int32_t ny_solid, int32_t flags, double lambda_s, double cv_chi, double rho_L,
                            double rho_V, double *out, void *stream);
 
 /* Measured FMA throughput of one GPU, the peak against which the

@@ -34,6 +34,8 @@ struct lbm_run {
     bool use_graphs = true;
     int parity = 0;                 // 0: state in buffers [0], 1: in [1]
     int64_t steps = 0;
+    int64_t series_from = 0;        // first step of the current trajectory (lbm_set_state restarts it)
+    bool diag_stale = false;        // lbm_set_state since the last step: no diagnostics of this state yet
     void *f[2] = {nullptr, nullptr};
     void *T[2] = {nullptr, nullptr};
     // moments and per-block partials are double-buffered by parity, so the
@@ -497,6 +499,7 @@ int lbm_step(lbm_handle h, int64_t n) {
     if (!h) return LBM_E_INVAL;
     if (n < 0) return fail(h, LBM_E_INVAL, "negative step count");
     CK(h, cudaSetDevice(h->device));
+    if (n > 0) h->diag_stale = false;  // the diagnostics kernel of these steps runs before any read-back
     int rc;
     if (h->bounds_check) {  // one step at a time, each waited for and checked
         while (n > 0) {
@@ -646,11 +649,19 @@ int lbm_set_state(lbm_handle h, const double *f, const double *T, int64_t step, 
     CK(h, cudaMemcpyAsync(h->dstep, &s, sizeof(s), cudaMemcpyHostToDevice, h->stream));
     CK(h, cudaStreamSynchronize(h->stream));  // host sources may be freed after return
     h->steps = step;
+    // the diagnostics ring and the last-step values describe the previous
+    // trajectory: rows before `step` are no longer served, and the scalar
+    // readers refuse until a step of the new state has run
+    h->series_from = step;
+    h->diag_stale = true;
     return LBM_OK;
 }
 
+static const char *kStaleDiag = "no step has run since lbm_set_state: the diagnostics describe the previous state";
+
 int lbm_wall_heat_flux(lbm_handle h, double *q_bottom_mean, double *q_top_local) {
     if (!h) return LBM_E_INVAL;
+    if (h->diag_stale) return fail(h, LBM_E_STATE, kStaleDiag);
     CK(h, cudaSetDevice(h->device));
     double last[SERIES_WIDTH];
     CK(h, cudaMemcpyAsync(last, h->last, sizeof(last), cudaMemcpyDeviceToHost, h->stream));
@@ -662,6 +673,7 @@ int lbm_wall_heat_flux(lbm_handle h, double *q_bottom_mean, double *q_top_local)
 
 static int read_last(lbm_run *h, int k, double *out) {
     if (!h || !out) return LBM_E_INVAL;
+    if (h->diag_stale) return fail(h, LBM_E_STATE, kStaleDiag);
     CK(h, cudaSetDevice(h->device));
     double last[SERIES_WIDTH];
     CK(h, cudaMemcpyAsync(last, h->last, sizeof(last), cudaMemcpyDeviceToHost, h->stream));
@@ -677,7 +689,7 @@ int lbm_series(lbm_handle h, int64_t first, int64_t count, double *out) {
     if (!h) return LBM_E_INVAL;
     if (count < 0 || (count > 0 && !out)) return fail(h, LBM_E_INVAL, "bad count or NULL out");
     if (count == 0) return LBM_OK;
-    if (first < 0 || first + count > h->steps || h->steps - first > h->series_cap)
+    if (first < h->series_from || first + count > h->steps || h->steps - first > h->series_cap)
         return fail(h, LBM_E_INVAL, "requested steps are not in the diagnostics ring");
     CK(h, cudaSetDevice(h->device));
     for (int64_t k = 0; k < count;) {
@@ -868,6 +880,7 @@ int lbm_batch_step(lbm_batch b, int64_t n) {
         for (auto h : b->runs) {
             if ((e = cudaStreamWaitEvent(h->stream, b->fork, 0)) != cudaSuccess) return bfail(b, LBM_E_CUDA, cudaGetErrorString(e));
             h->steps += 2;
+            h->diag_stale = false;
         }
         n -= 2;
     }

@@ -42,12 +42,17 @@ __device__ __forceinline__ double warp_sum(double v) {
 // Stage 1: block b reduces fluid sites [b K, (b + 1) K) and columns
 // [b K, (b + 1) K) (when < nx) into partials[b][0..3].  Every slot that
 // stage 2 reads is written here, so nothing has to start at zero.
+// ns >= 3: heater rows 0..ns-1 (model B); ns = 0 without periodic rows:
+// model A, T row 0 the wall's Dirichlet row, coupled to the first fluid row
+// with the fluid's conductivity on both sides (the per-step diagnostics'
+// rule); periodic in y: no wall, no flux.
 __global__ void __launch_bounds__(kThreads)
-k_static_partials(const double *__restrict__ rho, const double *__restrict__ T, int nx, int nf, int ns,
+k_static_partials(const double *__restrict__ rho, const double *__restrict__ T, int nx, int nf, int ns, int periodic,
                   double lambda_s, double cv_chi, double threshold, double *__restrict__ partials) {
     __shared__ double sh[4][kThreads / 32];
     const long long sites = (long long)nx * nf;
     const long long base = (long long)blockIdx.x * kSitesPerBlock;
+    const bool model_a = ns == 0 && !periodic;
     double m = 0.0, v = 0.0, qb = 0.0, qt = 0.0;
     for (int j = threadIdx.x; j < kSitesPerBlock; j += kThreads) {
         const long long k = base + j;
@@ -56,15 +61,22 @@ k_static_partials(const double *__restrict__ rho, const double *__restrict__ T, 
             m += r;
             v += (r < threshold) ? 1.0 : 0.0;
         }
-        if (k < nx && ns >= 3) {
+        if (k < nx && !periodic && (ns >= 3 || model_a)) {
             const int x = (int)k;
-            // Eq. 36 at the heater bottom, rows 0..2
-            const double dTdy = ((4.0 * T[nx + x] - T[2 * nx + x]) - 3.0 * T[x]) / 2.0;
-            qb += (-lambda_s) * dTdy;
-            // face flux through the heater surface (harmonic-mean conductance)
-            const double l1 = cv_chi * rho[x];
-            const double lf = (2.0 * (lambda_s * l1)) / (lambda_s + l1);
-            qt += (-lf) * (T[(size_t)ns * nx + x] - T[(size_t)(ns - 1) * nx + x]);
+            const int nsw = model_a ? 1 : ns;  // T row of the first fluid row
+            // face flux through the heater surface or the model-A wall link
+            // (harmonic-mean conductance)
+            const double l1 = cv_chi * rho[x], l0 = model_a ? cv_chi * rho[x] : lambda_s;
+            const double lf = (2.0 * (l0 * l1)) / (l0 + l1);
+            const double q = (-lf) * (T[(size_t)nsw * nx + x] - T[(size_t)(nsw - 1) * nx + x]);
+            qt += q;
+            if (model_a) {
+                qb += q;  // no heater: the wall flux stands for both
+            } else {
+                // Eq. 36 at the heater bottom, rows 0..2
+                const double dTdy = ((4.0 * T[nx + x] - T[2 * nx + x]) - 3.0 * T[x]) / 2.0;
+                qb += (-lambda_s) * dTdy;
+            }
         }
     }
     m = warp_sum(m); v = warp_sum(v); qb = warp_sum(qb); qt = warp_sum(qt);
@@ -81,7 +93,7 @@ k_static_partials(const double *__restrict__ rho, const double *__restrict__ T, 
 // Stage 2 (one block): fixed-order sum of the partials, scaled to the same
 // four values as the per-step diagnostics series.
 __global__ void __launch_bounds__(kThreads)
-k_static_final(const double *__restrict__ partials, int nblk, int nx, int nf, int ns, double *__restrict__ out) {
+k_static_final(const double *__restrict__ partials, int nblk, int nx, int nf, int has_flux_i, double *__restrict__ out) {
     __shared__ double sh[4][kThreads / 32];
     double a[4] = {0.0, 0.0, 0.0, 0.0};
     for (int b = threadIdx.x; b < nblk; b += kThreads)
@@ -96,7 +108,7 @@ k_static_final(const double *__restrict__ partials, int nblk, int nx, int nf, in
         double s[4] = {0.0, 0.0, 0.0, 0.0};
         for (int c = 0; c < 4; c++)
             for (int i = 0; i < kThreads / 32; i++) s[c] += sh[c][i];
-        const double has_flux = ns >= 3 ? 1.0 : 0.0;
+        const double has_flux = has_flux_i ? 1.0 : 0.0;
         out[0] = has_flux * s[2] / (double)nx;        // mean heater-bottom flux
         out[1] = has_flux * s[3] / (double)nx;        // mean heater-surface flux
         out[2] = s[1] / ((double)nx * (double)nf);    // vapour fraction
@@ -107,14 +119,20 @@ k_static_final(const double *__restrict__ partials, int nblk, int nx, int nf, in
 }  // namespace
 
 extern "C" int lbm_diagnostics_static(const double *rho, const double *T, int32_t nx, int32_t ny_fluid,
-                                      int32_t ny_solid, double lambda_s, double cv_chi, double rho_L,
-                                      double rho_V, double *out, void *stream) {
+                                      int32_t ny_solid, int32_t flags, double lambda_s, double cv_chi,
+                                      double rho_L, double rho_V, double *out, void *stream) {
     if (!rho || !T || !out) {
         lbmgb::set_global_error("lbm_diagnostics_static: rho, T and out must be device pointers, not NULL");
         return LBM_E_INVAL;
     }
     if (nx < 1 || ny_fluid < 1 || ny_solid < 0) {
         lbmgb::set_global_error("lbm_diagnostics_static: nx, ny_fluid must be >= 1 and ny_solid >= 0");
+        return LBM_E_INVAL;
+    }
+    const bool periodic = (flags & LBM_PERIODIC_Y) != 0;
+    if (ny_solid == 1 || ny_solid == 2 || (periodic && ny_solid != 0)) {
+        lbmgb::set_global_error("lbm_diagnostics_static: ny_solid must be >= 3 (heater), or 0 (model A, or a "
+                                "domain periodic in y)");
         return LBM_E_INVAL;
     }
     const long long sites = (long long)nx * ny_fluid;
@@ -150,8 +168,9 @@ extern "C" int lbm_diagnostics_static(const double *rho, const double *T, int32_
     const int nblk = (int)((std::max<long long>(sites, nx) + kSitesPerBlock - 1) / kSitesPerBlock);
     cudaStream_t s = (cudaStream_t)stream;
     const double threshold = 0.5 * (rho_L + rho_V);
-    k_static_partials<<<nblk, kThreads, 0, s>>>(rho, T, nx, ny_fluid, ny_solid, lambda_s, cv_chi, threshold, partials);
-    k_static_final<<<1, kThreads, 0, s>>>(partials, nblk, nx, ny_fluid, ny_solid, out);
+    k_static_partials<<<nblk, kThreads, 0, s>>>(rho, T, nx, ny_fluid, ny_solid, periodic ? 1 : 0, lambda_s, cv_chi,
+                                                threshold, partials);
+    k_static_final<<<1, kThreads, 0, s>>>(partials, nblk, nx, ny_fluid, periodic ? 0 : 1, out);
     e = cudaGetLastError();
     if (e != cudaSuccess) {
         lbmgb::set_global_error(std::string("lbm_diagnostics_static: launch failed: ") + cudaGetErrorString(e));

@@ -163,7 +163,7 @@ def load(path: str = LIB_PATH):
     L.lbm_server_destroy.argtypes = [C.c_void_p]
     L.lbm_server_last_error.argtypes = [C.c_void_p]
     L.lbm_server_last_error.restype = C.c_char_p
-    L.lbm_diagnostics_static.argtypes = [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_int32,
+    L.lbm_diagnostics_static.argtypes = [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
                                          C.c_double, C.c_double, C.c_double, C.c_double, C.c_void_p,
                                          C.c_void_p]
     L.lbm_peak_fma.argtypes = [C.c_int32, C.c_int32, C.c_int32, _D]
@@ -392,7 +392,8 @@ class Run:
 def diagnostics_static(rho_ptr: int, T_ptr: int, cfg, out_ptr: int, stream=None):
     """Allocation-free diagnostics of a state held in float64 device arrays
     (see lbm_diagnostics_static in include/lbm.h); out_ptr receives 4 doubles."""
-    rc = load().lbm_diagnostics_static(rho_ptr, T_ptr, cfg.nx, cfg.nf, cfg.ns, cfg.lambda_s, cfg.cv_chi,
+    flags = LBM_PERIODIC_Y if cfg.periodic_y else 0
+    rc = load().lbm_diagnostics_static(rho_ptr, T_ptr, cfg.nx, cfg.nf, cfg.ns, flags, cfg.lambda_s, cfg.cv_chi,
                                        cfg.rho_L, cfg.rho_V, out_ptr, stream)
     _check(rc, None, "lbm_diagnostics_static")
 

@@ -24,13 +24,27 @@ def _lib():
     lbm.load()
 
 
-def test_static_diagnostics_match_the_step_diagnostics_twice():
+CASES = {
+    # heater rows under the fluid (model B)
+    "heater": lambda: W.small_parity().replace(bc_mode="noise", spot_x=(), c_w_spot=(), rho_mean=2.42),
+    # no heater (model A): T has one wall row below the fluid; both flux
+    # slots carry the wall flux
+    "model_a": lambda: W.small_parity().replace(nx=48, nf=40, ns=0, liquid_rows=13, bc_mode="noise", spot_x=(),
+                                                c_w_spot=(), rho_mean=2.42),
+    # periodic in y: no wall, both fluxes zero
+    "periodic": lambda: W.periodic_box(40, 30, liquid_rows=10, init_noise=1e-3, isothermal=False),
+}
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_static_diagnostics_match_the_step_diagnostics_twice(case):
     torch = pytest.importorskip("torch")
-    cfg = W.small_parity().replace(bc_mode="noise", spot_x=(), c_w_spot=(), rho_mean=2.42)
+    cfg = CASES[case]()
     run = lbm.Run(cfg)
     dev = torch.device("cuda", 0)
     rho = torch.empty((cfg.nf, cfg.nx), dtype=torch.float64, device=dev)
-    T = torch.empty((cfg.ns + cfg.nf, cfg.nx), dtype=torch.float64, device=dev)
+    nt = cfg.nf + (1 if cfg.model_a else cfg.ns)
+    T = torch.empty((nt, cfg.nx), dtype=torch.float64, device=dev)
     out = torch.full((4,), float("nan"), dtype=torch.float64, device=dev)
     for steps in (7, 25):
         run.step(steps)
@@ -41,7 +55,21 @@ def test_static_diagnostics_match_the_step_diagnostics_twice():
         torch.cuda.synchronize(dev)
         got = out.cpu().numpy()
         np.testing.assert_allclose(got, want, rtol=TOL, atol=1e-15)
-        assert got[0] != 0.0 and 0.0 < got[2] < 1.0
+        assert 0.0 < got[2] < 1.0
+        if case == "periodic":
+            assert got[0] == 0.0 and got[1] == 0.0
+        else:
+            assert got[0] != 0.0 and got[1] != 0.0
+        if case == "model_a":
+            assert got[0] == got[1]
+
+
+def test_static_diagnostics_reject_heater_rows_the_library_does_not_build():
+    pytest.importorskip("torch")
+    for ns in (1, 2):
+        with pytest.raises(lbm.LbmError) as ei:
+            lbm.diagnostics_static(1, 1, W.small_parity().replace(ns=ns), 1)
+        assert ei.value.code == lbm.LBM_E_INVAL
 
 
 def test_static_diagnostics_reject_sizes_beyond_the_capacity():
