@@ -12,6 +12,12 @@ namespace lbmgb {
 enum { FLAG_PERIODIC_Y = 1, FLAG_ISOTHERMAL = 2, FLAG_FROZEN_FLOW = 4, FLAG_MODEL_A = 8 };
 enum { TOP_WALL = 0, TOP_OUTFLOW = 1 };
 enum { BCM_SPOTS = 0, BCM_NOISE = 1, BCM_SINE = 2 };
+// ERRW_TIMEOUT: a staged-copy wait ran out (100 ms).  The block stops, then
+// waits once more (bounded) for each stage with copies outstanding before it
+// exits.  If the copy engine itself has stalled, copies can still be in flight
+// when those waits also run out, and could land in shared memory that a later
+// block owns: the step's results are invalid either way, and the host reports
+// LBM_E_TIMEOUT.
 enum { ERRW_PSI = 1, ERRW_NONFINITE_RHO = 2, ERRW_NONFINITE_T = 4, ERRW_TIMEOUT = 8 };
 enum { TAG_INIT_NOISE = 1, TAG_BOTTOM_NOISE = 2 };
 enum { SERIES_WIDTH = 4 };

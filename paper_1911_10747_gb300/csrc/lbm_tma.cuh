@@ -161,6 +161,7 @@ k_flow_tma(const __grid_constant__ CUtensorMap map_f, const __grid_constant__ CU
     int cxt = (int)blockIdx.x % tiles_x, cyt = (int)blockIdx.x / tiles_x;
     uint32_t phase = 0;  // bit s: parity of stage s's next completion
     int pending = -1;    // stage with copies in flight that nobody waited for
+    int stalled = -1;    // stage whose wait ran out
     if (tid == 0 && (int)blockIdx.x < ntiles) stage_tile(cxt, cyt, 0);
     if ((int)blockIdx.x < ntiles) pending = 0;
     int k = 0;  // tiles done by this block
@@ -216,6 +217,7 @@ k_flow_tma(const __grid_constant__ CUtensorMap map_f, const __grid_constant__ CU
         }
         if (__syncthreads_or(!ok)) {  // a stage never completed: stop cleanly
             errbits |= ERRW_TIMEOUT;
+            stalled = s;
             break;
         }
 
@@ -251,10 +253,13 @@ k_flow_tma(const __grid_constant__ CUtensorMap map_f, const __grid_constant__ CU
         __syncthreads();  // s_psi and this stage are rewritten
         cxt = nxt; cyt = nyt;
     }
-    if (pending >= 0 && tid == 0) {
-        // only after a timeout: let the copies into the other stage land
-        // before the block's shared memory is released
-        mbar_wait(&bar[pending], (phase >> pending) & 1u);
+    if (tid == 0) {
+        // only after a timeout: let the copies into the other stage, and any
+        // still owed to the stage whose wait ran out, land before the block's
+        // shared memory is released (each wait bounded; the stalled stage's
+        // parity bit was already flipped at its wait)
+        if (pending >= 0) mbar_wait(&bar[pending], (phase >> pending) & 1u);
+        if (stalled >= 0) mbar_wait(&bar[stalled], ((phase >> stalled) & 1u) ^ 1u);
     }
     #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
