@@ -251,6 +251,17 @@ void orc_relax(const double *m, const double *meq, const double *S, const double
 /* ---- run object ---------------------------------------------------------- */
 static int wrapx(int x, int nx) { return ((x % nx) + nx) % nx; }
 
+/* Threads for the per-site loops (1 = serial, the checker's setting).  Each
+ * loop iteration writes only its own sites and reads values no other
+ * iteration of the same loop writes, and the diagnostics sums stay serial,
+ * so any thread count gives bit-identical results (built without OpenMP the
+ * pragmas are ignored and the count has no effect). */
+static int g_threads = 1;
+void orc_set_threads(int n) { g_threads = n > 0 ? n : 1; }
+int orc_threads(void) { return g_threads; }
+#define ORC_PARALLEL_ROWS _Pragma("omp parallel for schedule(static) num_threads(g_threads) if(g_threads > 1)")
+#define ORC_PARALLEL_ROWS_ERR _Pragma("omp parallel for schedule(static) num_threads(g_threads) if(g_threads > 1) reduction(|:err)")
+
 void orc_destroy(orc_run *r)
 {
     if (!r) return;
@@ -369,6 +380,8 @@ static void lbm_part(orc_run *r)
     const double tau_e = 1.0 / p->s[1], tau_s = 1.0 / p->s[2];
 
     /* 1. density (Eq. 10) and pseudopotential (Eq. 12-13) at every fluid site */
+    unsigned err = 0;
+    ORC_PARALLEL_ROWS_ERR
     for (int y = 0; y < nf; y++)
         for (int x = 0; x < nx; x++) {
             size_t k = (size_t)y * nx + x;
@@ -378,11 +391,13 @@ static void lbm_part(orc_run *r)
             double T = r->T[(size_t)(ns + y) * nx + x];
             r->rho[k] = rho;
             r->psi[k] = orc_psi(rho, T, p->a, p->b, p->R, r->kappa, r->Tc, p->G, &bad);
-            if (bad) r->err |= ERR_PSI;
-            if (!isfinite(rho)) r->err |= ERR_NONFINITE;
+            if (bad) err |= ERR_PSI;
+            if (!isfinite(rho)) err |= ERR_NONFINITE;
         }
+    r->err |= err;
 
     /* 2-4. forces, velocity, relaxation time, MRT collision at every site */
+    ORC_PARALLEL_ROWS
     for (int y = 0; y < nf; y++)
         for (int x = 0; x < nx; x++) {
             size_t k = (size_t)y * nx + x;
@@ -441,6 +456,7 @@ static void lbm_part(orc_run *r)
     /* 5. streaming, Eq. 8, pulled from x - e_i; halfway bounce-back (static
      * walls) when x - e_i is a heater or top-wall site; OUTFLOW top (option):
      * unknown downward populations copied from the row below (zero gradient). */
+    ORC_PARALLEL_ROWS
     for (int y = 0; y < nf; y++)
         for (int x = 0; x < nx; x++) {
             size_t k = (size_t)y * nx + x;
@@ -508,6 +524,7 @@ static void fd_part(orc_run *r)
     const int py = (p->flags & F_PERIODIC_Y) != 0;
     const int ext = py ? nt : nt + 1; /* rows held in the work arrays */
     /* frozen fields on the extended grid */
+    ORC_PARALLEL_ROWS
     for (int row = 0; row < ext; row++)
         for (int x = 0; x < nx; x++) {
             size_t k = (size_t)row * nx + x;
@@ -526,6 +543,7 @@ static void fd_part(orc_run *r)
             }
         }
     /* Dirichlet rows: bottom row 0 already holds T_b(x, n); top ghost = T_sat */
+    ORC_PARALLEL_ROWS
     for (int row = 0; row < ext; row++)
         for (int x = 0; x < nx; x++) {
             size_t k = (size_t)row * nx + x;
@@ -534,8 +552,10 @@ static void fd_part(orc_run *r)
     const int r0 = py ? 0 : 1, r1 = nt; /* evolved rows [r0, r1) */
     /* Eq. 25-26 */
     for (int stage = 0; stage < 4; stage++) {
+        ORC_PARALLEL_ROWS
         for (int row = r0; row < r1; row++)
             for (int x = 0; x < nx; x++) r->h[(size_t)row * nx + x] = K_site(r, r->Tk, row, x);
+        ORC_PARALLEL_ROWS
         for (int row = r0; row < r1; row++)
             for (int x = 0; x < nx; x++) {
                 size_t k = (size_t)row * nx + x;
@@ -553,20 +573,25 @@ static void fd_part(orc_run *r)
                     r->acc[k] = r->acc[k] + hk;
                 }
             }
-        if (stage < 3)
+        if (stage < 3) {
+            ORC_PARALLEL_ROWS
             for (int row = r0; row < r1; row++)
                 for (int x = 0; x < nx; x++) {
                     size_t k = (size_t)row * nx + x;
                     r->Tk[k] = r->Ta[k];
                 }
+        }
     }
+    unsigned err = 0;
+    ORC_PARALLEL_ROWS_ERR
     for (int row = r0; row < r1; row++)
         for (int x = 0; x < nx; x++) {
             size_t k = (size_t)row * nx + x;
             double Tn1 = r->T[k] + r->acc[k] / 6.0;
-            if (!isfinite(Tn1)) r->err |= ERR_NONFINITE;
+            if (!isfinite(Tn1)) err |= ERR_NONFINITE;
             r->T[k] = Tn1;
         }
+    r->err |= err;
 }
 
 /* Diagnostics after the step: Eq. 36/39 heat flux at the heater bottom

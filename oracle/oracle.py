@@ -21,13 +21,29 @@ _LIB = os.path.join(_HERE, "liblbm_oracle.so")
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc -O2 and no FMA contraction."""
+    """Compile the oracle with gcc -O2 and no FMA contraction, with OpenMP
+    for the optional threaded per-site loops (without it if the compiler has
+    no OpenMP runtime: the loops then run serially whatever the thread count)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + ".tmp.%d" % os.getpid()
-        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-std=c11",
-                               "-D_DEFAULT_SOURCE", "-o", tmp, _SRC, "-lm"])
+        base = ["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-std=c11", "-D_DEFAULT_SOURCE", "-o", tmp,
+                _SRC, "-lm"]
+        try:
+            subprocess.check_call(base + ["-fopenmp"], stderr=subprocess.DEVNULL)
+        except subprocess.CalledProcessError:
+            subprocess.check_call(base)
         os.replace(tmp, _LIB)
     return _LIB
+
+
+def set_threads(n: int) -> None:
+    """Threads for the oracle's per-site loops (1: serial).  Results are
+    bit-identical for every count; the diagnostics sums stay serial."""
+    lib().orc_set_threads(int(n))
+
+
+def threads() -> int:
+    return int(lib().orc_threads())
 
 
 class _Params(C.Structure):
@@ -60,6 +76,8 @@ def lib():
         L.orc_create.argtypes = [C.POINTER(_Params)]
         L.orc_destroy.argtypes = [C.c_void_p]
         L.orc_step.argtypes = [C.c_void_p, C.c_longlong]
+        L.orc_set_threads.argtypes = [C.c_int]
+        L.orc_threads.restype = C.c_int
         for name in ("orc_f", "orc_T", "orc_rho", "orc_ux", "orc_uy", "orc_q_top", "orc_diag"):
             getattr(L, name).restype = _D
             getattr(L, name).argtypes = [C.c_void_p]
