@@ -3,6 +3,7 @@
 // the flow and heat kernels are compiled; lbm_autotune picks among them.
 #include "lbm_fast.cuh"
 #include "lbm_tma.cuh"
+#include "lbm_heatwave.cuh"
 
 namespace lbmgb {
 namespace {
@@ -23,6 +24,9 @@ cudaError_t diag(const DevParams &p, const StepBuffers &b, int nblk, cudaStream_
     {"heatrows_" #BW "x" #BY "x" #R, HeatRowsShape<P, BW, BY, R, MB>::launch, HeatRowsShape<P, BW, BY, R, MB>::prepare}
 #define HEATP(P, BY, R, MB) \
     {"heatpair_64x" #BY "x" #R, HeatPairShape<P, BY, R, MB>::launch, HeatPairShape<P, BY, R, MB>::prepare}
+#define HEATW(P, CL, WPB, MB, RS) \
+    {"heatwave_c" #CL "_w" #WPB "_b" #MB "_r" #RS, HeatWaveShape<P, CL, WPB, MB, RS>::launch, \
+     HeatWaveShape<P, CL, WPB, MB, RS>::prepare}
 #define HEATV(P, TX, TY, BX, BY) \
     {"heat_" #TX "x" #TY "_t" #BX "x" #BY, HeatFastShape<P, TX, TY, BX, BY>::launch, HeatFastShape<P, TX, TY, BX, BY>::prepare}
 
@@ -35,6 +39,7 @@ const HeatVariant heats32[] = {
     HEATS(PolicyF32, 64, 6, 6, 1),
     HEATS(PolicyF32, 32, 8, 4, 2),
     HEATP(PolicyF32, 12, 4, 1), HEATP(PolicyF32, 8, 4, 1),
+    HEATW(PolicyF32, 2, 2, 4, 8),
     HEATV(PolicyF32, 32, 16, 32, 8), HEATV(PolicyF32, 64, 32, 32, 16),
 };
 const FlowVariant flows16[] = {FLOWP(PolicyF16, 32, 8, 2, 2), FLOWV(PolicyF16, 32, 8, 2, 3)};

@@ -12,8 +12,8 @@ cudaError_t diag(const DevParams &p, const StepBuffers &b, int nblk, cudaStream_
     return launch_diag<P, 512>(p, b, nblk, s);
 }
 cudaError_t no_prepare() { return cudaSuccess; }
-const FlowVariant flows[] = {{"flow64_32x16", Flow::launch, Flow::blocks, no_prepare}};
-const HeatVariant heats[] = {{"heat64_32x16", Heat::launch, Heat::prepare}};
+const FlowVariant flows[] = {{"flow64_32x8x2", Flow::launch, Flow::blocks, no_prepare}};
+const HeatVariant heats[] = {{"heat64_32x16_t256", Heat::launch, Heat::prepare}};
 const KernelSet ks = {"fp64", sizeof(double), sizeof(double), sizeof(double), 1, flows, 1, heats, diag,
                       launch_init<P>, launch_import<P>, launch_export<P>};
 }  // namespace

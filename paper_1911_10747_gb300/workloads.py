@@ -28,7 +28,8 @@ DEFAULT_S = (1.0, 0.8, 0.8, 1.0, 1.1, 1.0, 1.1, 1.0, 1.0)
 
 #: Weight of the thermodynamic-consistency term of Eq. 9 (the paper does not
 #: print its value); chosen so that a flat interface at 0.86 Tc reproduces the
-#: Maxwell coexistence densities (see tests/test_oracle_physics.py).
+#: Maxwell coexistence densities (see test_flat_interface_coexistence_matches_maxwell
+#: in tests/test_oracle_step.py).
 DEFAULT_VARPI = 0.11
 
 #: Wettability coefficients c_w = G_w psi(rho_w) of Eq. 14.  The paper fixes

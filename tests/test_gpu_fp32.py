@@ -214,15 +214,16 @@ def test_fp32_bulk_copy_flow_in_a_periodic_box():
     dict(nx=40, nf=33, ns=4, liquid_rows=11, top_mode="outflow", bc_mode="noise", spot_x=(), c_w_spot=()),
     dict(nx=96, nf=40, ns=0, liquid_rows=13, bc_mode="sine", spot_x=(), c_w_spot=()),
 ])
-def test_fp32_paired_column_heat_variants_against_the_oracle(kw):
-    """The heat kernels that hold two columns per thread as packed pairs:
-    several tiles across with a ragged last tile, a domain narrower than one
-    tile (columns wrap inside the tile), model A, each bottom mode."""
+def test_fp32_paired_column_and_wavefront_heat_variants_against_the_oracle(kw):
+    """The heat kernels that hold two columns per thread as packed pairs and
+    the row-wavefront kernels (one warp per column strip): several tiles or
+    strips across with a ragged last one, a domain narrower than one tile or
+    strip (columns wrap inside it), model A, each bottom mode."""
     cfg = W.small_parity(precision="fp32").replace(rho_mean=2.3, **kw)
     if cfg.bc_mode == "sine":
         cfg = cfg.replace(sine_t0=5, sine_t1=50, sine_wavelength=48.0)
     names = lbm.Run(cfg).variants()["heat"]
-    pair = [i for i, n in enumerate(names) if n.startswith("heatpair_")]
+    pair = [i for i, n in enumerate(names) if n.startswith(("heatpair_", "heatwave_"))]
     assert pair
     o = O.OracleRun(cfg)
     o.step(60)
