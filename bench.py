@@ -472,7 +472,8 @@ def measure_chf(lbm, W, steps):
                                  spot_x=W.scaled_spots(256), spot_half_width=3,
                                  c_w_spot=W.DEFAULT_CW_SPOTS, g=W.stable_gravity(384, 128), seed=21)
     dts = [0.04, 0.08, 0.12, 0.16, 0.20, 0.24, 0.28]
-    cfgs = [base.replace(T_b_over_Tc=0.86 + d, precision=p) for p in ("fp32", "fp64", "fp16") for d in dts]
+    precs = ("fp32", "fp64", "fp16", "fp32_dfsrc")
+    cfgs = [base.replace(T_b_over_Tc=0.86 + d, precision=p) for p in precs for d in dts]
     runs = [lbm.Run(c, series_capacity=steps + 8) for c in cfgs]
     alive = list(range(len(runs)))
     fault = [None] * len(runs)
@@ -505,16 +506,23 @@ def measure_chf(lbm, W, steps):
     for r in runs:
         r.close()
     n = len(dts)
-    q32, q64, q16 = q[:n], q[n:2 * n], q[2 * n:]
+    q32, q64, q16, qdf = q[:n], q[n:2 * n], q[2 * n:3 * n], q[3 * n:]
     both = [j for j in range(n) if q32[j] is not None and q64[j] is not None]
     c32 = max(q32[j] for j in both) if both else None
     c64 = max(q64[j] for j in both) if both else None
     all3 = [j for j in both if q16[j] is not None]
     c16 = max(q16[j] for j in all3) if all3 else None
     c64b = max(q64[j] for j in all3) if all3 else None
+    bdf = [j for j in both if qdf[j] is not None]
+    cdf = max(qdf[j] for j in bdf) if bdf else None
+    c64d = max(q64[j] for j in bdf) if bdf else None
     return {"domain": "256x384 fluid + 16 heater rows, spots", "steps": steps, "superheats_over_Tc": dts,
-            "q_fp32": q32, "q_fp64": q64, "q_fp16": q16, "fault_step_fp32": fault[:n],
-            "fault_step_fp64": fault[n:2 * n], "fault_step_fp16": fault[2 * n:],
+            "q_fp32": q32, "q_fp64": q64, "q_fp16": q16, "q_fp32_dfsrc": qdf, "fault_step_fp32": fault[:n],
+            "fault_step_fp64": fault[n:2 * n], "fault_step_fp16": fault[2 * n:3 * n],
+            "fault_step_fp32_dfsrc": fault[3 * n:],
+            "chf_rel_error_fp32_dfsrc": abs(cdf - c64d) / abs(c64d) if bdf else None,
+            "max_rel_error_curve_fp32_dfsrc": max(abs(qdf[j] - q64[j]) / abs(q64[j]) for j in bdf) if bdf else None,
+            "max_rel_diff_curve_fp32_vs_dfsrc": max(abs(q32[j] - qdf[j]) / abs(qdf[j]) for j in bdf) if bdf else None,
             "chf_fp32": c32, "chf_fp64": c64, "chf_fp16": c16,
             "chf_superheat_fp32": dts[q32.index(c32)] if both else None,
             "chf_superheat_fp64": dts[q64.index(c64)] if both else None,
@@ -523,6 +531,55 @@ def measure_chf(lbm, W, steps):
             "chf_rel_error_fp16": abs(c16 - c64b) / abs(c64b) if all3 else None,
             "max_rel_error_curve_fp16": max(abs(q16[j] - q64[j]) / abs(q64[j]) for j in all3) if all3 else None,
             "seconds": dt}
+
+
+def measure_dfsrc(lbm, W, torch, stream, steps, err_steps=20):
+    """FP32 with the Eq. 24 source in double-float arithmetic on the
+    benchmarked workload: step time (autotuned among its heat shapes), and
+    the errors of it and of the all-FP32 path on the same heat-kernel shape
+    after `err_steps` steps against the FP64 GPU path (which matches the FP64
+    oracle bit for bit in the parity tests), so the source term's share of
+    the FP32 error shows."""
+    import numpy as np
+    cfg = W.large(precision="fp32_dfsrc", seed=3)
+    r = lbm.Run(cfg, stream=stream.cuda_stream)
+    r.autotune(10)
+    v = r.variants()
+    r.step(3)
+    r.sync()
+    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a0.record(stream)
+    r.step(steps)
+    a1.record(stream)
+    a1.synchronize()
+    ms = a0.elapsed_time(a1) / steps
+    r.set_timing(True)
+    r.step(min(steps, 100))
+    kms, _ = r.kernel_times()
+    r.close()
+    torch.cuda.empty_cache()
+    ref = lbm.Run(W.large(precision="fp64", seed=3), stream=stream.cuda_stream)
+    ref.step(err_steps)
+    want = ref.fields(("rho", "T"))
+    ref.close()
+    torch.cuda.empty_cache()
+    errs = {}
+    for prec, heat in (("fp32", "heatrows_64x8x4"), ("fp32_dfsrc", "heatrows_64x8x4_dfsrc")):
+        g = lbm.Run(W.large(precision=prec, seed=3), stream=stream.cuda_stream)
+        gv = g.variants()
+        g.select_variants(0, gv["heat"].index(heat))
+        g.step(err_steps)
+        got = g.fields(("rho", "T"))
+        g.close()
+        torch.cuda.empty_cache()
+        errs[prec] = {k: float(np.max(np.abs(got[k] - want[k]) / np.abs(want[k]))) for k in ("rho", "T")}
+    return {"value": cfg.fluid_sites / (ms / 1e3) / 1e6, "unit": "MLUPS", "ms_per_step": ms, "steps": steps,
+            "kernel_ms": {"flow": kms[0], "heat": kms[1], "diag": kms[2]},
+            "variants": {"flow": v["flow"][v["selected"][0]], "heat": v["heat"][v["selected"][1]]},
+            "max_rel_error_vs_fp64": errs, "error_steps": err_steps,
+            "note": "source term of Eq. 24 in double-float (FP32 pairs, ~48-bit significand); errors after "
+                    f"{err_steps} steps against the FP64 GPU path, both FP32 runs on the same heat shape "
+                    "(heatrows_64x8x4) and flow variant"}
 
 
 def run_ours(args):
@@ -699,6 +756,11 @@ def run_ours(args):
                 "flow_roofline": {"bound": "hbm", "achieved": fl16, "peak": hbm, "unit": "GB/s", "frac": fl16 / hbm,
                                   "bytes_per_site": ALG_FLOW_BYTES["fp16"]}}
 
+    # ---- FP32 with the Eq. 24 source in double-float arithmetic ----
+    dfsrc = None
+    if not args.no_dfsrc and args.precision == "fp32":
+        dfsrc = measure_dfsrc(lbm, W, torch, stream, max(20, min(500, args.steps // 4)))
+
     # ---- boiling-curve sweep: 48 runs batched (FP32, one concurrent graph)
     # versus the same runs one after another in FP64 ----
     sweep = None
@@ -755,6 +817,7 @@ def run_ours(args):
             "cpu_baseline": cpu,
             "fp64": fp64,
             "fp16": fp16,
+            "fp32_dfsrc": dfsrc,
             "sweep": sweep,
             "serve": serve,
             "chf": chf,
@@ -778,6 +841,7 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-fp16", action="store_true", help="skip the FP16-storage throughput block")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-dfsrc", action="store_true", help="skip the double-float source-term block")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--sweep-steps", type=int, default=200)

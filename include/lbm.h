@@ -64,7 +64,12 @@ enum lbm_status {
 
 enum lbm_top_mode { LBM_TOP_WALL = 0, LBM_TOP_OUTFLOW = 1 };
 enum lbm_bc_mode { LBM_BC_SPOTS = 0, LBM_BC_NOISE = 1, LBM_BC_SINE = 2 };
-enum lbm_precision { LBM_FP64 = 0, LBM_FP32 = 1, LBM_FP16 = 2 };
+/* LBM_FP32_DFSRC: LBM_FP32 with the phase-change source of Eq. 24
+ * (-(T / rho C_V)(dp/dT)_rho div u) evaluated in double-float arithmetic
+ * (pairs of FP32 numbers, about 48 significand bits) instead of FP32: the
+ * rho-only EOS factors, 1 / (rho C_V) and div u once per step, C1 T +
+ * C2 sqrt(T) at every RK stage.  Everything else as LBM_FP32. */
+enum lbm_precision { LBM_FP64 = 0, LBM_FP32 = 1, LBM_FP16 = 2, LBM_FP32_DFSRC = 3 };
 enum lbm_flags { LBM_PERIODIC_Y = 1, LBM_ISOTHERMAL = 2, LBM_FROZEN_FLOW = 4 };
 enum lbm_field_mask {
     LBM_FIELD_RHO = 1, LBM_FIELD_UX = 2, LBM_FIELD_UY = 4, LBM_FIELD_T = 8, LBM_FIELD_F = 16
@@ -138,7 +143,8 @@ typedef struct {
 /* Library options. */
 typedef struct {
     int32_t precision;      /* lbm_precision: FP64 (oracle parity), FP32 shifted
-                               populations, FP16 population storage (probe) */
+                               populations, FP16 population storage (probe),
+                               FP32 with a double-float phase-change source */
     int32_t use_graphs;     /* 1: lbm_step replays a captured two-step CUDA graph */
     void *stream;           /* cudaStream_t to queue work on; NULL: library-owned stream */
     double rho_shift;       /* reference density of the shifted populations; <= 0: rho_mean */

@@ -15,6 +15,7 @@
 #include <type_traits>
 
 #include "lbm_device.cuh"
+#include "lbm_dfloat.cuh"
 
 namespace lbmgb {
 
@@ -33,6 +34,9 @@ struct FParams {
     float a_kappa, kappa_over_Tc, B_coef;          // (dp/dT)_rho pieces: a kappa, kappa / Tc, (1 + kappa) / sqrt(Tc)
     float dTb, Tb_noise, sine_amp, sine_wl;        // bottom: T_b - T_sat, T_b A, amp Tc, wavelength
     unsigned tx_pad;                               // test hook of the staged-copy waits (0)
+    // the same constants as double-float pairs (hi, lo) for the heat kernels
+    // that evaluate the Eq. 24 source in double-float arithmetic
+    float df_tsat[2], df_b[2], df_R[2], df_akappa[2], df_koTc[2], df_Bcoef[2], df_cv[2], df_w1[2], df_w2[2];
 };
 
 inline FParams make_fparams(const DevParams &p) {
@@ -56,6 +60,10 @@ inline FParams make_fparams(const DevParams &p) {
     q.dTb = (float)(p.T_b - p.T_sat); q.Tb_noise = (float)(p.T_b * p.bc_noise);
     q.sine_amp = (float)p.sine_amp; q.sine_wl = (float)p.sine_wl;
     q.tx_pad = p.tx_pad;
+    auto split = [](double v, float *o) { o[0] = (float)v; o[1] = (float)(v - (double)o[0]); };
+    split(p.T_sat, q.df_tsat); split(p.b, q.df_b); split(p.R, q.df_R); split(p.a * p.kappa, q.df_akappa);
+    split(p.kappa / p.Tc, q.df_koTc); split((1.0 + p.kappa) / sqrt(p.Tc), q.df_Bcoef); split(p.c_v, q.df_cv);
+    split(1.0 / 9.0, q.df_w1); split(1.0 / 36.0, q.df_w2);
     return q;
 }
 
@@ -912,7 +920,10 @@ __device__ __forceinline__ void cp_async4(float *dst, const float *src, bool pre
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
-template <class P, int BW, int BY, int R, int MINB, bool WIDE>
+// DF: the phase-change source of Eq. 24 in double-float arithmetic (the
+// rho-only EOS factors, 1 / (rho c), div u and C1, C2 once per step; C1 T +
+// C2 sqrt(T) per stage), everything else as in the FP32 kernel.
+template <class P, int BW, int BY, int R, int MINB, bool WIDE, bool DF = false>
 __global__ void __launch_bounds__(BW * BY, MINB)
 k_heat_rows(const FParams p, int tiles_x, int ntiles, const typename P::tst *__restrict__ Tin,
             typename P::tst *__restrict__ Tout, const float *__restrict__ rho_i, const float *__restrict__ ux_i,
@@ -933,6 +944,7 @@ k_heat_rows(const FParams p, int tiles_x, int ntiles, const typename P::tst *__r
     unsigned errbits = 0;
 
     float Tn[R], Tc[R], acc[R], kk[R][8], ks[R], c0[R], c2[R];
+    dfloat C1d[R], C2d[R];  // DF: the source coefficients in double-float
     int pk = 0, px = 0;  // kinds of the staged cells (3 bits per cell) and their column
 
     const int gdx = (int)gridDim.x % tiles_x, gdy = (int)gridDim.x / tiles_x;
@@ -1044,6 +1056,7 @@ k_heat_rows(const FParams p, int tiles_x, int ntiles, const typename P::tst *__r
                 ks[c] = ((kk[c][0] + kk[c][1]) + (kk[c][2] + kk[c][3])) + ((kk[c][4] + kk[c][5]) + (kk[c][6] + kk[c][7]));
                 c0[c] = 0.0f;
                 c2[c] = 0.0f;
+                C1d[c] = C2d[c] = df_from(0.0f);
                 acc[c] = 0.0f;
             }
         }
@@ -1054,13 +1067,20 @@ k_heat_rows(const FParams p, int tiles_x, int ntiles, const typename P::tst *__r
             // advection (-u . grad T = sum_a adv_a T_a, adv_a = -3 w_a (e_a . u))
             // and the (dp/dT)_rho div u source of Eq. 24, with the Eq. 27 gradient
             float dd[R];
+            dfloat Dd[R];  // DF: the same divergence sum in double-float
+            const dfloat dw1 = {p.df_w1[0], p.df_w1[1]}, dw2 = {p.df_w2[0], p.df_w2[1]};
+            auto ddiff = [](float a, float b) { return df_two_sum(a, -b); };  // a - b exactly
             {
                 float Ul[R + 2], Ur[R + 2];
                 column(sU, xl, Ul);
                 column(sU, xr, Ur);
                 #pragma unroll
-                for (int c = 0; c < R; c++)
+                for (int c = 0; c < R; c++) {
                     dd[c] = w1 * (Ur[c + 1] - Ul[c + 1]) + w2 * ((Ur[c + 2] - Ul[c]) + (Ur[c] - Ul[c + 2]));
+                    if constexpr (DF)
+                        Dd[c] = df_add(df_mul(dw1, ddiff(Ur[c + 1], Ul[c + 1])),
+                                       df_mul(dw2, df_add(ddiff(Ur[c + 2], Ul[c]), ddiff(Ur[c], Ul[c + 2]))));
+                }
             }
             {
                 float Vl[R + 2], Vr[R + 2];
@@ -1071,6 +1091,9 @@ k_heat_rows(const FParams p, int tiles_x, int ntiles, const typename P::tst *__r
                 for (int c = 0; c < R; c++) {
                     const float vN = c + 1 < R ? uy[c + 1] : Vt, vS = c > 0 ? uy[c - 1] : Vb;
                     dd[c] += w1 * (vN - vS) + w2 * ((Vr[c + 2] - Vl[c]) - (Vr[c] - Vl[c + 2]));
+                    if constexpr (DF)
+                        Dd[c] = df_add(Dd[c], df_add(df_mul(dw1, ddiff(vN, vS)),
+                                                     df_mul(dw2, df_sub(ddiff(Vr[c + 2], Vl[c]), ddiff(Vr[c], Vl[c + 2])))));
                 }
             }
             #pragma unroll
@@ -1095,9 +1118,26 @@ k_heat_rows(const FParams p, int tiles_x, int ntiles, const typename P::tst *__r
                 const float B = pa * p.B_coef;
                 const float g0 = -divu * irc[c];
                 const float C1 = g0 * A;
-                ks[c] -= C1;
-                c0[c] = C1 * tsat;
-                c2[c] = g0 * B;
+                if constexpr (DF) {
+                    // (dp/dT)_rho = A + B / sqrt(T), C1 = -(3 D / (rho C_V)) A, C2 = -(3 D / (rho C_V)) B
+                    const dfloat one = df_from(1.0f);
+                    const dfloat db = {p.df_b[0], p.df_b[1]}, dR = {p.df_R[0], p.df_R[1]};
+                    const dfloat dak = {p.df_akappa[0], p.df_akappa[1]}, dko = {p.df_koTc[0], p.df_koTc[1]};
+                    const dfloat dBc = {p.df_Bcoef[0], p.df_Bcoef[1]}, dcv = {p.df_cv[0], p.df_cv[1]};
+                    const dfloat bR = df_mul_f(db, r);
+                    const dfloat iomb = df_rcp(df_sub(one, bR));
+                    const dfloat iden = df_rcp(df_add(one, df_mul(bR, df_sub(df_from(2.0f), bR))));
+                    const dfloat akr2 = df_mul(dak, df_two_prod(r, r));
+                    const dfloat Ad = df_sub(df_mul(df_mul_f(dR, r), iomb), df_mul(akr2, df_mul(dko, iden)));
+                    const dfloat Bd = df_mul(akr2, df_mul(dBc, iden));
+                    const dfloat g0d = df_mul(df_mul_f(Dd[c], -3.0f), df_rcp(df_mul_f(dcv, r)));
+                    C1d[c] = df_mul(g0d, Ad);
+                    C2d[c] = df_mul(g0d, Bd);
+                } else {
+                    ks[c] -= C1;
+                    c0[c] = C1 * tsat;
+                    c2[c] = g0 * B;
+                }
             }
         }
         };
@@ -1123,7 +1163,13 @@ k_heat_rows(const FParams p, int tiles_x, int ntiles, const typename P::tst *__r
                     const float t0 = Tc[c];
                     const float tN = c + 1 < R ? Tc[c + 1] : Tt, tS = c > 0 ? Tc[c - 1] : Tb;
                     // T_0 + T_sat > 0 in every cell whose value is used
-                    float v = c0[c] + c2[c] * fast_sqrt(t0 + tsat);
+                    float v;
+                    if constexpr (DF) {
+                        const dfloat ta = df_add(df_from(t0), dfloat{p.df_tsat[0], p.df_tsat[1]});
+                        v = df_to_float(df_add(df_mul(C1d[c], ta), df_mul(C2d[c], df_sqrt(ta))));
+                    } else {
+                        v = c0[c] + c2[c] * fast_sqrt(t0 + tsat);
+                    }
                     v += kk[c][0] * Tr[c + 1] + kk[c][1] * tN + kk[c][2] * Tl[c + 1] + kk[c][3] * tS +
                          kk[c][4] * Tr[c + 2] + kk[c][5] * Tl[c + 2] + kk[c][6] * Tl[c] + kk[c][7] * Tr[c] - ks[c] * t0;
                     h[c] = v;
@@ -1159,14 +1205,14 @@ k_heat_rows(const FParams p, int tiles_x, int ntiles, const typename P::tst *__r
     if (errbits) atomicOr(err, errbits);
 }
 
-template <class P, int BW, int BY, int R, int MINB>
+template <class P, int BW, int BY, int R, int MINB, bool DF = false>
 struct HeatRowsShape {
     static int grid_blocks;
     static cudaError_t prepare() {
         int dev = 0, sms = 0, per = 0;
         cudaError_t e = cudaGetDevice(&dev);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_heat_rows<P, BW, BY, R, MINB, true>, BW * BY, 0);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_heat_rows<P, BW, BY, R, MINB, true, DF>, BW * BY, 0);
         if (e != cudaSuccess) return e;
         grid_blocks = sms * (per > 0 ? per : 1);
         return cudaSuccess;
@@ -1177,15 +1223,15 @@ struct HeatRowsShape {
         const int ntiles = tx * ty;
         const int g = ntiles < grid_blocks ? ntiles : grid_blocks;
         const bool wide = p.nx >= BW && (!(p.flags & FLAG_PERIODIC_Y) || p.nt >= R * BY);
-        auto k = wide ? k_heat_rows<P, BW, BY, R, MINB, true> : k_heat_rows<P, BW, BY, R, MINB, false>;
+        auto k = wide ? k_heat_rows<P, BW, BY, R, MINB, true, DF> : k_heat_rows<P, BW, BY, R, MINB, false, DF>;
         k<<<g, dim3(BW, BY), 0, s>>>(
             make_fparams(p), tx, ntiles, (const typename P::tst *)b.T_in, (typename P::tst *)b.T_out,
             (const float *)b.rho, (const float *)b.ux, (const float *)b.uy, b.step, b.err);
         return cudaGetLastError();
     }
 };
-template <class P, int BW, int BY, int R, int MINB>
-int HeatRowsShape<P, BW, BY, R, MINB>::grid_blocks = 152;
+template <class P, int BW, int BY, int R, int MINB, bool DF>
+int HeatRowsShape<P, BW, BY, R, MINB, DF>::grid_blocks = 152;
 
 // ============================================================================
 // Heat kernel, FP32, paired columns.  The tiles, halo, strips and per-cell

@@ -22,6 +22,9 @@ cudaError_t diag(const DevParams &p, const StepBuffers &b, int nblk, cudaStream_
      FlowTmaShape<P, BY, RY, MB>::prepare}
 #define HEATS(P, BW, BY, R, MB) \
     {"heatrows_" #BW "x" #BY "x" #R, HeatRowsShape<P, BW, BY, R, MB>::launch, HeatRowsShape<P, BW, BY, R, MB>::prepare}
+#define HEATSD(P, BW, BY, R, MB)                                                                 \
+    {"heatrows_" #BW "x" #BY "x" #R "_dfsrc", HeatRowsShape<P, BW, BY, R, MB, true>::launch,          \
+     HeatRowsShape<P, BW, BY, R, MB, true>::prepare}
 #define HEATP(P, BY, R, MB) \
     {"heatpair_64x" #BY "x" #R, HeatPairShape<P, BY, R, MB>::launch, HeatPairShape<P, BY, R, MB>::prepare}
 #define HEATW(P, CL, WPB, MB, RS) \
@@ -42,6 +45,8 @@ const HeatVariant heats32[] = {
     HEATW(PolicyF32, 2, 2, 4, 8),
     HEATV(PolicyF32, 32, 16, 32, 8), HEATV(PolicyF32, 64, 32, 32, 16),
 };
+// the Eq. 24 source in double-float arithmetic (precision LBM_FP32_DFSRC)
+const HeatVariant heats32df[] = {HEATSD(PolicyF32, 64, 8, 4, 1), HEATSD(PolicyF32, 64, 6, 5, 1)};
 const FlowVariant flows16[] = {FLOWP(PolicyF16, 32, 8, 2, 2), FLOWV(PolicyF16, 32, 8, 2, 3)};
 const HeatVariant heats16[] = {HEATS(PolicyF16, 64, 10, 3, 1), HEATS(PolicyF16, 64, 8, 4, 1), HEATP(PolicyF16, 12, 4, 1),
                                HEATV(PolicyF16, 32, 32, 32, 16)};
@@ -50,6 +55,10 @@ const KernelSet ks32 = {"fp32", sizeof(float), sizeof(float), sizeof(float),
                         (int)(sizeof(flows32) / sizeof(flows32[0])), flows32,
                         (int)(sizeof(heats32) / sizeof(heats32[0])), heats32, diag<PolicyF32>,
                         launch_init<PolicyF32>, launch_import<PolicyF32>, launch_export<PolicyF32>};
+const KernelSet ks32df = {"fp32dfsrc", sizeof(float), sizeof(float), sizeof(float),
+                          (int)(sizeof(flows32) / sizeof(flows32[0])), flows32,
+                          (int)(sizeof(heats32df) / sizeof(heats32df[0])), heats32df, diag<PolicyF32>,
+                          launch_init<PolicyF32>, launch_import<PolicyF32>, launch_export<PolicyF32>};
 const KernelSet ks16 = {"fp16", sizeof(__half), sizeof(float), sizeof(float),
                         (int)(sizeof(flows16) / sizeof(flows16[0])), flows16,
                         (int)(sizeof(heats16) / sizeof(heats16[0])), heats16, diag<PolicyF16>,
@@ -57,4 +66,5 @@ const KernelSet ks16 = {"fp16", sizeof(__half), sizeof(float), sizeof(float),
 }  // namespace
 const KernelSet *kernels_fp32() { return &ks32; }
 const KernelSet *kernels_fp16() { return &ks16; }
+const KernelSet *kernels_fp32_dfsrc() { return &ks32df; }
 }  // namespace lbmgb

@@ -106,5 +106,6 @@ void set_global_error(const std::string &msg);
 const KernelSet *kernels_fp64();
 const KernelSet *kernels_fp32();
 const KernelSet *kernels_fp16();
+const KernelSet *kernels_fp32_dfsrc();
 
 }  // namespace lbmgb

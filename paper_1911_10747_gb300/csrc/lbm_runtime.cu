@@ -313,6 +313,7 @@ int lbm_create(const lbm_domain_t *domain, const lbm_heater_t *heater, const lbm
         case LBM_FP64: h->ks = kernels_fp64(); break;
         case LBM_FP32: h->ks = kernels_fp32(); break;
         case LBM_FP16: h->ks = kernels_fp16(); break;
+        case LBM_FP32_DFSRC: h->ks = kernels_fp32_dfsrc(); break;
         default: delete h; return fail(nullptr, LBM_E_INVAL, "opts.precision invalid");
     }
     if ((opts->dev_alloc == nullptr) != (opts->dev_free == nullptr)) {
@@ -910,7 +911,8 @@ int lbm_device_bytes(const lbm_domain_t *domain, const lbm_heater_t *heater, con
     if (!domain || !heater || !opts || !bytes) return fail(nullptr, LBM_E_INVAL, "NULL argument");
     const KernelSet *ks = opts->precision == LBM_FP64 ? kernels_fp64()
                           : opts->precision == LBM_FP32 ? kernels_fp32()
-                          : opts->precision == LBM_FP16 ? kernels_fp16() : nullptr;
+                          : opts->precision == LBM_FP16 ? kernels_fp16()
+                          : opts->precision == LBM_FP32_DFSRC ? kernels_fp32_dfsrc() : nullptr;
     if (!ks) return fail(nullptr, LBM_E_INVAL, "opts.precision invalid");
     if (domain->nx < 1 || domain->ny_fluid < 1 || heater->ny_solid < 0) return fail(nullptr, LBM_E_INVAL, "bad sizes");
     const uint64_t nfl = (uint64_t)domain->nx * domain->ny_fluid;

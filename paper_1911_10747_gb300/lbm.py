@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(_PKG, "liblbm_gb300.so")
 LBM_OK, LBM_E_INVAL, LBM_E_NOMEM, LBM_E_CUDA, LBM_E_NUMERIC, LBM_E_TIMEOUT, LBM_E_STATE = range(7)
 LBM_TOP_WALL, LBM_TOP_OUTFLOW = 0, 1
 LBM_BC_SPOTS, LBM_BC_NOISE, LBM_BC_SINE = 0, 1, 2
-LBM_FP64, LBM_FP32, LBM_FP16 = 0, 1, 2
+LBM_FP64, LBM_FP32, LBM_FP16, LBM_FP32_DFSRC = 0, 1, 2, 3
 LBM_PERIODIC_Y, LBM_ISOTHERMAL, LBM_FROZEN_FLOW = 1, 2, 4
 LBM_FIELD_RHO, LBM_FIELD_UX, LBM_FIELD_UY, LBM_FIELD_T, LBM_FIELD_F = 1, 2, 4, 8, 16
 
@@ -211,7 +211,7 @@ def structs_from_config(cfg, stream=None, use_graphs=True, series_capacity=0, de
     bc.sine_t0, bc.sine_t1 = cfg.sine_t0, cfg.sine_t1
     bc.spot_half_width, bc.c_w_base, bc.c_w_top = cfg.spot_half_width, cfg.c_w_base, cfg.c_w_top
     op = lbm_opts_t()
-    op.precision = {"fp64": LBM_FP64, "fp32": LBM_FP32, "fp16": LBM_FP16}[cfg.precision]
+    op.precision = {"fp64": LBM_FP64, "fp32": LBM_FP32, "fp16": LBM_FP16, "fp32_dfsrc": LBM_FP32_DFSRC}[cfg.precision]
     op.use_graphs = 1 if use_graphs else 0
     op.stream = stream
     op.rho_shift = cfg.rho_shift

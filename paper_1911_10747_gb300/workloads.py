@@ -95,7 +95,8 @@ class RunConfig:
     sine_t0: int = 3000
     sine_t1: int = 15000
     seed: int = 1
-    precision: str = "fp64"      # "fp64", "fp32" (shifted populations) or "fp16" (storage probe)
+    precision: str = "fp64"      # "fp64", "fp32" (shifted populations), "fp16" (storage probe) or
+                                 # "fp32_dfsrc" (FP32 with the Eq. 24 source in double-float arithmetic)
     rho_shift: float = 0.0       # shifted-population reference density; 0 => rho_mean
 
     def replace(self, **kw) -> "RunConfig":
