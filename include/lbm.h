@@ -69,7 +69,10 @@ enum lbm_bc_mode { LBM_BC_SPOTS = 0, LBM_BC_NOISE = 1, LBM_BC_SINE = 2 };
  * (pairs of FP32 numbers, about 48 significand bits) instead of FP32: the
  * rho-only EOS factors, 1 / (rho C_V) and div u once per step, C1 T +
  * C2 sqrt(T) at every RK stage.  Everything else as LBM_FP32. */
-enum lbm_precision { LBM_FP64 = 0, LBM_FP32 = 1, LBM_FP16 = 2, LBM_FP32_DFSRC = 3 };
+/* LBM_FP64_FMA: the FP64 path compiled with fused multiply-add contraction;
+ * faster, no longer bit-identical to a plain evaluation of the formulas
+ * (LBM_FP64), and held to a relative 1e-12 per site of it. */
+enum lbm_precision { LBM_FP64 = 0, LBM_FP32 = 1, LBM_FP16 = 2, LBM_FP32_DFSRC = 3, LBM_FP64_FMA = 4 };
 enum lbm_flags { LBM_PERIODIC_Y = 1, LBM_ISOTHERMAL = 2, LBM_FROZEN_FLOW = 4 };
 enum lbm_field_mask {
     LBM_FIELD_RHO = 1, LBM_FIELD_UX = 2, LBM_FIELD_UY = 4, LBM_FIELD_T = 8, LBM_FIELD_F = 16
@@ -144,7 +147,8 @@ typedef struct {
 typedef struct {
     int32_t precision;      /* lbm_precision: FP64 (oracle parity), FP32 shifted
                                populations, FP16 population storage (probe),
-                               FP32 with a double-float phase-change source */
+                               FP32 with a double-float phase-change source,
+                               FP64 with FMA contraction */
     int32_t use_graphs;     /* 1: lbm_step replays a captured two-step CUDA graph */
     void *stream;           /* cudaStream_t to queue work on; NULL: library-owned stream */
     double rho_shift;       /* reference density of the shifted populations; <= 0: rho_mean */
@@ -276,6 +280,10 @@ int lbm_autotune(lbm_handle h, int iters, double *best_ms);
 int lbm_batch_create(const lbm_handle *runs, int32_t n, lbm_batch *out);
 int lbm_batch_step(lbm_batch b, int64_t n);
 int lbm_batch_sync(lbm_batch b);
+/* Non-blocking: *done = 1 when every kernel queued on the batch and on its
+ * runs' streams has finished, else 0 (faults are reported by
+ * lbm_batch_sync, not here). */
+int lbm_batch_query(lbm_batch b, int32_t *done);
 int lbm_batch_destroy(lbm_batch b);
 const char *lbm_batch_last_error(lbm_batch b);
 
@@ -301,7 +309,17 @@ int lbm_device_bytes(const lbm_domain_t *domain, const lbm_heater_t *heater, con
  * finish times in seconds since the server was created.
  * lbm_server_result copies the final diagnostics (4 values, as one row of
  * lbm_series) and the kept fields (rho: NF*NX, T: NT*NX values, NT as in
- * lbm_fields).  Not thread-safe. */
+ * lbm_fields).
+ * lbm_server_poll is the non-blocking form of a tick: if the chunk in flight
+ * has finished it retires finished runs; it admits queued requests (their
+ * runs are created and initialised on their own streams while a chunk may
+ * still be running); and if no chunk is in flight it launches the next one
+ * over every active run, then returns without waiting.  Requests that
+ * arrive during a chunk are thus admitted at once and join at the next chunk
+ * boundary.  lbm_server_tick first completes a chunk in flight, admits,
+ * launches the next chunk and waits for it (one whole chunk per call).
+ * *finished counts the requests that reached state 2 or 3 in the call.
+ * Not thread-safe. */
 typedef struct lbm_server_s *lbm_server;
 int lbm_server_create(uint64_t hbm_budget_bytes, int32_t max_active, int32_t chunk_steps, int32_t device,
                       lbm_server *out);
@@ -309,6 +327,7 @@ int lbm_server_submit(lbm_server s, const lbm_domain_t *domain, const lbm_heater
                       const lbm_eos_t *eos, const lbm_bc_t *bc, const lbm_opts_t *opts, int64_t steps,
                       int32_t keep_fields, int64_t *id);
 int lbm_server_tick(lbm_server s, int32_t *finished);
+int lbm_server_poll(lbm_server s, int32_t *finished);
 int lbm_server_status(lbm_server s, int64_t id, int32_t *state, double *times /* [3] */);
 int lbm_server_result(lbm_server s, int64_t id, double *diag4, double *rho, double *T);
 int lbm_server_counts(lbm_server s, int32_t *queued, int32_t *active, uint64_t *bytes_in_use);

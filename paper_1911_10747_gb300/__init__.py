@@ -20,6 +20,6 @@ Many independent runs step together with :class:`.lbm.Batch` (one
 concurrent graph); :class:`.lbm.Server` admits runs as they arrive under an
 HBM budget (continuous batching).  Model A is ``ns=0``; the bottom
 condition is ``bc_mode`` = ``"spots"``, ``"noise"`` or ``"sine"``;
-``precision`` = ``"fp64"``, ``"fp32"`` or ``"fp16"`` (storage).
+``precision`` = ``"fp64"``, ``"fp64_fma"``, ``"fp32"``, ``"fp32_dfsrc"`` or ``"fp16"`` (storage).
 """
 __all__ = ["lbm", "workloads"]

@@ -1,7 +1,8 @@
 """Build the CUDA library liblbm_gb300.so in-tree for sm_103a.
 
-Six translation units compiled in parallel by nvcc, then linked:
+Seven translation units compiled in parallel by nvcc, then linked:
   csrc/lbm_fp64.cu     FP64 kernels, -fmad=false (plain rounding of each op)
+  csrc/lbm_fp64fma.cu  the same FP64 kernels with FMA contraction
   csrc/lbm_fp32.cu     FP32 / FP16-storage kernels
   csrc/lbm_runtime.cu  host runtime and the C ABI of include/lbm.h
   csrc/lbm_static_diag.cu  the allocation-free diagnostics entry point
@@ -23,7 +24,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "liblbm_gb300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-UNITS = {"lbm_fp64.cu": ["-fmad=false"], "lbm_fp32.cu": [], "lbm_runtime.cu": [],
+UNITS = {"lbm_fp64.cu": ["-fmad=false"], "lbm_fp64fma.cu": ["-fmad=true"], "lbm_fp32.cu": [], "lbm_runtime.cu": [],
          "lbm_static_diag.cu": ["-fmad=false"], "lbm_server.cu": [], "lbm_peak.cu": []}
 
 

@@ -107,5 +107,6 @@ const KernelSet *kernels_fp64();
 const KernelSet *kernels_fp32();
 const KernelSet *kernels_fp16();
 const KernelSet *kernels_fp32_dfsrc();
+const KernelSet *kernels_fp64_fma();
 
 }  // namespace lbmgb

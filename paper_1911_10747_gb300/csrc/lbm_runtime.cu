@@ -314,6 +314,7 @@ int lbm_create(const lbm_domain_t *domain, const lbm_heater_t *heater, const lbm
         case LBM_FP32: h->ks = kernels_fp32(); break;
         case LBM_FP16: h->ks = kernels_fp16(); break;
         case LBM_FP32_DFSRC: h->ks = kernels_fp32_dfsrc(); break;
+        case LBM_FP64_FMA: h->ks = kernels_fp64_fma(); break;
         default: delete h; return fail(nullptr, LBM_E_INVAL, "opts.precision invalid");
     }
     if ((opts->dev_alloc == nullptr) != (opts->dev_free == nullptr)) {
@@ -893,6 +894,29 @@ int lbm_batch_step(lbm_batch b, int64_t n) {
     return LBM_OK;
 }
 
+int lbm_batch_query(lbm_batch b, int32_t *done) {
+    if (!b || !done) return LBM_E_INVAL;
+    cudaError_t e = cudaSetDevice(b->device);
+    if (e != cudaSuccess) return bfail(b, LBM_E_CUDA, cudaGetErrorString(e));
+    *done = 0;
+    std::vector<cudaStream_t> streams{b->stream};
+    for (auto h : b->runs) {
+        streams.push_back(h->stream);
+        streams.push_back(h->dstream);
+    }
+    for (cudaStream_t st : streams) {
+        if (!st) continue;
+        e = cudaStreamQuery(st);
+        if (e == cudaErrorNotReady) {
+            cudaGetLastError();  // not an error: clear it
+            return LBM_OK;
+        }
+        if (e != cudaSuccess) return bfail(b, LBM_E_CUDA, cudaGetErrorString(e));
+    }
+    *done = 1;
+    return LBM_OK;
+}
+
 int lbm_batch_sync(lbm_batch b) {
     if (!b) return LBM_E_INVAL;
     cudaError_t e = cudaSetDevice(b->device);
@@ -912,7 +936,8 @@ int lbm_device_bytes(const lbm_domain_t *domain, const lbm_heater_t *heater, con
     const KernelSet *ks = opts->precision == LBM_FP64 ? kernels_fp64()
                           : opts->precision == LBM_FP32 ? kernels_fp32()
                           : opts->precision == LBM_FP16 ? kernels_fp16()
-                          : opts->precision == LBM_FP32_DFSRC ? kernels_fp32_dfsrc() : nullptr;
+                          : opts->precision == LBM_FP32_DFSRC ? kernels_fp32_dfsrc()
+                          : opts->precision == LBM_FP64_FMA ? kernels_fp64_fma() : nullptr;
     if (!ks) return fail(nullptr, LBM_E_INVAL, "opts.precision invalid");
     if (domain->nx < 1 || domain->ny_fluid < 1 || heater->ny_solid < 0) return fail(nullptr, LBM_E_INVAL, "bad sizes");
     const uint64_t nfl = (uint64_t)domain->nx * domain->ny_fluid;

@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(_PKG, "liblbm_gb300.so")
 LBM_OK, LBM_E_INVAL, LBM_E_NOMEM, LBM_E_CUDA, LBM_E_NUMERIC, LBM_E_TIMEOUT, LBM_E_STATE = range(7)
 LBM_TOP_WALL, LBM_TOP_OUTFLOW = 0, 1
 LBM_BC_SPOTS, LBM_BC_NOISE, LBM_BC_SINE = 0, 1, 2
-LBM_FP64, LBM_FP32, LBM_FP16, LBM_FP32_DFSRC = 0, 1, 2, 3
+LBM_FP64, LBM_FP32, LBM_FP16, LBM_FP32_DFSRC, LBM_FP64_FMA = 0, 1, 2, 3, 4
 LBM_PERIODIC_Y, LBM_ISOTHERMAL, LBM_FROZEN_FLOW = 1, 2, 4
 LBM_FIELD_RHO, LBM_FIELD_UX, LBM_FIELD_UY, LBM_FIELD_T, LBM_FIELD_F = 1, 2, 4, 8, 16
 
@@ -31,8 +31,8 @@ EXPORTS = ("lbm_create", "lbm_destroy", "lbm_step", "lbm_sync", "lbm_step_count"
            "lbm_set_timing", "lbm_kernel_times", "lbm_kernels_per_step", "lbm_variants",
            "lbm_variant_name", "lbm_select_variants", "lbm_autotune", "lbm_diagnostics_static",
            "lbm_batch_create", "lbm_batch_step", "lbm_batch_sync", "lbm_batch_destroy",
-           "lbm_batch_last_error", "lbm_device_bytes", "lbm_server_create", "lbm_server_submit",
-           "lbm_server_tick", "lbm_server_status", "lbm_server_result", "lbm_server_counts",
+           "lbm_batch_last_error", "lbm_batch_query", "lbm_device_bytes", "lbm_server_create", "lbm_server_submit",
+           "lbm_server_tick", "lbm_server_poll", "lbm_server_status", "lbm_server_result", "lbm_server_counts",
            "lbm_server_destroy", "lbm_server_last_error", "lbm_peak_fma",
            "lbm_last_error",
            "lbm_status_string")
@@ -146,6 +146,7 @@ def load(path: str = LIB_PATH):
     L.lbm_batch_create.argtypes = [C.POINTER(C.c_void_p), C.c_int32, C.POINTER(C.c_void_p)]
     L.lbm_batch_step.argtypes = [C.c_void_p, C.c_int64]
     L.lbm_batch_sync.argtypes = [C.c_void_p]
+    L.lbm_batch_query.argtypes = [C.c_void_p, C.POINTER(C.c_int32)]
     L.lbm_batch_destroy.argtypes = [C.c_void_p]
     L.lbm_batch_last_error.argtypes = [C.c_void_p]
     L.lbm_batch_last_error.restype = C.c_char_p
@@ -156,6 +157,7 @@ def load(path: str = LIB_PATH):
                                     C.POINTER(lbm_eos_t), C.POINTER(lbm_bc_t), C.POINTER(lbm_opts_t),
                                     C.c_int64, C.c_int32, C.POINTER(C.c_int64)]
     L.lbm_server_tick.argtypes = [C.c_void_p, C.POINTER(C.c_int32)]
+    L.lbm_server_poll.argtypes = [C.c_void_p, C.POINTER(C.c_int32)]
     L.lbm_server_status.argtypes = [C.c_void_p, C.c_int64, C.POINTER(C.c_int32), _D]
     L.lbm_server_result.argtypes = [C.c_void_p, C.c_int64, _D, _D, _D]
     L.lbm_server_counts.argtypes = [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
@@ -211,7 +213,8 @@ def structs_from_config(cfg, stream=None, use_graphs=True, series_capacity=0, de
     bc.sine_t0, bc.sine_t1 = cfg.sine_t0, cfg.sine_t1
     bc.spot_half_width, bc.c_w_base, bc.c_w_top = cfg.spot_half_width, cfg.c_w_base, cfg.c_w_top
     op = lbm_opts_t()
-    op.precision = {"fp64": LBM_FP64, "fp32": LBM_FP32, "fp16": LBM_FP16, "fp32_dfsrc": LBM_FP32_DFSRC}[cfg.precision]
+    op.precision = {"fp64": LBM_FP64, "fp32": LBM_FP32, "fp16": LBM_FP16, "fp32_dfsrc": LBM_FP32_DFSRC,
+                    "fp64_fma": LBM_FP64_FMA}[cfg.precision]
     op.use_graphs = 1 if use_graphs else 0
     op.stream = stream
     op.rho_shift = cfg.rho_shift
@@ -432,6 +435,12 @@ class Batch:
     def sync(self):
         self._check(load().lbm_batch_sync(self._b), "lbm_batch_sync")
 
+    def done(self) -> bool:
+        """Non-blocking: has all queued work of the batch finished?"""
+        d = C.c_int32()
+        self._check(load().lbm_batch_query(self._b, C.byref(d)), "lbm_batch_query")
+        return bool(d.value)
+
     def close(self):
         if getattr(self, "_b", None):
             load().lbm_batch_destroy(self._b)
@@ -477,8 +486,16 @@ class Server:
         return int(rid.value)
 
     def tick(self) -> int:
+        """Advance by one whole chunk (waits for it); returns requests finished."""
         n = C.c_int32()
         self._check(load().lbm_server_tick(self._s, C.byref(n)), "lbm_server_tick")
+        return int(n.value)
+
+    def poll(self) -> int:
+        """Non-blocking tick: retire a finished chunk, admit arrivals, launch
+        the next chunk; returns requests finished."""
+        n = C.c_int32()
+        self._check(load().lbm_server_poll(self._s, C.byref(n)), "lbm_server_poll")
         return int(n.value)
 
     def status(self, rid: int):

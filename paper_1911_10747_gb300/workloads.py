@@ -97,6 +97,7 @@ class RunConfig:
     seed: int = 1
     precision: str = "fp64"      # "fp64", "fp32" (shifted populations), "fp16" (storage probe) or
                                  # "fp32_dfsrc" (FP32 with the Eq. 24 source in double-float arithmetic)
+                                 # or "fp64_fma" (FP64 with FMA contraction)
     rho_shift: float = 0.0       # shifted-population reference density; 0 => rho_mean
 
     def replace(self, **kw) -> "RunConfig":
