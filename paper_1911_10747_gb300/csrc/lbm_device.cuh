@@ -672,13 +672,27 @@ __global__ void k_init_rho(const DevParams p, typename P::real *__restrict__ rho
     rho[k] = (typename P::real)(base * (1.0 + p.init_noise * (2.0 * U - 1.0)));
 }
 
+// Sum of the initial densities in a fixed order: block b of nblk sums the
+// contiguous sites [b chunk, (b + 1) chunk) into out[1 + b]; then one block
+// sums out[1 .. nblk] into out[0].  The order depends only on the domain
+// size, so the mean is the same on every call; the blocks spread over the
+// device instead of one block reading the whole field.
 template <class P, int NT>
-__global__ void __launch_bounds__(NT) k_sum_rho(const DevParams p, const typename P::real *__restrict__ rho,
-                                                double *__restrict__ out) {
+__global__ void __launch_bounds__(NT) k_sum_rho_part(const DevParams p, const typename P::real *__restrict__ rho,
+                                                     double *__restrict__ out, long long chunk) {
     __shared__ double sh[2][NT / 32];
-    const size_t nfl = (size_t)p.nx * p.nf;
+    const long long nfl = (long long)p.nx * p.nf;
+    const long long k0 = (long long)blockIdx.x * chunk, k1 = k0 + chunk < nfl ? k0 + chunk : nfl;
     double s = 0.0, z = 0.0;
-    for (size_t k = threadIdx.x; k < nfl; k += NT) s += (double)rho[k];
+    for (long long k = k0 + threadIdx.x; k < k1; k += NT) s += (double)rho[k];
+    block_sum2<NT>(s, z, sh);
+    if (threadIdx.x == 0) out[1 + blockIdx.x] = s;
+}
+template <int NT>
+__global__ void __launch_bounds__(NT) k_sum_rho_final(double *__restrict__ out, int nblk) {
+    __shared__ double sh[2][NT / 32];
+    double s = 0.0, z = 0.0;
+    for (int b = threadIdx.x; b < nblk; b += NT) s += out[1 + b];
     block_sum2<NT>(s, z, sh);
     if (threadIdx.x == 0) out[0] = s;
 }
@@ -783,7 +797,15 @@ cudaError_t launch_init(const DevParams &p, const StepBuffers &b, int phase, cud
     const size_t nfl = (size_t)p.nx * p.nf, ntl = (size_t)p.nx * p.nt;
     if (phase == 0) {
         k_init_rho<P><<<(unsigned)((nfl + 255) / 256), 256, 0, s>>>(p, (R *)b.rho);
-        k_sum_rho<P, 1024><<<1, 1024, 0, s>>>(p, (const R *)b.rho, b.scratch);
+        // partial sums in scratch[1 ..] (the scratch holds 1024 doubles)
+        long long chunk = 256 * 16;
+        long long nblk = ((long long)nfl + chunk - 1) / chunk;
+        if (nblk > 1023) {
+            chunk = ((long long)nfl + 1022) / 1023;
+            nblk = ((long long)nfl + chunk - 1) / chunk;
+        }
+        k_sum_rho_part<P, 256><<<(unsigned)nblk, 256, 0, s>>>(p, (const R *)b.rho, b.scratch, chunk);
+        k_sum_rho_final<1024><<<1, 1024, 0, s>>>(b.scratch, (int)nblk);
     } else {
         const size_t n = nfl > ntl ? nfl : ntl;
         k_init_state<P><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p, (const R *)b.rho, (typename P::fst *)b.f_out,

@@ -5,7 +5,8 @@
 // one chunk through a concurrent batch graph, and retires the runs that
 // reached their step count (their diagnostics, and optionally rho and T, are
 // kept on the host and their device memory is freed for the next
-// admissions).  Requests that arrive while others run join at the next tick.
+// admissions).  lbm_server_poll does the same without waiting: requests that
+// arrive while a chunk runs are admitted at once and join at the next chunk.
 #include <algorithm>
 #include <chrono>
 #include <cstring>
@@ -52,6 +53,9 @@ struct lbm_server_s {
     std::vector<int64_t> active;
     lbm_batch batch = nullptr;
     bool dirty = true;
+    bool inflight = false;   // a chunk of inflight_k steps is queued on the batch
+    int64_t inflight_k = 0;
+    std::vector<int64_t> inflight_ids;  // the runs in that chunk (later admissions are not)
     int64_t next_id = 1;
     std::chrono::steady_clock::time_point t0;
     std::string msg;
@@ -93,6 +97,7 @@ int lbm_server_create(uint64_t hbm_budget_bytes, int32_t max_active, int32_t chu
 
 int lbm_server_destroy(lbm_server s) {
     if (!s) return LBM_OK;
+    if (s->batch && s->inflight) lbm_batch_sync(s->batch);
     if (s->batch) lbm_batch_destroy(s->batch);
     for (auto &kv : s->reqs)
         if (kv.second->h) lbm_destroy(kv.second->h);
@@ -126,10 +131,8 @@ int lbm_server_submit(lbm_server s, const lbm_domain_t *domain, const lbm_heater
     return LBM_OK;
 }
 
-int lbm_server_tick(lbm_server s, int32_t *finished) {
-    if (!s) return LBM_E_INVAL;
-    int nfin = 0;
-    // admission: arrival order, while slots and memory allow
+// Admission: arrival order, while slots and memory allow.
+static void admit(lbm_server_s *s, int &nfin) {
     while (!s->queue.empty() && (int)s->active.size() < s->max_active) {
         Request &r = *s->reqs[s->queue.front()];
         if (s->used + r.bytes > s->budget) break;
@@ -149,10 +152,11 @@ int lbm_server_tick(lbm_server s, int32_t *finished) {
         s->active.push_back(r.id);
         s->dirty = true;
     }
-    if (s->active.empty()) {
-        if (finished) *finished = nfin;
-        return LBM_OK;
-    }
+}
+
+// Queue the next chunk over every active run (no wait).
+static int launch_chunk(lbm_server_s *s) {
+    if (s->inflight || s->active.empty()) return LBM_OK;
     if (s->dirty) {
         if (s->batch) lbm_batch_destroy(s->batch);
         s->batch = nullptr;
@@ -165,11 +169,34 @@ int lbm_server_tick(lbm_server s, int32_t *finished) {
     int64_t k = s->chunk;
     for (int64_t id : s->active) k = std::min(k, s->reqs[id]->steps - s->reqs[id]->done);
     int rc = lbm_batch_step(s->batch, k);
-    if (rc == LBM_OK) rc = lbm_batch_sync(s->batch);
+    if (rc != LBM_OK) return sfail(s, rc, lbm_batch_last_error(s->batch));
+    s->inflight = true;
+    s->inflight_k = k;
+    s->inflight_ids = s->active;
+    return LBM_OK;
+}
+
+// Finish the chunk in flight (waiting for it, or only if it is done) and
+// retire the runs that reached their step count or faulted.
+static int complete_chunk(lbm_server_s *s, bool wait, int &nfin) {
+    if (!s->inflight) return LBM_OK;
+    if (!wait) {
+        int32_t done = 0;
+        int rc = lbm_batch_query(s->batch, &done);
+        if (rc != LBM_OK) return sfail(s, rc, lbm_batch_last_error(s->batch));
+        if (!done) return LBM_OK;
+    }
+    int rc = lbm_batch_sync(s->batch);
     if (rc != LBM_OK && rc != LBM_E_NUMERIC) return sfail(s, rc, lbm_batch_last_error(s->batch));
+    const int64_t k = s->inflight_k;
+    s->inflight = false;
     std::vector<int64_t> still;
     for (int64_t id : s->active) {
         Request &r = *s->reqs[id];
+        if (std::find(s->inflight_ids.begin(), s->inflight_ids.end(), id) == s->inflight_ids.end()) {
+            still.push_back(id);  // admitted after the chunk was launched
+            continue;
+        }
         r.done += k;
         int src = lbm_sync(r.h);
         if (src != LBM_OK) {  // a faulted run is retired alone; the others go on
@@ -199,6 +226,26 @@ int lbm_server_tick(lbm_server s, int32_t *finished) {
         nfin++;
     }
     s->active.swap(still);
+    return LBM_OK;
+}
+
+int lbm_server_tick(lbm_server s, int32_t *finished) {
+    if (!s) return LBM_E_INVAL;
+    int nfin = 0, rc;
+    if ((rc = complete_chunk(s, true, nfin)) != LBM_OK) return rc;
+    admit(s, nfin);
+    if ((rc = launch_chunk(s)) != LBM_OK) return rc;
+    if ((rc = complete_chunk(s, true, nfin)) != LBM_OK) return rc;
+    if (finished) *finished = nfin;
+    return LBM_OK;
+}
+
+int lbm_server_poll(lbm_server s, int32_t *finished) {
+    if (!s) return LBM_E_INVAL;
+    int nfin = 0, rc;
+    if ((rc = complete_chunk(s, false, nfin)) != LBM_OK) return rc;
+    admit(s, nfin);
+    if ((rc = launch_chunk(s)) != LBM_OK) return rc;
     if (finished) *finished = nfin;
     return LBM_OK;
 }

@@ -1,7 +1,10 @@
 """Batches of runs: every run's result is the same alone and inside a mixed
-batch (different sizes, precisions and bottom modes), bitwise."""
+batch (different sizes, precisions and bottom modes), bitwise; the FP64
+members, a sweep-drawn one among them, match the oracle."""
 import numpy as np
 import pytest
+
+from oracle import oracle as O
 
 from paper_1911_10747_gb300 import lbm
 from paper_1911_10747_gb300 import workloads as W
@@ -24,6 +27,7 @@ def mixed_configs():
         base.replace(precision="fp32", bc_mode="noise", spot_x=(), c_w_spot=(), seed=9),
         W.sweep(3, seed=11)[0].replace(nf=96, liquid_rows=32),
         base.replace(precision="fp16", top_mode="outflow"),
+        W.sweep(3, seed=12)[1].replace(nf=90, liquid_rows=30, precision="fp64"),
     ]
 
 
@@ -50,6 +54,13 @@ def test_results_alone_and_in_a_batch_are_identical():
         got = r.fields(("rho", "ux", "uy", "T", "f"))
         for k in got:
             assert np.array_equal(got[k], alone[i][k]), (i, k)
+        if cfgs[i].precision == "fp64":
+            o = O.OracleRun(cfgs[i])
+            o.step(21)
+            umax = max(np.abs(o.ux).max(), np.abs(o.uy).max())
+            assert np.max(np.abs(got["rho"] - o.rho) / np.abs(o.rho)) <= 1e-12, i
+            assert np.max(np.abs(got["T"] - o.T) / np.abs(o.T)) <= 1e-12, i
+            assert np.max(np.abs(got["ux"] - o.ux)) <= 1e-12 * umax, i
     batch.close()
 
 

@@ -1,8 +1,13 @@
 """Continuous batching: requests that arrive while others run are admitted
 as slots and memory free up, the budget and slot limit hold at every tick,
-and each request's result is the same alone and in the mix (bitwise)."""
+each request's result is the same alone and in the mix (bitwise), and the
+FP64 requests' results match the oracle."""
+import time
+
 import numpy as np
 import pytest
+
+from oracle import oracle as O
 
 from paper_1911_10747_gb300 import lbm
 from paper_1911_10747_gb300 import workloads as W
@@ -65,6 +70,48 @@ def test_requests_give_the_same_results_alone_and_in_the_mix():
         assert np.array_equal(rho, r0) and np.array_equal(T, t0), i
         st, (ts, t1, t2) = srv.status(i)
         assert ts <= t1 <= t2
+        if c.precision == "fp64":
+            # the served FP64 run against the oracle (1e-12 per site; the two
+            # sides sum the initial densities in different orders)
+            o = O.OracleRun(c)
+            o.step(n)
+            assert np.max(np.abs(rho - o.rho) / np.abs(o.rho)) <= 1e-12, i
+            assert np.max(np.abs(T - o.T) / np.abs(o.T)) <= 1e-12, i
+            od = o.diagnostics()
+            want = [od["q_bottom"], od["q_top"], od["vapour_fraction"], od["mass"]]
+            np.testing.assert_allclose(diag, want, rtol=1e-11, atol=1e-16)
+    srv.close()
+
+
+def test_poll_admits_arrivals_while_a_chunk_runs():
+    """lbm_server_poll does not wait for the chunk in flight: a request that
+    arrives during a long chunk is admitted (its run created on its own
+    stream) by the next poll, which returns long before the chunk ends; the
+    request joins at the next chunk, and every result equals the run alone."""
+    big = W.small_parity(precision="fp64").replace(nx=512, nf=512, ns=8, liquid_rows=170,
+                                                    spot_x=W.scaled_spots(512), rho_mean=2.4)
+    small = W.small_parity(precision="fp32").replace(rho_mean=2.42)
+    srv = lbm.Server(hbm_budget_bytes=10**10, max_active=4, chunk_steps=400)
+    a = srv.submit(big, 800, keep_fields=True)
+    srv.poll()                                    # admits a, launches its first chunk
+    assert srv.status(a)[0] == 1
+    b = srv.submit(small, 30, keep_fields=True)
+    t0 = time.perf_counter()
+    srv.poll()                                    # admits b while a's chunk runs
+    dt = time.perf_counter() - t0
+    q, active, _ = srv.counts()
+    assert srv.status(b)[0] == 1 and active == 2 and q == 0
+    print("poll during a chunk took", dt, "s")
+    assert dt < 0.2, dt
+    deadline = time.perf_counter() + 120
+    while any(srv.status(i)[0] < 2 for i in (a, b)):
+        assert time.perf_counter() < deadline
+        if srv.poll() == 0:
+            time.sleep(0.001)
+    for i, (c, n) in ((a, (big, 800)), (b, (small, 30))):
+        diag, rho, T = srv.result(i, fields=True)
+        d0, r0, t0_ = alone(*(c, n))
+        assert np.array_equal(diag, d0) and np.array_equal(rho, r0) and np.array_equal(T, t0_), i
     srv.close()
 
 
