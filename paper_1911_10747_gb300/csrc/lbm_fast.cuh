@@ -442,12 +442,17 @@ k_flow_fast(const FParams p, const typename P::fst *__restrict__ fin, typename P
 // sites are already loading into registers.  Tiles that touch no boundary
 // use flow_site's interior form.  WIDE (compile time) promises nx >= TX + 1
 // and, if periodic in y, nf >= TY + 2, so that index wraps are a compare.
-template <class P, int BX, int BY, int RY, int MINB, bool WIDE>
-__global__ void __launch_bounds__(BX *BY, MINB)
-k_flow_pers(const FParams p, int tiles_x, int ntiles, const typename P::fst *__restrict__ fin, typename P::fst *__restrict__ fout,
-            const typename P::tst *__restrict__ Tin, float *__restrict__ rho_o, float *__restrict__ ux_o,
-            float *__restrict__ uy_o, const double *__restrict__ cw, double *__restrict__ part,
-            unsigned *__restrict__ err, const long long *__restrict__ stepp) {
+// The body of the persistent flow kernel over tiles first, first + step, ...
+// (below end) of a run.  PER_TILE: each tile writes its own mass and
+// vapour-count partials (part[2 tile], part[2 tile + 1]), so the run's sums
+// do not depend on which block did which tile; otherwise the block writes
+// one pair at part[2 part_slot].
+template <class P, int BX, int BY, int RY, bool WIDE, bool PER_TILE>
+__device__ __forceinline__ void
+flow_pers_body(const FParams &p, int tiles_x, int end, int first, int step, const typename P::fst *__restrict__ fin,
+               typename P::fst *__restrict__ fout, const typename P::tst *__restrict__ Tin, float *__restrict__ rho_o,
+               float *__restrict__ ux_o, float *__restrict__ uy_o, const double *__restrict__ cw,
+               double *__restrict__ part, unsigned *__restrict__ err, const long long *__restrict__ stepp, int part_slot) {
     using S = typename P::fst;
     constexpr int TX = BX, TY = BY * RY, SW = TX + 2, SH = TY + 2, NT = BX * BY;
     __shared__ float s_psi[SH * SW];
@@ -478,8 +483,8 @@ k_flow_pers(const FParams p, int tiles_x, int ntiles, const typename P::fst *__r
     // every wrap below is one compare instead of an integer modulo
     auto wx = [&](int v) { return WIDE ? wrap1(v, nx) : wrapi(v, nx); };
     auto wy = [&](int v) { return WIDE ? wrap1(v, nf) : wrapi(v, nf); };
-    // tile coordinates advance by gridDim.x tiles per iteration without a division
-    const int gdx = (int)gridDim.x % tiles_x, gdy = (int)gridDim.x / tiles_x;
+    // tile coordinates advance by `step` tiles per iteration without a division
+    const int gdx = step % tiles_x, gdy = step / tiles_x;
     // populations (as stored: converted only when the tile starts, so that
     // no instruction waits on the loads before then) and temperature of the
     // next tile, loaded during this tile
@@ -538,9 +543,9 @@ k_flow_pers(const FParams p, int tiles_x, int ntiles, const typename P::fst *__r
         }
     };
     float mass = 0.0f, nvap = 0.0f;
-    int cxt = (int)blockIdx.x % tiles_x, cyt = (int)blockIdx.x / tiles_x;  // current tile
-    if ((int)blockIdx.x < ntiles) { fetch_ring(cxt, cyt); fetch_main(cxt, cyt); }
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    int cxt = first % tiles_x, cyt = first / tiles_x;  // current tile
+    if (first < end) { fetch_ring(cxt, cyt); fetch_main(cxt, cyt); }
+    for (int tile = first; tile < end; tile += step) {
     const int x0 = cxt * TX, y0 = cyt * TY;
     int nxt = cxt + gdx, nyt = cyt + gdy;  // next tile of this block
     if (nxt >= tiles_x) { nxt -= tiles_x; nyt += 1; }
@@ -550,7 +555,7 @@ k_flow_pers(const FParams p, int tiles_x, int ntiles, const typename P::fst *__r
         for (int i = 0; i < 9; i++) g[r][i] = to_f(pg[r][i]);
         gT[r] = pTv[r];
     }
-    const bool more = tile + (int)gridDim.x < ntiles;
+    const bool more = tile + step < end;
     // the next tile's own sites load from here on, under this tile's psi and
     // collision work; its ring sites once this tile's ring psi is done
     if (more) fetch_main(nxt, nyt);
@@ -614,27 +619,60 @@ k_flow_pers(const FParams p, int tiles_x, int ntiles, const typename P::fst *__r
     };
     if (x0 == 0 || x0 + TX >= nx || y0 == 0 || y0 + TY >= nf) collide(std::true_type{});
     else collide(std::false_type{});
+    if constexpr (PER_TILE) {
+        #pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            mass += __shfl_down_sync(0xffffffffu, mass, o);
+            nvap += __shfl_down_sync(0xffffffffu, nvap, o);
+        }
+        if ((tid & 31) == 0) { s_red[0][tid >> 5] = mass; s_red[1][tid >> 5] = nvap; }
+        mass = 0.0f;
+        nvap = 0.0f;
+    }
     __syncthreads();  // s_psi is rewritten by the next tile
+    if constexpr (PER_TILE) {
+        // (s_red is rewritten only after the next tile's psi barrier)
+        if (tid == 0) {
+            double m = 0.0, v = 0.0;
+            #pragma unroll
+            for (int w = 0; w < NT / 32; w++) { m += (double)s_red[0][w]; v += (double)s_red[1][w]; }
+            part[2 * tile] = m;
+            part[2 * tile + 1] = v;
+        }
+    }
     cxt = nxt; cyt = nyt;
     }
-    // per-block mass and vapour count: FP32 inside the block, FP64 across blocks
-    #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        mass += __shfl_down_sync(0xffffffffu, mass, o);
-        nvap += __shfl_down_sync(0xffffffffu, nvap, o);
-    }
-    if ((tid & 31) == 0) { s_red[0][tid >> 5] = mass; s_red[1][tid >> 5] = nvap; }
-    __syncthreads();
-    if (tid == 0) {
-        double m = 0.0, v = 0.0;
+    if constexpr (!PER_TILE) {
+        // per-block mass and vapour count: FP32 inside the block, FP64 across blocks
         #pragma unroll
-        for (int w = 0; w < NT / 32; w++) { m += (double)s_red[0][w]; v += (double)s_red[1][w]; }
-        const int bi = blockIdx.y * gridDim.x + blockIdx.x;
-        part[2 * bi] = m;
-        part[2 * bi + 1] = v;
+        for (int o = 16; o > 0; o >>= 1) {
+            mass += __shfl_down_sync(0xffffffffu, mass, o);
+            nvap += __shfl_down_sync(0xffffffffu, nvap, o);
+        }
+        if ((tid & 31) == 0) { s_red[0][tid >> 5] = mass; s_red[1][tid >> 5] = nvap; }
+        __syncthreads();
+        if (tid == 0) {
+            double m = 0.0, v = 0.0;
+            #pragma unroll
+            for (int w = 0; w < NT / 32; w++) { m += (double)s_red[0][w]; v += (double)s_red[1][w]; }
+            part[2 * part_slot] = m;
+            part[2 * part_slot + 1] = v;
+        }
     }
     if (errbits) atomicOr(err, errbits);
 }
+
+template <class P, int BX, int BY, int RY, int MINB, bool WIDE>
+__global__ void __launch_bounds__(BX *BY, MINB)
+k_flow_pers(const __grid_constant__ FParams p, int tiles_x, int ntiles, const typename P::fst *__restrict__ fin,
+            typename P::fst *__restrict__ fout, const typename P::tst *__restrict__ Tin, float *__restrict__ rho_o,
+            float *__restrict__ ux_o, float *__restrict__ uy_o, const double *__restrict__ cw,
+            double *__restrict__ part, unsigned *__restrict__ err, const long long *__restrict__ stepp) {
+    flow_pers_body<P, BX, BY, RY, WIDE, false>(p, tiles_x, ntiles, (int)blockIdx.x, (int)gridDim.x, fin, fout, Tin,
+                                               rho_o, ux_o, uy_o, cw, part, err, stepp, (int)blockIdx.x);
+}
+
+
 
 // ============================================================================
 // Heat kernel, FP32.  Output tile TX x TY, 4-cell halo.  Shared arrays per
@@ -1249,11 +1287,15 @@ int HeatRowsShape<P, BW, BY, R, MINB, DF>::grid_blocks = 152;
 // read only by halo cells.
 // ============================================================================
 
-template <class P, int BY, int R, int MINB, bool WIDE>
-__global__ void __launch_bounds__(32 * BY, MINB)
-k_heat_pair(const FParams p, int tiles_x, int ntiles, const typename P::tst *__restrict__ Tin,
-            typename P::tst *__restrict__ Tout, const float *__restrict__ rho_i, const float *__restrict__ ux_i,
-            const float *__restrict__ uy_i, const long long *__restrict__ stepp, unsigned *__restrict__ err) {
+// The body of the paired heat kernel over tiles first, first + step, ...
+// (below end) of a run: a persistent block of a single-run launch, or a
+// block's contiguous share of a run in a multi-run launch; p may live in the
+// constant bank or in shared memory.
+template <class P, int BY, int R, bool WIDE>
+__device__ __forceinline__ void
+heat_pair_body(const FParams &p, int tiles_x, int end, int first, int step, const typename P::tst *__restrict__ Tin,
+               typename P::tst *__restrict__ Tout, const float *__restrict__ rho_i, const float *__restrict__ ux_i,
+               const float *__restrict__ uy_i, const long long *__restrict__ stepp, unsigned *__restrict__ err) {
     constexpr int HW = 32, BW = 2 * HW, NSL = HW, H = 4, SH = R * BY, TXO = BW - 2 * H, TYO = SH - 2 * H;
     __shared__ float2 sT[2][SH][NSL];
     // 1/lambda, u_x, u_y of the tile for the coefficient pass; afterwards the
@@ -1273,7 +1315,7 @@ k_heat_pair(const FParams p, int tiles_x, int ntiles, const typename P::tst *__r
     float2 Tn[R], Tc[R], acc[R], kk[R][8], nks[R], c0[R], c2[R];
     int pk = 0, pxa = 0, pxb = 0;  // kinds of the staged rows (3 bits per row) and their columns
 
-    const int gdx = (int)gridDim.x % tiles_x, gdy = (int)gridDim.x / tiles_x;
+    const int gdx = step % tiles_x, gdy = step / tiles_x;
     auto interior = [&](int tyt) {
         const int rlo = tyt * TYO - H;
         return !py && rlo >= ns && rlo + SH <= nt;
@@ -1317,12 +1359,12 @@ k_heat_pair(const FParams p, int tiles_x, int ntiles, const typename P::tst *__r
         else fetch_tile(txt, tyt, std::false_type{});
     };
     const float w1 = 1.0f / 9.0f, w2 = 1.0f / 36.0f;
-    int cxt = (int)blockIdx.x % tiles_x, cyt = (int)blockIdx.x / tiles_x;
-    if ((int)blockIdx.x < ntiles) fetch(cxt, cyt);
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    int cxt = first % tiles_x, cyt = first / tiles_x;
+    if (first < end) fetch(cxt, cyt);
+    for (int tile = first; tile < end; tile += step) {
         int nxt = cxt + gdx, nyt = cyt + gdy;
         if (nxt >= tiles_x) { nxt -= tiles_x; nyt += 1; }
-        const bool more = tile + (int)gridDim.x < ntiles;
+        const bool more = tile + step < end;
         // neighbour rows, clamped into the tile (edge cells compute values
         // nobody reads from them)
         const int yb = y0 > 0 ? y0 - 1 : 0, yt = y0 + R < SH ? y0 + R : SH - 1;
@@ -1536,6 +1578,16 @@ k_heat_pair(const FParams p, int tiles_x, int ntiles, const typename P::tst *__r
     if (errbits) atomicOr(err, errbits);
 }
 
+
+template <class P, int BY, int R, int MINB, bool WIDE>
+__global__ void __launch_bounds__(32 * BY, MINB)
+k_heat_pair(const __grid_constant__ FParams p, int tiles_x, int ntiles, const typename P::tst *__restrict__ Tin,
+            typename P::tst *__restrict__ Tout, const float *__restrict__ rho_i, const float *__restrict__ ux_i,
+            const float *__restrict__ uy_i, const long long *__restrict__ stepp, unsigned *__restrict__ err) {
+    heat_pair_body<P, BY, R, WIDE>(p, tiles_x, ntiles, (int)blockIdx.x, (int)gridDim.x, Tin, Tout, rho_i, ux_i, uy_i,
+                                   stepp, err);
+}
+
 template <class P, int BY, int R, int MINB>
 struct HeatPairShape {
     static int grid_blocks;
@@ -1571,10 +1623,10 @@ namespace lbmgb {
 // Diagnostics kernel, FP32 path, single pass: every global load is issued
 // before the first reduction, then one block-wide reduction of four sums.
 template <class P, int NT>
-__global__ void __launch_bounds__(NT)
-k_diag_flat(const FParams p, const float *__restrict__ T, const float *__restrict__ rho,
-            const double *__restrict__ part, int nblk, double *__restrict__ q_top, double *__restrict__ series,
-            int cap, double *__restrict__ last, long long *__restrict__ stepp, double inv_nx, double inv_nfl) {
+__device__ __forceinline__ void
+diag_flat_body(const FParams &p, const float *__restrict__ T, const float *__restrict__ rho,
+               const double *__restrict__ part, int nblk, double *__restrict__ q_top, double *__restrict__ series,
+               int cap, double *__restrict__ last, long long *__restrict__ stepp, double inv_nx, double inv_nfl) {
     __shared__ double sh[4][NT / 32];
     const int nx = p.nx, ns = p.ns, t = threadIdx.x;
     const bool model_a = (p.flags & FLAG_MODEL_A) != 0;  // no heater: wall flux for both
@@ -1629,6 +1681,14 @@ k_diag_flat(const FParams p, const float *__restrict__ T, const float *__restric
             *stepp = n + 1;
         }
     }
+}
+
+template <class P, int NT>
+__global__ void __launch_bounds__(NT)
+k_diag_flat(const __grid_constant__ FParams p, const float *__restrict__ T, const float *__restrict__ rho,
+            const double *__restrict__ part, int nblk, double *__restrict__ q_top, double *__restrict__ series,
+            int cap, double *__restrict__ last, long long *__restrict__ stepp, double inv_nx, double inv_nfl) {
+    diag_flat_body<P, NT>(p, T, rho, part, nblk, q_top, series, cap, last, stepp, inv_nx, inv_nfl);
 }
 
 template <class P, int NT>

@@ -4,6 +4,7 @@
 #include "lbm_fast.cuh"
 #include "lbm_tma.cuh"
 #include "lbm_heatwave.cuh"
+#include "lbm_multi.cuh"
 
 namespace lbmgb {
 namespace {
@@ -30,39 +31,45 @@ cudaError_t diag(const DevParams &p, const StepBuffers &b, int nblk, cudaStream_
 #define HEATW(P, CL, WPB, MB, RS) \
     {"heatwave_c" #CL "_w" #WPB "_b" #MB "_r" #RS, HeatWaveShape<P, CL, WPB, MB, RS>::launch, \
      HeatWaveShape<P, CL, WPB, MB, RS>::prepare}
+#define FLOWM(P) {"flowmulti_32x8x2", MultiKernels<P>::flow, MultiKernels<P>::flow_blocks, MultiKernels<P>::prepare}
+#define HEATM(P) {"heatmulti_64x12x4", MultiKernels<P>::heat, MultiKernels<P>::prepare}
+#define MULTI(P) sizeof(MultiRun), fill_multi, multi_flow_tiles, multi_heat_tiles, MultiKernels<P>::launch
+#define NOMULTI 0, nullptr, nullptr, nullptr, nullptr
 #define HEATV(P, TX, TY, BX, BY) \
     {"heat_" #TX "x" #TY "_t" #BX "x" #BY, HeatFastShape<P, TX, TY, BX, BY>::launch, HeatFastShape<P, TX, TY, BX, BY>::prepare}
 
 const FlowVariant flows32[] = {
     FLOWT(PolicyF32, 4, 2, 3), FLOWP(PolicyF32, 64, 4, 2, 2), FLOWP(PolicyF32, 32, 8, 2, 2),
     FLOWP(PolicyF32, 32, 8, 1, 3), FLOWV(PolicyF32, 32, 8, 2, 3), FLOWV(PolicyF32, 64, 4, 2, 3),
+    FLOWM(PolicyF32),
 };
 const HeatVariant heats32[] = {
     HEATS(PolicyF32, 64, 6, 5, 1), HEATS(PolicyF32, 64, 8, 4, 1), HEATS(PolicyF32, 64, 10, 3, 1),
     HEATS(PolicyF32, 64, 6, 6, 1),
     HEATS(PolicyF32, 32, 8, 4, 2),
     HEATP(PolicyF32, 12, 4, 1), HEATP(PolicyF32, 8, 4, 1),
-    HEATW(PolicyF32, 2, 2, 4, 8),
+    HEATW(PolicyF32, 2, 2, 4, 8), HEATM(PolicyF32),
     HEATV(PolicyF32, 32, 16, 32, 8), HEATV(PolicyF32, 64, 32, 32, 16),
 };
 // the Eq. 24 source in double-float arithmetic (precision LBM_FP32_DFSRC)
 const HeatVariant heats32df[] = {HEATSD(PolicyF32, 64, 8, 4, 1), HEATSD(PolicyF32, 64, 6, 5, 1)};
-const FlowVariant flows16[] = {FLOWP(PolicyF16, 32, 8, 2, 2), FLOWV(PolicyF16, 32, 8, 2, 3)};
+const FlowVariant flows16[] = {FLOWP(PolicyF16, 32, 8, 2, 2), FLOWV(PolicyF16, 32, 8, 2, 3), FLOWM(PolicyF16)};
 const HeatVariant heats16[] = {HEATS(PolicyF16, 64, 10, 3, 1), HEATS(PolicyF16, 64, 8, 4, 1), HEATP(PolicyF16, 12, 4, 1),
-                               HEATV(PolicyF16, 32, 32, 32, 16)};
+                               HEATV(PolicyF16, 32, 32, 32, 16), HEATM(PolicyF16)};
 
 const KernelSet ks32 = {"fp32", sizeof(float), sizeof(float), sizeof(float),
                         (int)(sizeof(flows32) / sizeof(flows32[0])), flows32,
                         (int)(sizeof(heats32) / sizeof(heats32[0])), heats32, diag<PolicyF32>,
-                        launch_init<PolicyF32>, launch_import<PolicyF32>, launch_export<PolicyF32>};
+                        launch_init<PolicyF32>, launch_import<PolicyF32>, launch_export<PolicyF32>, MULTI(PolicyF32)};
+// (the multi-run flow variant, listed last, needs a run descriptor this set does not keep)
 const KernelSet ks32df = {"fp32dfsrc", sizeof(float), sizeof(float), sizeof(float),
-                          (int)(sizeof(flows32) / sizeof(flows32[0])), flows32,
+                          (int)(sizeof(flows32) / sizeof(flows32[0])) - 1, flows32,
                           (int)(sizeof(heats32df) / sizeof(heats32df[0])), heats32df, diag<PolicyF32>,
-                          launch_init<PolicyF32>, launch_import<PolicyF32>, launch_export<PolicyF32>};
+                          launch_init<PolicyF32>, launch_import<PolicyF32>, launch_export<PolicyF32>, NOMULTI};
 const KernelSet ks16 = {"fp16", sizeof(__half), sizeof(float), sizeof(float),
                         (int)(sizeof(flows16) / sizeof(flows16[0])), flows16,
                         (int)(sizeof(heats16) / sizeof(heats16[0])), heats16, diag<PolicyF16>,
-                        launch_init<PolicyF16>, launch_import<PolicyF16>, launch_export<PolicyF16>};
+                        launch_init<PolicyF16>, launch_import<PolicyF16>, launch_export<PolicyF16>, MULTI(PolicyF16)};
 }  // namespace
 const KernelSet *kernels_fp32() { return &ks32; }
 const KernelSet *kernels_fp16() { return &ks16; }

@@ -18,7 +18,9 @@ enum { BCM_SPOTS = 0, BCM_NOISE = 1, BCM_SINE = 2 };
 // when those waits also run out, and could land in shared memory that a later
 // block owns: the step's results are invalid either way, and the host reports
 // LBM_E_TIMEOUT.
-enum { ERRW_PSI = 1, ERRW_NONFINITE_RHO = 2, ERRW_NONFINITE_T = 4, ERRW_TIMEOUT = 8 };
+// ERRW_DESC: a multi-run kernel block found a descriptor it cannot trust
+// (not filled, or its tile outside its run) and skipped its tile.
+enum { ERRW_PSI = 1, ERRW_NONFINITE_RHO = 2, ERRW_NONFINITE_T = 4, ERRW_TIMEOUT = 8, ERRW_DESC = 16 };
 enum { TAG_INIT_NOISE = 1, TAG_BOTTOM_NOISE = 2 };
 enum { SERIES_WIDTH = 4 };
 
@@ -64,6 +66,7 @@ struct StepBuffers {
     double *q_top;           // [nx] local interface flux of the last step
     double *last;            // [SERIES_WIDTH] diagnostics of the last step
     double *scratch;         // reduction scratch for init (>= 1024 doubles)
+    const void *mdesc;       // the run's own multi-run descriptor for this parity (kernel sets that have one)
 };
 
 // One launch shape of the flow or heat kernel.  Every variant of a kernel
@@ -98,6 +101,18 @@ struct KernelSet {
     // storage -> float64 device arrays (any pointer may be NULL).
     cudaError_t (*export_fields)(const DevParams &, const StepBuffers &, double *rho, double *ux,
                                  double *uy, double *T, double *f, cudaStream_t);
+    // Multi-run launches (one launch per kernel kind steps many runs over a
+    // work list of (run, tile)); multi_desc_bytes = 0 if the set has none.
+    size_t multi_desc_bytes;
+    // a run's descriptor (host memory `out`) for its buffers of parity 0 / 1,
+    // the parity of its state at phase 0, and its first tiles in the launch
+    void (*multi_fill)(const DevParams &, const StepBuffers &b0, const StepBuffers &b1, int parity, int flow_tile0,
+                       int heat_tile0, void *out);
+    int (*multi_flow_tiles)(const DevParams &);
+    int (*multi_heat_tiles)(const DevParams &);
+    // kind 0 flow, 1 heat, 2 diagnostics over nruns descriptors (device), tiles of that kind in total
+    cudaError_t (*multi_launch)(int kind, const void *desc, int nruns, int tiles, int phase, unsigned *errw,
+                                cudaStream_t);
 };
 
 // Message returned by lbm_last_error(NULL) (thread-local).

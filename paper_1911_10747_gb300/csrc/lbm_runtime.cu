@@ -48,6 +48,7 @@ struct lbm_run {
     cudaEvent_t ev_heat = nullptr, ev_diag = nullptr;    // plain launches
     cudaEvent_t cev_heat = nullptr, cev_diag = nullptr;  // inside stream captures
     double *scratch = nullptr;
+    void *mdesc = nullptr;          // two multi-run descriptors (state parity 0, 1), kernel sets that have them
     double *stage = nullptr;        // float64 staging for read-back / import
     size_t stage_elems = 0;
     unsigned *err = nullptr;
@@ -103,6 +104,7 @@ static StepBuffers buffers(lbm_run *h, int par) {
     b.q_top = h->q_top;
     b.last = h->last;
     b.scratch = h->scratch;
+    b.mdesc = h->mdesc ? static_cast<const char *>(h->mdesc) + par * h->ks->multi_desc_bytes : nullptr;
     return b;
 }
 // Buffers describing the current state as the "output" side (init / import)
@@ -157,7 +159,7 @@ static void free_all(lbm_run *h) {
     for (cudaEvent_t ev : {h->ev_heat, h->ev_diag, h->cev_heat, h->cev_diag})
         if (ev) cudaEventDestroy(ev);
     if (h->dstream) cudaStreamDestroy(h->dstream);
-    dfree(h, h->scratch); dfree(h, h->stage); dfree(h, h->err); dfree(h, h->dstep);
+    dfree(h, h->scratch); dfree(h, h->stage); dfree(h, h->err); dfree(h, h->dstep); dfree(h, h->mdesc);
     for (auto &v : h->ev)
         for (auto &e : v) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
@@ -270,6 +272,8 @@ static int check_err_word(lbm_run *h) {
     CK(h, cudaStreamSynchronize(h->stream));
     if (e & ERRW_TIMEOUT)
         return fail(h, LBM_E_TIMEOUT, "a kernel's wait for its staged data ran out (the step's results are invalid)");
+    if (e & ERRW_DESC)
+        return fail(h, LBM_E_STATE, "a multi-run kernel found a descriptor it could not trust and skipped its tile");
     if (e) {
         std::string m = "numerical fault latched by the kernels:";
         if (e & ERRW_PSI) m += " negative pseudopotential radicand;";
@@ -369,8 +373,10 @@ int lbm_create(const lbm_domain_t *domain, const lbm_heater_t *heater, const lbm
         {(void **)&h->q_top, (size_t)p.nx * sizeof(double)}, {(void **)&h->last, SERIES_WIDTH * sizeof(double)},
         {(void **)&h->scratch, 1024 * sizeof(double)}, {(void **)&h->err, sizeof(unsigned)},
         {(void **)&h->dstep, sizeof(long long)},
+        {&h->mdesc, 2 * h->ks->multi_desc_bytes},
     };
     for (auto &a : allocs) {
+        if (a.bytes == 0) continue;
         e = dalloc(h, a.ptr, a.bytes);
         if (e != cudaSuccess) {
             fail(h, LBM_E_NOMEM, std::string("device allocation of ") + std::to_string(a.bytes) + " bytes failed: " +
@@ -413,6 +419,19 @@ int lbm_create(const lbm_domain_t *domain, const lbm_heater_t *heater, const lbm
     if (!(h->p.rho_mean > 0)) h->p.rho_mean = sum / (double)nfl;
     h->p.rho_shift = (opts->rho_shift > 0) ? opts->rho_shift : h->p.rho_mean;
     if ((e = h->ks->init(h->p, b, 1, h->stream)) != cudaSuccess) { cuda_fail(h, e, "init kernels"); return bad(LBM_E_CUDA); }
+    if (h->mdesc) {
+        // the run's own multi-run descriptors (for the "multi" launch-shape
+        // variants), one per state parity, now that rho_mean is fixed
+        const size_t db = h->ks->multi_desc_bytes;
+        std::vector<char> hd(2 * db);
+        for (int par = 0; par < 2; par++)
+            h->ks->multi_fill(h->p, buffers(h, 0), buffers(h, 1), par, 0, 0, hd.data() + par * db);
+        if ((e = cudaMemcpyAsync(h->mdesc, hd.data(), 2 * db, cudaMemcpyHostToDevice, h->stream)) != cudaSuccess ||
+            (e = cudaStreamSynchronize(h->stream)) != cudaSuccess) {
+            cuda_fail(h, e, "run descriptors");
+            return bad(LBM_E_CUDA);
+        }
+    }
     if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) { cuda_fail(h, e, "init sync"); return bad(LBM_E_CUDA); }
     *out = h;
     return LBM_OK;
@@ -744,11 +763,29 @@ int lbm_kernels_per_step(lbm_handle h) { return h ? 3 : 0; }
 }  // extern "C"
 
 // ---- batches of runs ---------------------------------------------------------
+// Runs of one kernel set that has multi-run kernels are stepped together:
+// per step one flow, one heat and one diagnostics launch over all their
+// tiles.  The other runs of a batch are stepped by their own kernels, one
+// concurrent branch per run.
+struct MultiGroup {
+    const KernelSet *ks = nullptr;
+    std::vector<int> idx;           // positions in the batch's run list
+    void *desc = nullptr;           // device descriptors, in idx order
+    std::vector<char> host;         // their host image
+    int flow_tiles = 0, heat_tiles = 0;
+    cudaStream_t gs = nullptr, gd = nullptr;       // kernel and diagnostics streams
+    cudaEvent_t ev_heat = nullptr, ev_diag = nullptr;    // inside graph captures
+    cudaEvent_t xev_heat = nullptr, xev_diag = nullptr;  // plain launches
+};
+
 struct lbm_batch_s {
     std::vector<lbm_run *> runs;
     std::vector<int> versions;
     std::vector<int> parities;      // each run's buffer parity when the graph was captured
     std::vector<cudaEvent_t> join;
+    std::vector<bool> in_group;     // stepped by a multi-run group
+    std::vector<MultiGroup> groups;
+    unsigned *errw = nullptr;       // error word of the groups' launches (ERRW_DESC)
     cudaEvent_t fork = nullptr;
     cudaStream_t stream = nullptr;
     cudaGraphExec_t graph = nullptr;
@@ -765,18 +802,98 @@ static void batch_free(lbm_batch_s *b) {
     if (b->graph) cudaGraphExecDestroy(b->graph);
     for (auto e : b->join) cudaEventDestroy(e);
     if (b->fork) cudaEventDestroy(b->fork);
+    for (auto &g : b->groups) {
+        if (g.desc) cudaFree(g.desc);
+        for (cudaEvent_t ev : {g.ev_heat, g.ev_diag, g.xev_heat, g.xev_diag})
+            if (ev) cudaEventDestroy(ev);
+        for (cudaStream_t st : {g.gs, g.gd})
+            if (st) cudaStreamDestroy(st);
+    }
+    if (b->errw) cudaFree(b->errw);
     if (b->stream) cudaStreamDestroy(b->stream);
 }
 
+// Descriptors of every group's runs for their current state parities
+// (phase 0 of the next launches), uploaded before any launch that uses them.
+static int batch_fill_groups(lbm_batch_s *b) {
+    // launches queued earlier may still read the descriptors: they all end
+    // up on the batch stream
+    if (!b->groups.empty()) {
+        cudaError_t e = cudaStreamSynchronize(b->stream);
+        if (e != cudaSuccess) return bfail(b, LBM_E_CUDA, std::string("batch sync: ") + cudaGetErrorString(e));
+    }
+    for (auto &g : b->groups) {
+        const size_t db = g.ks->multi_desc_bytes;
+        int f0 = 0, h0 = 0;
+        for (size_t k = 0; k < g.idx.size(); k++) {
+            lbm_run *h = b->runs[g.idx[k]];
+            g.ks->multi_fill(h->p, buffers(h, 0), buffers(h, 1), h->parity, f0, h0, g.host.data() + k * db);
+            f0 += g.ks->multi_flow_tiles(h->p);
+            h0 += g.ks->multi_heat_tiles(h->p);
+        }
+        g.flow_tiles = f0;
+        g.heat_tiles = h0;
+        // ordered on the batch stream and waited for: a plain cudaMemcpy from
+        // pageable memory may return before its data lands, and it is not
+        // ordered with the non-blocking streams the kernels run on
+        cudaError_t e = cudaMemcpyAsync(g.desc, g.host.data(), g.host.size(), cudaMemcpyHostToDevice, b->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+        if (e != cudaSuccess) return bfail(b, LBM_E_CUDA, std::string("batch descriptors: ") + cudaGetErrorString(e));
+    }
+    return LBM_OK;
+}
+
+// One step (phase 0 or 1 of the current descriptors) of every group, ordered
+// after `from` and joined back into it.  As for a single run, the
+// diagnostics run on their own stream under the next step's flow kernel; the
+// heat kernel (and with FP16 storage also the flow kernel) waits for the
+// previous step's diagnostics, which advance the step counters.
+static cudaError_t batch_groups_step(lbm_batch_s *b, int phase, bool first, bool captured, cudaEvent_t fork) {
+    cudaError_t e = cudaSuccess;
+    for (auto &g : b->groups) {
+        cudaEvent_t ev_heat = captured ? g.ev_heat : g.xev_heat, ev_diag = captured ? g.ev_diag : g.xev_diag;
+        const int n = (int)g.idx.size();
+        const bool fp16 = g.ks->f_elem == 2;
+        if (first) {
+            if ((e = cudaStreamWaitEvent(g.gs, fork, 0)) != cudaSuccess) return e;
+            if ((e = cudaStreamWaitEvent(g.gd, fork, 0)) != cudaSuccess) return e;
+        } else if (fp16 && (e = cudaStreamWaitEvent(g.gs, ev_diag, 0)) != cudaSuccess) {
+            return e;
+        }
+        if ((e = g.ks->multi_launch(0, g.desc, n, g.flow_tiles, phase, b->errw, g.gs)) != cudaSuccess) return e;
+        if (!first && !fp16 && (e = cudaStreamWaitEvent(g.gs, ev_diag, 0)) != cudaSuccess) return e;
+        if ((e = g.ks->multi_launch(1, g.desc, n, g.heat_tiles, phase, b->errw, g.gs)) != cudaSuccess) return e;
+        if ((e = cudaEventRecord(ev_heat, g.gs)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(g.gd, ev_heat, 0)) != cudaSuccess) return e;
+        if ((e = g.ks->multi_launch(2, g.desc, n, 0, phase, b->errw, g.gd)) != cudaSuccess) return e;
+        if ((e = cudaEventRecord(ev_diag, g.gd)) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+static cudaError_t batch_groups_join(lbm_batch_s *b, bool captured, cudaStream_t into) {
+    cudaError_t e = cudaSuccess;
+    for (auto &g : b->groups) {
+        cudaEvent_t ev_heat = captured ? g.ev_heat : g.xev_heat, ev_diag = captured ? g.ev_diag : g.xev_diag;
+        if ((e = cudaEventRecord(ev_heat, g.gs)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(into, ev_heat, 0)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(into, ev_diag, 0)) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 // Capture two steps of every run: the batch stream forks to each run's
-// stream, each run queues its own kernels, the branches join back.
+// stream (runs outside a multi-run group: each queues its own kernels) and
+// to the groups' streams (one launch per kernel kind and step for all the
+// group's runs), and the branches join back.
 static int batch_build_graph(lbm_batch_s *b) {
+    int rc = batch_fill_groups(b);
+    if (rc != LBM_OK) return rc;
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return bfail(b, LBM_E_CUDA, std::string("batch capture: ") + cudaGetErrorString(e));
-    int rc = LBM_OK;
     if ((e = cudaEventRecord(b->fork, b->stream)) != cudaSuccess) rc = LBM_E_CUDA;
     for (size_t i = 0; i < b->runs.size() && rc == LBM_OK; i++) {
+        if (b->in_group[i]) continue;
         lbm_run *h = b->runs[i];
         if ((e = cudaStreamWaitEvent(h->stream, b->fork, 0)) != cudaSuccess) { rc = LBM_E_CUDA; break; }
         if ((rc = launch_step(h, false, false, true)) != LBM_OK || (rc = launch_step(h, false, true, true)) != LBM_OK) {
@@ -785,6 +902,12 @@ static int batch_build_graph(lbm_batch_s *b) {
         }
         if ((e = join_diag(h, true)) != cudaSuccess || (e = cudaEventRecord(b->join[i], h->stream)) != cudaSuccess ||
             (e = cudaStreamWaitEvent(b->stream, b->join[i], 0)) != cudaSuccess) { rc = LBM_E_CUDA; break; }
+    }
+    if (rc == LBM_OK && !b->groups.empty()) {
+        if ((e = batch_groups_step(b, 0, true, true, b->fork)) != cudaSuccess ||
+            (e = batch_groups_step(b, 1, false, true, b->fork)) != cudaSuccess ||
+            (e = batch_groups_join(b, true, b->stream)) != cudaSuccess)
+            rc = LBM_E_CUDA;
     }
     cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
     if (rc != LBM_OK || e2 != cudaSuccess) {
@@ -819,10 +942,40 @@ int lbm_batch_create(const lbm_handle *runs, int32_t n, lbm_batch *out) {
         b->runs.push_back(runs[i]);
         b->versions.push_back(-1);
         b->parities.push_back(-1);
+        b->in_group.push_back(false);
+    }
+    // runs whose kernel set has multi-run kernels are stepped per kernel set
+    // in one launch per kernel kind
+    for (int i = 0; i < n; i++) {
+        const KernelSet *ks = b->runs[i]->ks;
+        if (ks->multi_desc_bytes == 0) continue;
+        MultiGroup *g = nullptr;
+        for (auto &q : b->groups)
+            if (q.ks == ks) g = &q;
+        if (!g) {
+            b->groups.emplace_back();
+            g = &b->groups.back();
+            g->ks = ks;
+        }
+        g->idx.push_back(i);
+        b->in_group[i] = true;
     }
     cudaError_t e = cudaSetDevice(b->device);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+    if (e == cudaSuccess && !b->groups.empty()) {
+        e = cudaMalloc(&b->errw, sizeof(unsigned));
+        if (e == cudaSuccess) e = cudaMemsetAsync(b->errw, 0, sizeof(unsigned), b->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    }
+    for (auto &g : b->groups) {
+        g.host.resize(g.idx.size() * g.ks->multi_desc_bytes);
+        if (e == cudaSuccess) e = cudaMalloc(&g.desc, g.host.size());
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&g.gs, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&g.gd, cudaStreamNonBlocking);
+        for (cudaEvent_t *ev : {&g.ev_heat, &g.ev_diag, &g.xev_heat, &g.xev_diag})
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+    }
     for (int i = 0; i < n && e == cudaSuccess; i++) {
         cudaEvent_t ev = nullptr;
         e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
@@ -887,9 +1040,33 @@ int lbm_batch_step(lbm_batch b, int64_t n) {
         n -= 2;
     }
     if (n == 1) {
-        // odd remainder: one step of every run on its own stream
-        for (auto h : b->runs)
-            if ((rc = lbm_step(h, 1)) != LBM_OK) return bfail(b, rc, h->msg);
+        // odd remainder: one step; runs outside the groups on their own
+        // streams, the groups by one plain launch per kernel kind
+        for (size_t i = 0; i < b->runs.size(); i++)
+            if (!b->in_group[i] && (rc = lbm_step(b->runs[i], 1)) != LBM_OK) return bfail(b, rc, b->runs[i]->msg);
+        if (!b->groups.empty()) {
+            if ((rc = batch_fill_groups(b)) != LBM_OK) return rc;
+            for (size_t i = 0; i < b->runs.size(); i++) {
+                if (!b->in_group[i]) continue;
+                if ((e = cudaEventRecord(b->join[i], b->runs[i]->stream)) != cudaSuccess ||
+                    (e = cudaStreamWaitEvent(b->stream, b->join[i], 0)) != cudaSuccess)
+                    return bfail(b, LBM_E_CUDA, cudaGetErrorString(e));
+            }
+            if ((e = cudaEventRecord(b->fork, b->stream)) != cudaSuccess ||
+                (e = batch_groups_step(b, 0, true, false, b->fork)) != cudaSuccess ||
+                (e = batch_groups_join(b, false, b->stream)) != cudaSuccess ||
+                (e = cudaEventRecord(b->fork, b->stream)) != cudaSuccess)
+                return bfail(b, LBM_E_CUDA, std::string("batch step: ") + cudaGetErrorString(e));
+            for (size_t i = 0; i < b->runs.size(); i++) {
+                if (!b->in_group[i]) continue;
+                lbm_run *h = b->runs[i];
+                if ((e = cudaStreamWaitEvent(h->stream, b->fork, 0)) != cudaSuccess)
+                    return bfail(b, LBM_E_CUDA, cudaGetErrorString(e));
+                h->parity ^= 1;
+                h->steps += 1;
+                h->diag_stale = false;
+            }
+        }
     }
     return LBM_OK;
 }
@@ -922,6 +1099,14 @@ int lbm_batch_sync(lbm_batch b) {
     cudaError_t e = cudaSetDevice(b->device);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) return bfail(b, LBM_E_CUDA, cudaGetErrorString(e));
+    if (b->errw) {
+        unsigned w = 0;
+        if ((e = cudaMemcpyAsync(&w, b->errw, sizeof(w), cudaMemcpyDeviceToHost, b->stream)) != cudaSuccess ||
+            (e = cudaStreamSynchronize(b->stream)) != cudaSuccess)
+            return bfail(b, LBM_E_CUDA, cudaGetErrorString(e));
+        if (w & ERRW_DESC)
+            return bfail(b, LBM_E_STATE, "a multi-run kernel found a descriptor it could not trust and skipped its tile");
+    }
     for (auto h : b->runs) {
         int rc = lbm_sync(h);
         if (rc != LBM_OK) return bfail(b, rc, h->msg);
@@ -948,7 +1133,7 @@ int lbm_device_bytes(const lbm_domain_t *domain, const lbm_heater_t *heater, con
     // per-column arrays, per-block partials for each parity (at most one
     // block per 32 sites), series ring, small words
     *bytes = 2 * 9 * nfl * ks->f_elem + 2 * ntl * ks->T_elem + 6 * nfl * ks->m_elem + 2 * 8 * (uint64_t)domain->nx +
-             2 * 2 * 8 * (nfl / 32 + 1) + cap * SERIES_WIDTH * 8 + 1024 * 8 + 4096;
+             2 * 2 * 8 * (nfl / 32 + 1) + cap * SERIES_WIDTH * 8 + 1024 * 8 + 4096 + 2 * ks->multi_desc_bytes;
     return LBM_OK;
 }
 

@@ -1,6 +1,9 @@
 """Batches of runs: every run's result is the same alone and inside a mixed
 batch (different sizes, precisions and bottom modes), bitwise; the FP64
-members, a sweep-drawn one among them, match the oracle."""
+members, a sweep-drawn one among them, match the oracle.  A batch steps its
+FP32 and FP16 runs with the multi-run kernels (one launch per kernel kind
+over a work list of (run, tile)); a run stepped alone with those kernels
+(the "multi" launch-shape variants) gives bit for bit the same."""
 import numpy as np
 import pytest
 
@@ -31,14 +34,23 @@ def mixed_configs():
     ]
 
 
+def multi(run):
+    """Select the multi-run kernels as the run's own launch shapes (FP32 and
+    FP16 storage; other precisions keep theirs)."""
+    v = run.variants()
+    if "flowmulti_32x8x2" in v["flow"]:
+        run.select_variants(v["flow"].index("flowmulti_32x8x2"), v["heat"].index("heatmulti_64x12x4"))
+    return run
+
+
 def test_results_alone_and_in_a_batch_are_identical():
     cfgs = mixed_configs()
     alone = []
     for c in cfgs:
-        r = lbm.Run(c)
+        r = multi(lbm.Run(c))
         r.step(21)
         alone.append(r.fields(("rho", "ux", "uy", "T", "f")))
-    runs = [lbm.Run(c) for c in cfgs]
+    runs = [multi(lbm.Run(c)) for c in cfgs]
     runs[1].step(1)                 # odd parity on entry
     batch = lbm.Batch(runs)
     batch.step(13)
@@ -64,17 +76,69 @@ def test_results_alone_and_in_a_batch_are_identical():
     batch.close()
 
 
-def test_batch_recaptures_after_variant_change():
-    cfgs = [W.small_parity(precision="fp32"), W.small_parity(precision="fp32", seed=3)]
+def test_batch_steps_its_fp32_runs_with_the_multi_run_kernels_whatever_their_variants():
+    """A variant change on a run between batch steps re-captures the batch
+    graph; the batch still steps its FP32 runs with the multi-run kernels,
+    so they match runs stepped alone with the multi variants, bitwise, over
+    even and odd step counts."""
+    cfgs = [W.small_parity(precision="fp32"), W.small_parity(precision="fp32", seed=3).replace(nx=40, nf=30, liquid_rows=10, spot_x=(5, 20, 35))]
     runs = [lbm.Run(c) for c in cfgs]
-    ref = [lbm.Run(c) for c in cfgs]
+    ref = [multi(lbm.Run(c)) for c in cfgs]
     b = lbm.Batch(runs)
     b.step(4)
     runs[0].select_variants(1, 1)
-    ref[0].select_variants(1, 1)
-    b.step(6)
+    b.step(7)
+    b.sync()
     for r in ref:
-        r.step(10)
+        r.step(11)
     for r, q in zip(runs, ref):
+        a, c = r.fields(("rho", "T", "f")), q.fields(("rho", "T", "f"))
+        for k in a:
+            assert np.array_equal(a[k], c[k]), k
+        assert np.array_equal(r.series(0, 11), q.series(0, 11))
+    b.close()
+
+
+def test_multi_run_variants_agree_with_the_single_run_kernels_and_the_oracle():
+    """The multi-run kernels do the single-run kernels' per-site arithmetic:
+    against the oracle within the FP32 bounds, on a ragged domain, model A
+    with the sine bottom, an open top with the noisy bottom and a doubly
+    periodic box with heat."""
+    from gpu_util import field_errors
+    cases = [W.small_parity(precision="fp32").replace(nx=70, nf=45, ns=5, liquid_rows=15, spot_x=(3, 40, 69),
+                                                       spot_half_width=2, rho_mean=2.3),
+             W.small_parity(precision="fp32").replace(nx=48, nf=40, ns=0, liquid_rows=13, bc_mode="sine", spot_x=(),
+                                                       c_w_spot=(), sine_t0=5, sine_t1=50, sine_wavelength=24.0,
+                                                       rho_mean=2.3),
+             W.small_parity(precision="fp32").replace(nx=40, nf=33, ns=4, liquid_rows=11, top_mode="outflow",
+                                                       bc_mode="noise", spot_x=(), c_w_spot=(), rho_mean=2.3),
+             W.periodic_box(64, 40, liquid_rows=13, init_noise=1e-3, isothermal=False, precision="fp32")]
+    for cfg in cases:
+        o = O.OracleRun(cfg)
+        o.step(60)
+        g = multi(lbm.Run(cfg))
+        g.step(60)
+        g.sync()
+        e = field_errors(g, o)
+        assert e["rho"] < 1e-4 and e["T"] < 1e-5, (cfg, e)
+
+
+def test_fresh_batches_take_odd_steps_at_once():
+    """A new batch whose first call is a single step fills its run
+    descriptors and launches at once (the descriptors must land before the
+    kernels read them); repeated with fresh batches of several sizes, the
+    runs match the same runs stepped alone with the multi variants."""
+    cfgs = [c.replace(nf=96, liquid_rows=32) for c in W.sweep(6, seed=21)]
+    runs = [lbm.Run(c) for c in cfgs]
+    ref = [multi(lbm.Run(c)) for c in cfgs]
+    total = 0
+    for k in (1, 3, 1, 2, 5):
+        b = lbm.Batch(runs[: 2 + (total % 5)])
+        b.step(k)
+        b.sync()
+        b.close()
+        total += 1
+    for r, q in zip(runs, ref):
+        q.step(r.step_count)
         a, c = r.fields(("rho", "T")), q.fields(("rho", "T"))
         assert np.array_equal(a["rho"], c["rho"]) and np.array_equal(a["T"], c["T"])
