@@ -114,11 +114,14 @@ def contact_angle(rho: np.ndarray, rho_L: float, rho_V: float) -> dict:
 
 
 def measure(c_w_values, steps: int = 30000, radius: float = 30.0, precision: str = "fp32",
-            nx: int = 200, nf: int = 100, **shape) -> list:
+            nx: int = 200, nf: int = 100, reading: str = "stated", **shape) -> list:
     """Step one drop per c_w together (one lbm.Batch) and return the
-    measured contact angle of each, with the drop's mass drift."""
+    measured contact angle of each, with the drop's mass drift.  reading:
+    "stated" (a = 2/49) or "paper_tc" (a = 3/49, the printed Tc)."""
     from . import lbm
     cfgs = [drop_config(c, nx=nx, nf=nf, precision=precision) for c in c_w_values]
+    if reading == "paper_tc":
+        cfgs = [W.paper_tc_reading(c) for c in cfgs]
     runs = []
     for cfg in cfgs:
         r = lbm.Run(cfg)

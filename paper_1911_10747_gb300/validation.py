@@ -78,10 +78,20 @@ def nu_lbm(q_mean, T_w, T_sat, lam_V, lambda_d):
 
 # ---- Laplace test ---------------------------------------------------------------
 
-def laplace_config(n: int, precision: str = "fp64") -> W.RunConfig:
+def with_reading(cfg: W.RunConfig, reading: str) -> W.RunConfig:
+    """"stated": a = 2/49 as printed; "paper_tc": a = 3/49, which gives the
+    printed Tc = 0.1094 (reading 1)."""
+    if reading == "stated":
+        return cfg
+    if reading == "paper_tc":
+        return W.paper_tc_reading(cfg)
+    raise ValueError(reading)
+
+
+def laplace_config(n: int, precision: str = "fp64", reading: str = "stated") -> W.RunConfig:
     """Periodic n x n box at T_sat, no gravity, no walls (the drop's own
     test case)."""
-    return W.periodic_box(n, n, liquid_rows=0, init_noise=0.0, precision=precision)
+    return with_reading(W.periodic_box(n, n, liquid_rows=0, init_noise=0.0, precision=precision), reading)
 
 
 def disc_density(cfg: W.RunConfig, radius: float, width: float = 4.0) -> np.ndarray:
@@ -90,13 +100,13 @@ def disc_density(cfg: W.RunConfig, radius: float, width: float = 4.0) -> np.ndar
     return cfg.rho_V + 0.5 * (cfg.rho_L - cfg.rho_V) * (1.0 - np.tanh(2.0 * (r - radius) / width))
 
 
-def laplace(radii, n: int = 128, steps: int = 20000, precision: str = "fp64") -> dict:
+def laplace(radii, n: int = 128, steps: int = 20000, precision: str = "fp64", reading: str = "stated") -> dict:
     """Drops of the given radii stepped together; for each the equivalent
     radius (from the liquid area, rho between the inner and the outer bulk
     value) and the pressure jump p_EOS(rho_in) - p_EOS(rho_out); sigma is
     the least-squares slope of dp against 1/R (with an intercept)."""
     from . import lbm
-    cfg = laplace_config(n, precision)
+    cfg = laplace_config(n, precision, reading)
     tc = critical_temperature(cfg.a, cfg.b, cfg.R)
     T = cfg.T_sat_over_Tc * tc
     runs = []
@@ -126,13 +136,13 @@ def laplace(radii, n: int = 128, steps: int = 20000, precision: str = "fp64") ->
     fit = A @ np.array([sigma, icpt])
     r2 = 1.0 - float(np.sum((dp - fit) ** 2) / np.sum((dp - dp.mean()) ** 2))
     return {"sigma": float(sigma), "intercept": float(icpt), "r2": r2, "drops": rows,
-            "setting": f"{n}x{n} periodic box at T_sat, {steps} steps, {precision}"}
+            "setting": f"{n}x{n} periodic box at T_sat, {steps} steps, {precision}, a = {cfg.a:.6f}"}
 
 
 # ---- film boiling (Sec. 3.2) ----------------------------------------------------
 
 def film_boiling_config(sigma: float, g: float = 5e-5, precision: str = "fp32", T_b_over_Tc: float = 1.27,
-                        seed: int = 7) -> W.RunConfig:
+                        seed: int = 7, reading: str = "stated") -> W.RunConfig:
     """Model B sized by lambda_d of Eq. 29: fluid 2 lambda_d x 1.5 lambda_d,
     heater 0.15 lambda_d, liquid in the lower half of the fluid; constant
     T_b with the sine of Sec. 3.2 (0.02 Tc, wavelength lambda_d) between
@@ -142,22 +152,23 @@ def film_boiling_config(sigma: float, g: float = 5e-5, precision: str = "fp32", 
     ld = taylor_wavelength(sigma, g, drho)
     t0 = characteristic_time(sigma, g, drho)
     nx, nf, ns = int(round(2 * ld)), int(round(1.5 * ld)), max(3, int(round(0.15 * ld)))
-    return base.replace(nx=nx, nf=nf, ns=ns, liquid_rows=nf // 2, g=g, rho_mean=0.0, bc_mode="sine",
-                        spot_x=(), c_w_spot=(), T_b_over_Tc=T_b_over_Tc, sine_amp_over_Tc=0.02,
-                        sine_wavelength=ld, sine_t0=int(round(5.0 * t0)), sine_t1=int(round(24.98 * t0)),
-                        lambda_s=16.25, rho_c_s=3 * base.rho_L * base.c_v, seed=seed)
+    return with_reading(base.replace(nx=nx, nf=nf, ns=ns, liquid_rows=nf // 2, g=g, rho_mean=0.0, bc_mode="sine",
+                                     spot_x=(), c_w_spot=(), T_b_over_Tc=T_b_over_Tc, sine_amp_over_Tc=0.02,
+                                     sine_wavelength=ld, sine_t0=int(round(5.0 * t0)),
+                                     sine_t1=int(round(24.98 * t0)), lambda_s=16.25,
+                                     rho_c_s=3 * base.rho_L * base.c_v, seed=seed), reading)
 
 
 def film_boiling(sigma: float, h_fg: float = 0.58, t_end_star: float = 60.0, g: float = 5e-5,
                  precision: str = "fp32", sample_every: int = 100, T_b_over_Tc: float = 1.27,
-                 c_w: float | None = None) -> dict:
+                 c_w: float | None = None, reading: str = "stated") -> dict:
     """Run the film-boiling case to t* = t_end_star and compare Eq. 35 with
     Eq. 34.  T_w is the space- and time-averaged temperature of the heater's
     top row and Q the space-averaged heat flux, both averaged over
     t* > 41.63 (Sec. 3.2); Q is reported at the heater bottom (Eq. 36) and
     through the heater surface."""
     from . import lbm
-    cfg = film_boiling_config(sigma, g=g, precision=precision, T_b_over_Tc=T_b_over_Tc)
+    cfg = film_boiling_config(sigma, g=g, precision=precision, T_b_over_Tc=T_b_over_Tc, reading=reading)
     if c_w is not None:
         cfg = cfg.replace(c_w_base=c_w)
     drho = cfg.rho_L - cfg.rho_V
@@ -197,7 +208,7 @@ def film_boiling(sigma: float, h_fg: float = 0.58, t_end_star: float = 60.0, g: 
             "vapour_fraction_end": float(ser[-1, 2]), "rho_first_fluid_row": rho_wall,
             "c_w": cfg.c_w_base, "mass_drift": float(ser[-1, 3] / ser[0, 3] - 1.0),
             "nu_series_surface": [round(nu_lbm(q, T_w, T_sat, lam_V, ld), 3) for q in ser[::every, 1]],
-            "precision": precision}
+            "precision": precision, "a": cfg.a}
 
 
 # ---- storage-precision report ---------------------------------------------------

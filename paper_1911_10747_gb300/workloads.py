@@ -49,6 +49,14 @@ DEFAULT_CW_SPOTS = (-1.371, -1.282, -1.197)
 #: the fluid like saturated vapour beyond it would.
 DEFAULT_CW_TOP = -0.465
 
+#: The attraction parameter a of Eq. 13.  Sec. 2.1 states a = 2/49 and,
+#: beside it, Tc = 0.1094; with b = 2/21 and R = 1 the printed Tc needs
+#: a = 3/49 (Tc = 0.0778 a / (0.45724 b R)).  A_STATED is the default;
+#: A_PAPER_TC is the reading that reproduces the printed Tc (and the
+#: latent heat h_LV = 0.58 of Sec. 3.1).
+A_STATED = 2.0 / 49.0
+A_PAPER_TC = 3.0 / 49.0
+
 
 @dataclass
 class RunConfig:
@@ -68,7 +76,7 @@ class RunConfig:
     c_w_base: float = DEFAULT_CW_BASE
     c_w_spot: tuple = ()
     c_w_top: float = DEFAULT_CW_TOP
-    a: float = 2.0 / 49.0
+    a: float = A_STATED
     b: float = 2.0 / 21.0
     R: float = 1.0
     omega: float = 0.344
@@ -244,3 +252,23 @@ def serving_requests(n: int = 200, seed: int = 5, step_scale: float = 1.0) -> li
                         seed=1000 + i, precision=prec)
         out.append((cfg, max(2, steps)))
     return out
+
+
+def psi_of(rho: float, cfg: "RunConfig") -> float:
+    """psi(rho, T_sat) of Eq. 12-13 for the configuration's EOS (G = -1)."""
+    import math
+    tc = (0.0778 * cfg.a) / (0.45724 * cfg.b * cfg.R)
+    T = cfg.T_sat_over_Tc * tc
+    kappa = 0.37464 + 1.54226 * cfg.omega - 0.26992 * cfg.omega ** 2
+    phi = (1.0 + kappa * (1.0 - math.sqrt(T / tc))) ** 2
+    br = cfg.b * rho
+    p = rho * cfg.R * T / (1.0 - br) - cfg.a * phi * rho * rho / (1.0 + 2.0 * br - br * br)
+    return math.sqrt(2.0 / (-cfg.G) * (rho / 3.0 - p))
+
+
+def paper_tc_reading(cfg: "RunConfig") -> "RunConfig":
+    """The configuration under the a = 3/49 reading (Tc = 0.1094 as printed):
+    temperatures stay fixed multiples of Tc, and the lid keeps c_w = -psi of
+    saturated vapour at the new T_sat."""
+    out = cfg.replace(a=A_PAPER_TC)
+    return out.replace(c_w_top=-psi_of(out.rho_V, out))
