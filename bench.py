@@ -35,11 +35,6 @@ METRIC = "MLUPS (fluid-site updates per second), one GB300"
 # read + written, temperature read)
 ALG_STEP_BYTES = {"fp32": 80, "fp64": 160, "fp16": 44}
 ALG_FLOW_BYTES = {"fp32": 76, "fp64": 152, "fp16": 40}
-# arithmetic of the heat kernel per temperature site and step: four RK
-# stages of ~46 flops (9-point conduction with link weights, Eq. 27 gradient,
-# advection, the C1 T + C2 sqrt(T) source, stage update) plus ~90 flops of
-# per-step coefficients (harmonic means, div u, EOS factors)
-HEAT_FLOPS = 274
 # FP32 peak from unit counts and clock: 152 SMs x 128 FP32 lanes x 2 flops x clock
 FP32_LANES = 152 * 128
 PROFILES = {"flow": os.path.join(ROOT, "profiles", "flow_kernel_2048x2048_fp32.md"),
@@ -56,7 +51,7 @@ def peaks():
         return 6800.0, "fallback"
 
 
-KERNEL_SOURCES = ("lbm_device.cuh", "lbm_fast.cuh", "lbm_tma.cuh")
+KERNEL_SOURCES = ("lbm_device.cuh", "lbm_dfloat.cuh", "lbm_fast.cuh", "lbm_tma.cuh")
 FP64_SOURCES = ("lbm_device.cuh", "lbm_fp64.cu")  # the FP64 kernels and their launch shapes
 
 
@@ -82,34 +77,47 @@ def kernel_source_hash(names=KERNEL_SOURCES) -> str:
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kind: str, variant: str):
-    """DRAM bytes per launch of the flow or heat kernel from the committed ncu
-    summary, or None when absent, taken on a different kernel source, or not
-    taken on the launch-shape variant that was timed."""
+def ncu_figure(kind: str, key: str, variant: str):
+    """A per-variant figure (`key[variant]: value`) from the committed ncu
+    summary of the flow or heat kernel, or None when absent, taken on a
+    different kernel source, or not taken on that launch-shape variant."""
     try:
         text = open(PROFILES[kind]).read()
     except OSError:
         return None
     m = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", text)
-    t = re.search(r"dram_bytes_per_full_launch\[" + re.escape(variant) + r"\]:\s*([0-9.eE+]+)", text)
+    t = re.search(re.escape(key) + r"\[" + re.escape(variant) + r"\]:\s*([0-9.eE+]+)", text)
     if not m or not t or m.group(1) != kernel_source_hash():
         return None
     return float(t.group(1))
+
+
+def ncu_traffic(kind: str, variant: str):
+    """DRAM bytes (read + written) per launch of the timed variant."""
+    return ncu_figure(kind, "dram_bytes_per_full_launch", variant)
 
 
 def ncu_instructions(kind: str, variant: str):
-    """Executed instructions per site (warp instructions x 32 / sites, ncu)
-    of the flow or heat variant in the committed summary, or None when absent
-    or taken on a different kernel source."""
-    try:
-        text = open(PROFILES[kind]).read()
-    except OSError:
-        return None
-    m = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", text)
-    t = re.search(r"instructions_per_site\[" + re.escape(variant) + r"\]:\s*([0-9.eE+]+)", text)
-    if not m or not t or m.group(1) != kernel_source_hash():
-        return None
-    return float(t.group(1))
+    """Executed instructions per site (warp instructions x 32 / sites)."""
+    return ncu_figure(kind, "instructions_per_site", variant)
+
+
+# the heat variant whose FP32 operations were counted when the timed one was not
+HEAT_COUNTED_VARIANT = "heatpair_64x12x4"
+
+
+def heat_flops(variant: str):
+    """FP32 flops per temperature site the heat kernel executes (ncu thread
+    instruction counts: FADD + FMUL + 2 FFMA, twice that for the packed
+    FADD2 / FMUL2 / FFMA2; the recomputed tile halo included) and the variant
+    they were counted on: the timed variant's own count, else the paired
+    64 x 12 x 4 kernel's (every variant does the same per-site arithmetic,
+    with its own halo share), else (None, None)."""
+    for v in (variant, HEAT_COUNTED_VARIANT):
+        f = ncu_figure("heat", "flops_per_site", v)
+        if f is not None:
+            return f, v
+    return None, None
 
 
 def issue_roofline(inst_per_site, sites, ms):
@@ -690,14 +698,17 @@ def run_ours(args):
                  "traffic": ncu_traffic("flow", vnames[0]) if args.precision == "fp32" else None,
                  "peak_source": peak_kind}
     fp32_peak = FP32_LANES * 2 * max_sm_mhz() * 1e6 / 1e12
-    heat_achieved = HEAT_FLOPS * cfg.temperature_sites / (kms[1] / 1e3) / 1e12
+    hflops, hcounted = heat_flops(vnames[1]) if args.precision == "fp32" else (None, None)
+    heat_achieved = hflops * cfg.temperature_sites / (kms[1] / 1e3) / 1e12 if hflops else None
     heat_roof = {"bound": "alu", "achieved": heat_achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                 "frac": heat_achieved / fp32_peak, "kernel": "k_heat", "flops_per_site": HEAT_FLOPS,
+                 "frac": heat_achieved / fp32_peak if hflops else None, "kernel": "k_heat",
+                 "flops_per_site": hflops, "flops_counted_on": hcounted,
+                 "flops_kind": "executed FP32 operations (ncu SASS counts, tile halo included)",
                  "traffic": ncu_traffic("heat", vnames[1]) if args.precision == "fp32" else None,
                  "peak_source": "152 SMs x 128 FP32 lanes x 2 x max SM clock"}
     # the same fraction against the FMA throughput measured on this GPU (context)
     fma32 = lbm.peak_fma(32, device=local)
-    heat_roof.update(measured_fma_peak=fma32, frac_of_measured_fma=heat_achieved / fma32)
+    heat_roof.update(measured_fma_peak=fma32, frac_of_measured_fma=heat_achieved / fma32 if hflops else None)
     # instruction issue (context: both kernels spend their time issuing or
     # waiting, not moving bytes or doing flops at the pipes' rates)
     if args.precision == "fp32":

@@ -27,6 +27,19 @@ def test_summary_values_are_used_only_for_the_current_kernel_sources(profile):
     assert bench.ncu_instructions("heat", "v1") is None     # no summary
 
 
+def test_heat_flops_take_the_timed_variants_count_else_the_counted_variants(profile):
+    h = bench.kernel_source_hash()
+    v = bench.HEAT_COUNTED_VARIANT
+    profile.write_text(f"flops_per_site[{v}]: 261.6\n"
+                       "flops_per_site[other]: 250.0\n"
+                       f"kernel_source_sha256_16: {h}\n")
+    assert bench.heat_flops("other") == (250.0, "other")
+    assert bench.heat_flops("uncounted") == (261.6, v)
+    profile.write_text(f"flops_per_site[{v}]: 261.6\n"
+                       "kernel_source_sha256_16: 0000000000000000\n")
+    assert bench.heat_flops(v) == (None, None)              # taken on other code
+
+
 def test_source_hash_ignores_comments_and_white_space(tmp_path, monkeypatch):
     a, b, c = tmp_path / "a.cuh", tmp_path / "b.cuh", tmp_path / "c.cuh"
     a.write_text("int f(int x) { return x + 1; }  // one\n")
