@@ -67,6 +67,7 @@ struct StepBuffers {
     double *last;            // [SERIES_WIDTH] diagnostics of the last step
     double *scratch;         // reduction scratch for init (>= 1024 doubles)
     const void *mdesc;       // the run's own multi-run descriptor for this parity (kernel sets that have one)
+    unsigned *wq;            // 2 words, zero between launches: work counter of the wavefront flow kernel
 };
 
 // One launch shape of the flow or heat kernel.  Every variant of a kernel

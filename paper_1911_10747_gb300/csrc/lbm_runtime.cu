@@ -98,6 +98,7 @@ static StepBuffers buffers(lbm_run *h, int par) {
     b.cw = h->cw;
     b.part = h->part[par];
     b.err = h->err;
+    b.wq = h->err + 2;  // words 2, 3 of the run's error-word block
     b.step = h->dstep;
     b.series = h->series;
     b.series_cap = h->series_cap;
@@ -371,7 +372,7 @@ int lbm_create(const lbm_domain_t *domain, const lbm_heater_t *heater, const lbm
         {(void **)&h->part[1], 2 * (size_t)max_blocks * sizeof(double)},
         {(void **)&h->series, (size_t)h->series_cap * SERIES_WIDTH * sizeof(double)},
         {(void **)&h->q_top, (size_t)p.nx * sizeof(double)}, {(void **)&h->last, SERIES_WIDTH * sizeof(double)},
-        {(void **)&h->scratch, 1024 * sizeof(double)}, {(void **)&h->err, sizeof(unsigned)},
+        {(void **)&h->scratch, 1024 * sizeof(double)}, {(void **)&h->err, 4 * sizeof(unsigned)},
         {(void **)&h->dstep, sizeof(long long)},
         {&h->mdesc, 2 * h->ks->multi_desc_bytes},
     };
@@ -398,10 +399,9 @@ int lbm_create(const lbm_domain_t *domain, const lbm_heater_t *heater, const lbm
         cwh[x] = c;
     }
     long long zero = 0;
-    unsigned zu = 0;
     if ((e = cudaMemcpyAsync(h->cw, cwh.data(), p.nx * sizeof(double), cudaMemcpyHostToDevice, h->stream)) != cudaSuccess ||
         (e = cudaMemcpyAsync(h->dstep, &zero, sizeof(zero), cudaMemcpyHostToDevice, h->stream)) != cudaSuccess ||
-        (e = cudaMemcpyAsync(h->err, &zu, sizeof(zu), cudaMemcpyHostToDevice, h->stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(h->err, 0, 4 * sizeof(unsigned), h->stream)) != cudaSuccess ||
         (e = cudaMemsetAsync(h->last, 0, SERIES_WIDTH * sizeof(double), h->stream)) != cudaSuccess ||
         (e = cudaMemsetAsync(h->q_top, 0, p.nx * sizeof(double), h->stream)) != cudaSuccess) {
         cuda_fail(h, e, "initial copies");

@@ -275,3 +275,54 @@ def test_fp32_heat_variants_in_a_periodic_box_with_heat(ny):
         g.sync()
         errs = field_errors(g, o)
         assert errs["rho"] < 1e-4 and errs["T"] < 1e-5, (name, errs)
+
+
+@pytest.mark.parametrize("kw", [
+    dict(nx=192, nf=45, ns=5, liquid_rows=15, spot_x=(3, 100, 191), spot_half_width=2),
+    dict(nx=128, nf=37, ns=4, liquid_rows=12, top_mode="outflow", bc_mode="noise", spot_x=(), c_w_spot=()),
+    dict(nx=128, nf=40, ns=0, liquid_rows=13, bc_mode="sine", spot_x=(), c_w_spot=()),
+    dict(nx=64, nf=200, ns=3, liquid_rows=60, spot_x=(0, 31, 63), spot_half_width=1),
+])
+def test_fp32_wavefront_flow_variants_against_the_oracle(kw):
+    """The flow kernels in which each warp sweeps a 64-column strip up a
+    segment of rows (nx a multiple of 64): several strips across with the
+    periodic x edges, nucleate spots on a strip edge, an open top, model A
+    with the sine bottom, and a tall single-strip domain cut into many
+    segments, against the oracle; and both wavefront shapes agree."""
+    cfg = W.small_parity(precision="fp32").replace(rho_mean=2.3, **kw)
+    if cfg.bc_mode == "sine":
+        cfg = cfg.replace(sine_t0=5, sine_t1=50, sine_wavelength=48.0)
+    names = lbm.Run(cfg).variants()["flow"]
+    wave = [i for i, n in enumerate(names) if n.startswith("flowwave_")]
+    assert len(wave) >= 2
+    o = O.OracleRun(cfg)
+    o.step(60)
+    got = []
+    for fv in wave:
+        g = lbm.Run(cfg)
+        g.select_variants(fv, 0)
+        g.step(60)
+        g.sync()
+        errs = field_errors(g, o)
+        assert errs["rho"] < 1e-4 and errs["T"] < 1e-5, (names[fv], errs)
+        assert g.mass() == pytest.approx(o.diagnostics()["mass"], rel=1e-6), names[fv]
+        got.append(g.fields(("rho", "f")))
+    for k in got[0]:   # same per-site arithmetic whatever the launch shape
+        assert np.max(np.abs(got[0][k] - got[1][k])) <= 1e-5 * np.abs(got[0][k]).max(), k
+
+
+@pytest.mark.parametrize("ny", [6, 70])
+def test_fp32_wavefront_flow_in_a_periodic_box(ny):
+    """Periodic in y: the sweep's first and last rows wrap (6 rows: fewer
+    than one segment), against the oracle."""
+    cfg = W.periodic_box(128, ny, liquid_rows=max(1, ny // 3), init_noise=1e-3, precision="fp32")
+    names = lbm.Run(cfg).variants()["flow"]
+    o = O.OracleRun(cfg)
+    o.step(40)
+    for fv in [i for i, n in enumerate(names) if n.startswith("flowwave_")]:
+        g = lbm.Run(cfg)
+        g.select_variants(fv, 0)
+        g.step(40)
+        g.sync()
+        errs = field_errors(g, o)
+        assert errs["rho"] < 1e-4, (names[fv], errs)

@@ -189,25 +189,27 @@ def test_fp64_parity_sessile_drop_from_set_state():
     assert all(v <= TOL64 for v in errs.values()), errs
 
 
-def test_staged_copy_wait_that_runs_out_is_reported_and_the_context_survives(monkeypatch):
-    """The staged-copy flow kernel bounds its waits on the copy barrier.  The
-    test hook makes each stage expect 16 bytes more than its copies deliver,
-    so every wait runs out (after 100 ms): the step must report
-    LBM_E_TIMEOUT, and a new run on the same context must work."""
+@pytest.mark.parametrize("variant", ["flowtma_64x4x2_b3", "flowwave_w4_b4"])
+def test_staged_copy_wait_that_runs_out_is_reported_and_the_context_survives(monkeypatch, variant):
+    """The flow kernels that stage rows or tiles by tensor copies bound their
+    waits on the copy barriers.  The test hook makes each stage expect 16
+    bytes more than its copies deliver, so every wait runs out (after
+    100 ms): the step must report LBM_E_TIMEOUT, and a new run on the same
+    context must work."""
     cfg = W.small_parity(precision="fp32").replace(nx=128, nf=40, ns=4, liquid_rows=12, rho_mean=2.3,
                                                    spot_x=(), c_w_spot=())
     monkeypatch.setenv("LBM_TEST_TX_PAD", "16")
     g = lbm.Run(cfg)
     monkeypatch.delenv("LBM_TEST_TX_PAD")
     names = g.variants()["flow"]
-    g.select_variants(names.index("flowtma_64x4x2_b3"), 0)
+    g.select_variants(names.index(variant), 0)
     g.step(1)
     with pytest.raises(lbm.LbmError) as ei:
         g.sync()
     assert "LBM_E_TIMEOUT" in str(ei.value)
     del g
     ok = lbm.Run(cfg)
-    ok.select_variants(names.index("flowtma_64x4x2_b3"), 0)
+    ok.select_variants(names.index(variant), 0)
     ok.step(3)
     ok.sync()
     assert ok.step_count == 3
