@@ -53,32 +53,25 @@ constexpr int FW_OT = 672, FW_OSF = 768, FW_OST = 832, FW_SLOT = 864;
 constexpr uint32_t FW_BYTES = 10u * FW_SC * 4u;     // main boxes of a row
 constexpr uint32_t FW_SIDE_BYTES = 10u * FW_H * 4u;  // wrapped halo boxes
 
-// The constants of the packed arithmetic, each in both halves of a pair,
-// passed as a kernel parameter (packed instructions read them from the
-// constant bank instead of holding them in registers).
+// The run's constants of the packed arithmetic, each in both halves of a
+// pair, passed as a kernel parameter.
 struct FlowWaveConsts {
-    float2 w1, w2, mG, topc, rho_mean, g, rho0, tsat, half, mhalf, one, two, three, four, six;
-    float2 m2, m3, m4, msix, rhoV, idtau, tauV, varpi, itauem, sgnts;
+    float2 mG, topc, rho_mean, g, rho0, tsat, rhoV, idtau, tauV, varpi, itauem, sgnts;
     float2 ms[7], hs[7];  // -s_k and 1 - s_k / 2 for k = 1..6 (index k)
-    float2 ninth, i36, sixth, twelfth, quarter;
-    float2 invTc, kappa, b, R, a, two_over_G, third;  // psi (Eq. 12-13)
+    float2 invTc, kappa, b, R, a, two_over_G;  // psi (Eq. 12-13)
 };
 inline FlowWaveConsts make_flowwave_consts(const FParams &q) {
     auto d = [](float v) { return make_float2(v, v); };
     FlowWaveConsts k{};
     const float w1 = 1.0f / 3.0f, w2 = 1.0f / 12.0f;
-    k.w1 = d(w1); k.w2 = d(w2); k.mG = d(q.mG);
+    k.mG = d(q.mG);
     k.topc = d(-((w1 + 2.0f * w2) * q.c_w_top));  // top-wall adhesion per unit psi
     k.rho_mean = d(q.rho_mean); k.g = d(q.g); k.rho0 = d(q.rho_shift); k.tsat = d(q.T_sat);
-    k.half = d(0.5f); k.mhalf = d(-0.5f); k.one = d(1.0f); k.two = d(2.0f); k.three = d(3.0f);
-    k.four = d(4.0f); k.six = d(6.0f); k.m2 = d(-2.0f); k.m3 = d(-3.0f); k.m4 = d(-4.0f); k.msix = d(-6.0f);
     k.rhoV = d(q.rho_V); k.idtau = d(q.inv_drho * q.dtau); k.tauV = d(q.tau_V);
     k.varpi = d(q.varpi12G2); k.itauem = d(q.inv_tauem); k.sgnts = d(q.sgn_over_taus);
     for (int i = 1; i <= 6; i++) { k.ms[i] = d(-q.s[i]); k.hs[i] = d(q.hs[i]); }
-    k.ninth = d(1.0f / 9.0f); k.i36 = d(1.0f / 36.0f); k.sixth = d(1.0f / 6.0f); k.twelfth = d(1.0f / 12.0f);
-    k.quarter = d(0.25f);
     k.invTc = d(q.inv_Tc); k.kappa = d(q.kappa); k.b = d(q.b); k.R = d(q.R); k.a = d(q.a);
-    k.two_over_G = d(q.two_over_G); k.third = d(1.0f / 3.0f);
+    k.two_over_G = d(q.two_over_G);
     return k;
 }
 
@@ -87,13 +80,13 @@ inline FlowWaveConsts make_flowwave_consts(const FParams &q) {
 __device__ __forceinline__ float2 psi_pair(const FlowWaveConsts &K, float2 rho, float2 T, unsigned &errbits) {
     const float2 tt = mul2(T, K.invTc);
     const float2 t1 = make_float2(fast_sqrt(tt.x), fast_sqrt(tt.y));
-    const float2 t2 = fma2(K.kappa, sub2(K.one, t1), K.one);
+    const float2 t2 = fma2(K.kappa, sub2(f2(1.0f), t1), f2(1.0f));
     const float2 phi = mul2(t2, t2);
     const float2 br = mul2(K.b, rho);
-    const float2 omb = sub2(K.one, br), den = fma2(br, sub2(K.two, br), K.one);
+    const float2 omb = sub2(f2(1.0f), br), den = fma2(br, sub2(f2(2.0f), br), f2(1.0f));
     const float2 num = sub2(mul2(mul2(K.R, T), den), mul2(mul2(mul2(K.a, phi), rho), omb));
     const float2 pr = mul2(mul2(rho, num), rcp2(mul2(omb, den)));
-    const float2 arg = mul2(K.two_over_G, sub2(pr, mul2(rho, K.third)));
+    const float2 arg = mul2(K.two_over_G, sub2(pr, mul2(rho, f2(1.0f / 3.0f))));
     // psi = 0 where the radicand is not positive; a negative (or NaN) one is a fault
     const bool bx = !(arg.x > 0.0f) && !(arg.x == 0.0f), by = !(arg.y > 0.0f) && !(arg.y == 0.0f);
     errbits |= (bx || by) ? (unsigned)ERRW_PSI : 0u;
@@ -116,16 +109,16 @@ __device__ __forceinline__ void wave_collide(const FParams &p, const FlowWaveCon
     const float2 a = sub2(E1, Wm);  // pNE - pSW
     const float2 b = sub2(Em, W1);  // pSE - pNW
     const float2 pre = mul2(K.mG, psi);
-    const float2 sx = fma2(K.w1, sub2(E0, W0), mul2(K.w2, add2(a, b)));
-    const float2 sy = fma2(K.w1, sub2(P1, Pm), mul2(K.w2, sub2(a, b)));
+    const float2 sx = fma2(f2(1.0f / 3.0f), sub2(E0, W0), mul2(f2(1.0f / 12.0f), add2(a, b)));
+    const float2 sy = fma2(f2(1.0f / 3.0f), sub2(P1, Pm), mul2(f2(1.0f / 12.0f), sub2(a, b)));
     const float2 rho = add2(d, K.rho0);
     float2 Fx = mul2(pre, sx);
     float2 Fy = mul2(pre, sy);
     if (bot) {  // Eq. 14 with the heater sites below (i = 4, 7, 8)
         const float cW = float(cw[xw]), cA = float(cw[c0]), cB = float(cw[c1]), cE = float(cw[xe]);
         const float2 cm = make_float2(cW, cA), cc = make_float2(cA, cB), cp = make_float2(cB, cE);
-        Fx = sub2(Fx, mul2(psi, mul2(K.w2, sub2(cp, cm))));
-        float2 Fay = mul2(psi, fma2(K.w1, cc, mul2(K.w2, add2(cm, cp))));
+        Fx = sub2(Fx, mul2(psi, mul2(f2(1.0f / 12.0f), sub2(cp, cm))));
+        float2 Fay = mul2(psi, fma2(f2(1.0f / 3.0f), cc, mul2(f2(1.0f / 12.0f), add2(cm, cp))));
         if (top && !outflow) Fay = add2(Fay, mul2(psi, K.topc));
         Fy = add2(Fy, Fay);
     } else if (top && !outflow) {
@@ -135,29 +128,29 @@ __device__ __forceinline__ void wave_collide(const FParams &p, const FlowWaveCon
     // moments of g (Eq. 6 with the rho0 shift folded into q0..q2)
     const float2 s14 = add2(add2(gp[1], gp[2]), add2(gp[3], gp[4]));
     const float2 s58 = add2(add2(gp[5], gp[6]), add2(gp[7], gp[8]));
-    const float2 m1 = fma2(K.two, s58, sub2(mul2(K.m4, gp[0]), s14));
-    const float2 m2 = add2(fma2(K.m2, s14, mul2(K.four, gp[0])), s58);
+    const float2 m1 = fma2(f2(2.0f), s58, sub2(mul2(f2(-4.0f), gp[0]), s14));
+    const float2 m2 = add2(fma2(f2(-2.0f), s14, mul2(f2(4.0f), gp[0])), s58);
     const float2 f13 = sub2(gp[1], gp[3]), f24 = sub2(gp[2], gp[4]);
     const float2 f57 = sub2(gp[5], gp[7]), f86 = sub2(gp[8], gp[6]);
     const float2 sp = add2(f57, f86), sm = sub2(f57, f86);
-    const float2 m3 = add2(f13, sp), m4 = fma2(K.m2, f13, sp);
-    const float2 m5 = add2(f24, sm), m6 = fma2(K.m2, f24, sm);
+    const float2 m3 = add2(f13, sp), m4 = fma2(f2(-2.0f), f13, sp);
+    const float2 m5 = add2(f24, sm), m6 = fma2(f2(-2.0f), f24, sm);
     const float2 m7 = sub2(add2(gp[1], gp[3]), add2(gp[2], gp[4]));
     const float2 m8 = sub2(add2(gp[5], gp[7]), add2(gp[6], gp[8]));
     const float2 irho = rcp2(rho);
-    const float2 ux = mul2(fma2(K.half, Fx, m3), irho), uy = mul2(fma2(K.half, Fy, m5), irho);
+    const float2 ux = mul2(fma2(f2(0.5f), Fx, m3), irho), uy = mul2(fma2(f2(0.5f), Fy, m5), irho);
     const float2 tau = fma2(sub2(rho, K.rhoV), K.idtau, K.tauV);
     const float2 s78 = rcp2(tau);
     const float2 uxx = mul2(ux, ux), uyy = mul2(uy, uy);
     const float2 ru2 = mul2(rho, add2(uxx, uyy));
-    const float2 q1 = fma2(K.three, ru2, mul2(K.m2, d)), q2 = fma2(K.m3, ru2, d);
+    const float2 q1 = fma2(f2(3.0f), ru2, mul2(f2(-2.0f), d)), q2 = fma2(f2(-3.0f), ru2, d);
     const float2 q3 = mul2(rho, ux), q5 = mul2(rho, uy);
     const float2 q7 = mul2(rho, sub2(uxx, uyy)), q8 = mul2(rho, mul2(ux, uy));
     const float2 uF = fma2(ux, Fx, mul2(uy, Fy));
     const float2 e2v = mul2(K.varpi, fma2(sx, sx, mul2(sy, sy)));
     const float2 eps = make_float2(psi.x > 0.0f ? e2v.x : 0.0f, psi.y > 0.0f ? e2v.y : 0.0f);
-    const float2 S1 = fma2(K.six, uF, mul2(eps, K.itauem));
-    const float2 S2 = fma2(K.msix, uF, mul2(eps, K.sgnts));
+    const float2 S1 = fma2(f2(6.0f), uF, mul2(eps, K.itauem));
+    const float2 S2 = fma2(f2(-6.0f), uF, mul2(eps, K.sgnts));
     // Eq. 7 (m0 unchanged; q4 = -q3, q6 = -q5)
     const float2 z1 = fma2(K.hs[1], S1, fma2(K.ms[1], sub2(m1, q1), m1));
     const float2 z2 = fma2(K.hs[2], S2, fma2(K.ms[2], sub2(m2, q2), m2));
@@ -165,17 +158,17 @@ __device__ __forceinline__ void wave_collide(const FParams &p, const FlowWaveCon
     const float2 z4 = sub2(fma2(K.ms[4], add2(m4, q3), m4), mul2(K.hs[4], Fx));
     const float2 z5 = fma2(K.hs[5], Fy, fma2(K.ms[5], sub2(m5, q5), m5));
     const float2 z6 = sub2(fma2(K.ms[6], add2(m6, q5), m6), mul2(K.hs[6], Fy));
-    const float2 h78 = fma2(K.mhalf, s78, K.one);
-    const float2 z7 = fma2(h78, mul2(K.two, sub2(mul2(ux, Fx), mul2(uy, Fy))),
+    const float2 h78 = fma2(f2(-0.5f), s78, f2(1.0f));
+    const float2 z7 = fma2(h78, mul2(f2(2.0f), sub2(mul2(ux, Fx), mul2(uy, Fy))),
                            sub2(m7, mul2(s78, sub2(m7, q7))));
     const float2 z8 = fma2(h78, fma2(ux, Fy, mul2(uy, Fx)), sub2(m8, mul2(s78, sub2(m8, q8))));
-    const float2 e0 = mul2(d, K.ninth), e1 = mul2(z1, K.i36), e2 = mul2(z2, K.i36);
-    const float2 e3 = mul2(z3, K.sixth), e4 = mul2(z4, K.twelfth), e5 = mul2(z5, K.sixth);
-    const float2 e6 = mul2(z6, K.twelfth), e7 = mul2(z7, K.quarter), e8 = mul2(z8, K.quarter);
-    const float2 A0 = fma2(K.m2, e2, sub2(e0, e1));  // axis-direction common part
-    const float2 B0 = add2(fma2(K.two, e1, e0), e2); // diagonal common part
-    const float2 fo0 = fma2(K.four, e2, fma2(K.m4, e1, e0));
-    const float2 t34 = fma2(K.m2, e4, e3), t56 = fma2(K.m2, e6, e5);
+    const float2 e0 = mul2(d, f2(1.0f / 9.0f)), e1 = mul2(z1, f2(1.0f / 36.0f)), e2 = mul2(z2, f2(1.0f / 36.0f));
+    const float2 e3 = mul2(z3, f2(1.0f / 6.0f)), e4 = mul2(z4, f2(1.0f / 12.0f)), e5 = mul2(z5, f2(1.0f / 6.0f));
+    const float2 e6 = mul2(z6, f2(1.0f / 12.0f)), e7 = mul2(z7, f2(0.25f)), e8 = mul2(z8, f2(0.25f));
+    const float2 A0 = fma2(f2(-2.0f), e2, sub2(e0, e1));  // axis-direction common part
+    const float2 B0 = add2(fma2(f2(2.0f), e1, e0), e2); // diagonal common part
+    const float2 fo0 = fma2(f2(4.0f), e2, fma2(f2(-4.0f), e1, e0));
+    const float2 t34 = fma2(f2(-2.0f), e4, e3), t56 = fma2(f2(-2.0f), e6, e5);
     const float2 fo1 = add2(add2(A0, t34), e7), fo3 = add2(sub2(A0, t34), e7);
     const float2 fo2 = sub2(add2(A0, t56), e7), fo4 = sub2(sub2(A0, t56), e7);
     const float2 cxx = add2(e3, e4), cyy = add2(e5, e6);
@@ -270,19 +263,17 @@ k_flow_wave(const __grid_constant__ CUtensorMap map_f, const __grid_constant__ C
         const int c0 = x0 + 2 * lane, c1 = c0 + 1;
         const int xw = c0 == 0 ? nx - 1 : c0 - 1, xe = c0 + 2 == nx ? 0 : c0 + 2;
         // this lane's halo column in a staged row: the west one (x0 - 1), in
-        // lane 31 the east one (x0 + 64); from the wrapped box at the edges
-        const bool hside = lane == 31 ? eedge : wedge;
-        const int hb = hside ? FW_OSF + (lane == 31 ? 0 : FW_H - 1) : (lane == 31 ? FW_H + FW_W : FW_H - 1);
-        const int hs = hside ? FW_H : FW_SC;
-        const int hT = hside ? FW_OST + (lane == 31 ? 0 : FW_H - 1) : FW_OT + (lane == 31 ? FW_H + FW_W : FW_H - 1);
+        // lane 31 the east one (x0 + 64); at the periodic edges of the domain
+        // the wrapped box's column is moved into that place first
+        const int hb = lane == 31 ? FW_H + FW_W : FW_H - 1;
         const uint32_t bytes = FW_BYTES + ((wedge || eedge) ? FW_SIDE_BYTES : 0u) + p.tx_pad;
-        // row r = ys - 1 + o is staged if the sweep reads it
+        // row r = ys - 1 + o is staged if the sweep reads it: every o < nit
+        // if periodic in y (r wrapped), else those of rows 0 .. nf - 1
+        const int kfirst = (!py && ys == 0) ? 1 : 0, klast = (!py && ye == nf) ? nit - 2 : nit - 1;
         auto staged = [&](int o, int &rr) {
             const int r = ys - 1 + o;
-            rr = r;
-            if (o >= nit) return false;
-            if (py) { rr = r < 0 ? r + nf : (r >= nf ? r - nf : r); return true; }
-            return r >= 0 && r < nf;
+            rr = r < 0 ? r + nf : (r >= nf ? r - nf : r);
+            return o >= kfirst && o <= klast;
         };
         // lane 0: stage row o into ring row s (its previous contents read)
         auto issue = [&](int o, int s) {
@@ -329,7 +320,18 @@ k_flow_wave(const __grid_constant__ CUtensorMap map_f, const __grid_constant__ C
             }
             __syncwarp();  // ring row sn (ordinal k - 1) is read
             issue(k + 2, sn);
-            const float *sr = ring + s * FW_SLOT;
+            float *const sr = ring + s * FW_SLOT;
+            if (ld && (wedge || eedge)) {
+                // the wrapped halo column into its place in the main box (whose
+                // copy read zeros there): lane 0 west, lane 31 east
+                if (lane == (wedge ? 0 : 31)) {
+                    const int to = wedge ? FW_H - 1 : FW_H + FW_W, from = wedge ? FW_H - 1 : 0;
+                    #pragma unroll
+                    for (int i = 0; i < 9; i++) sr[i * FW_SC + to] = sr[FW_OSF + i * FW_H + from];
+                    sr[FW_OT + to] = sr[FW_OST + from];
+                }
+                __syncwarp();
+            }
             float2 Pn, Wn, En, Dn = f2(0.0f);
             if (ld) {
                 float2 gr[9];
@@ -340,10 +342,10 @@ k_flow_wave(const __grid_constant__ CUtensorMap map_f, const __grid_constant__ C
                           gr[8]);
                 float hg[9];
                 #pragma unroll
-                for (int i = 0; i < 9; i++) hg[i] = sr[hb + i * hs];
+                for (int i = 0; i < 9; i++) hg[i] = sr[hb + i * FW_SC];
                 const float hd = ((hg[0] + hg[1]) + (hg[2] + hg[3])) + ((hg[4] + hg[5]) + (hg[6] + hg[7])) + hg[8];
                 Pn = psi_pair(K, add2(Dn, K.rho0), add2(Tr, K.tsat), errbits);
-                const float hp = psi_fast(p, hd + p.rho_shift, sr[hT] + p.T_sat, errbits);
+                const float hp = psi_fast(p, hd + p.rho_shift, sr[FW_OT + hb] + p.T_sat, errbits);
                 const float wn = __shfl_up_sync(FULL, Pn.y, 1), en = __shfl_down_sync(FULL, Pn.x, 1);
                 Wn = make_float2(lane == 0 ? hp : wn, Pn.x);
                 En = make_float2(Pn.y, lane == 31 ? hp : en);
@@ -395,9 +397,9 @@ k_flow_wave(const __grid_constant__ CUtensorMap map_f, const __grid_constant__ C
     if (errbits) atomicOr(err, errbits);
 }
 
-// Launch shape of k_flow_wave; domains it cannot take run k_flow_pers
-// (32 x 16-site tiles) instead.
-template <int WPB, int MINB>
+// Launch shape of k_flow_wave (U2: work units per resident warp, times
+// two); domains it cannot take run k_flow_pers (32 x 16-site tiles) instead.
+template <int WPB, int MINB, int U2>
 struct FlowWaveShape {
     using Fallback = FlowPersShape<PolicyF32, 32, 8, 2, 2>;
     static constexpr size_t smem_bytes = (size_t)WPB * FW_RS * FW_SLOT * sizeof(float) + 128;
@@ -419,12 +421,12 @@ struct FlowWaveShape {
         grid_blocks = sms * (per > 0 ? per : 1);
         return cudaSuccess;
     }
-    // strips of 64 columns x segments of at least 8 rows, about three units
+    // strips of 64 columns x segments of at least 8 rows, about U2 / 2 units
     // per resident warp (taken from the counter, so a warp that starts late
-    // takes fewer)
+    // takes fewer; longer segments re-read fewer rows at their ends)
     static void shape(const DevParams &p, int &nstrips, int &seg, int &nunits) {
         nstrips = p.nx / FW_W;
-        const long long want = 3LL * grid_blocks * WPB;
+        const long long want = (long long)U2 * grid_blocks * WPB / 2;
         int nseg = (int)std::max<long long>(1, want / nstrips);
         seg = std::max(8, (p.nf + nseg - 1) / nseg);
         nseg = (p.nf + seg - 1) / seg;
@@ -469,7 +471,7 @@ struct FlowWaveShape {
         return cudaGetLastError();
     }
 };
-template <int WPB, int MINB>
-int FlowWaveShape<WPB, MINB>::grid_blocks = 152;
+template <int WPB, int MINB, int U2>
+int FlowWaveShape<WPB, MINB, U2>::grid_blocks = 152;
 
 }  // namespace lbmgb

@@ -22,9 +22,9 @@ cudaError_t diag(const DevParams &p, const StepBuffers &b, int nblk, cudaStream_
 #define FLOWT(P, BY, RY, MB)                                                                      \
     {"flowtma_64x" #BY "x" #RY "_b" #MB, FlowTmaShape<P, BY, RY, MB>::launch, FlowTmaShape<P, BY, RY, MB>::blocks, \
      FlowTmaShape<P, BY, RY, MB>::prepare}
-#define FLOWW(WPB, MB)                                                                            \
-    {"flowwave_w" #WPB "_b" #MB, FlowWaveShape<WPB, MB>::launch, FlowWaveShape<WPB, MB>::blocks,       \
-     FlowWaveShape<WPB, MB>::prepare}
+#define FLOWW(WPB, MB, U2)                                                                        \
+    {"flowwave_w" #WPB "_b" #MB "_u" #U2, FlowWaveShape<WPB, MB, U2>::launch,                          \
+     FlowWaveShape<WPB, MB, U2>::blocks, FlowWaveShape<WPB, MB, U2>::prepare}
 #define HEATS(P, BW, BY, R, MB) \
     {"heatrows_" #BW "x" #BY "x" #R, HeatRowsShape<P, BW, BY, R, MB>::launch, HeatRowsShape<P, BW, BY, R, MB>::prepare}
 #define HEATSD(P, BW, BY, R, MB)                                                                 \
@@ -45,7 +45,7 @@ cudaError_t diag(const DevParams &p, const StepBuffers &b, int nblk, cudaStream_
 const FlowVariant flows32[] = {
     FLOWT(PolicyF32, 4, 2, 3), FLOWP(PolicyF32, 64, 4, 2, 2), FLOWP(PolicyF32, 32, 8, 2, 2),
     FLOWP(PolicyF32, 32, 8, 1, 3), FLOWV(PolicyF32, 32, 8, 2, 3), FLOWV(PolicyF32, 64, 4, 2, 3),
-    FLOWW(4, 3), FLOWW(4, 4),
+    FLOWW(4, 3, 6), FLOWW(4, 4, 6), FLOWW(4, 3, 8), FLOWW(4, 4, 8),
     FLOWM(PolicyF32),
 };
 const HeatVariant heats32[] = {

@@ -54,6 +54,7 @@ __device__ __forceinline__ uint64_t global_ns() {
 // bounded wait for phase `parity`: false once 100 ms (or 2^20 polls) have
 // passed without it
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;  // the usual case: no timer read
     const uint64_t t0 = global_ns();
     for (int it = 0; it < (1 << 20); it++) {
         if (mbar_try_wait(bar, parity)) return true;
