@@ -51,7 +51,7 @@ def peaks():
         return 6800.0, "fallback"
 
 
-KERNEL_SOURCES = ("lbm_device.cuh", "lbm_dfloat.cuh", "lbm_fast.cuh", "lbm_tma.cuh")
+KERNEL_SOURCES = ("lbm_device.cuh", "lbm_dfloat.cuh", "lbm_fast.cuh", "lbm_tma.cuh", "lbm_flowwave.cuh")
 FP64_SOURCES = ("lbm_device.cuh", "lbm_fp64.cu")  # the FP64 kernels and their launch shapes
 
 

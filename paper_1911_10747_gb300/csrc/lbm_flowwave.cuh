@@ -213,6 +213,162 @@ __device__ __forceinline__ void wave_collide(const FParams &p, const FlowWaveCon
     }
 }
 
+// A warp's ring of staged rows and the state of its copies.
+struct WaveRing {
+    float *ring;    // FW_RS rows of FW_SLOT floats, 128-byte aligned
+    uint64_t *bar;  // their mbarriers (one arrival: lane 0's, plus the bytes)
+    uint32_t ph;    // bit s: parity of ring row s's next completion
+    int busy;       // bit s: ring row s has copies nobody waited for
+    bool failed;    // a row wait ran out
+};
+
+// lane 0 initialises the warp's barriers
+__device__ __forceinline__ void wave_ring_init(WaveRing &w, float *ring, uint64_t *bar, int lane) {
+    w.ring = ring;
+    w.bar = bar;
+    w.ph = 0;
+    w.busy = 0;
+    w.failed = false;
+    if (lane == 0) {
+        #pragma unroll
+        for (int s = 0; s < FW_RS; s++) mbar_init(&bar[s], 1);
+        fence_proxy_async();  // the initialised barriers are visible to the copy engine
+    }
+    __syncwarp();
+}
+
+// after a wait ran out: let the copies still owed to the ring land before
+// its shared memory is released (each wait bounded)
+__device__ __forceinline__ void wave_ring_drain(WaveRing &w) {
+    #pragma unroll
+    for (int s = 0; s < FW_RS; s++)
+        if (w.busy & (1 << s)) mbar_wait(&w.bar[s], (w.ph >> s) & 1u);
+}
+
+// One work unit of one run: the 64-column strip at x0, rows ys .. ye - 1,
+// swept upward through the warp's ring; the mass and vapour count of the
+// collided sites are added to mass and nvap (FP32, per lane).
+__device__ __forceinline__ void wave_unit(const FParams &p, const FlowWaveConsts &K, const CUtensorMap *map_f,
+                                          const CUtensorMap *map_t, const CUtensorMap *map_fs,
+                                          const CUtensorMap *map_ts, int x0, int ys, int ye, float *const (&op)[9],
+                                          float *__restrict__ rho_o, float *__restrict__ ux_o,
+                                          float *__restrict__ uy_o, const double *__restrict__ cw, WaveRing &w,
+                                          int lane, float &mass, float &nvap, unsigned &errbits) {
+    const unsigned FULL = 0xffffffffu;
+    const int nx = p.nx, nf = p.nf, ns = p.ns;
+    const bool py = (p.flags & FLAG_PERIODIC_Y) != 0;
+    const bool outflow = p.top_mode == TOP_OUTFLOW;
+    const int po = FW_H + 2 * lane;  // this lane's pair in a staged array
+    const bool wedge = x0 == 0, eedge = x0 + FW_W == nx;
+    const int nit = ye - ys + 2;  // rows ys - 1 .. ye
+    const int c0 = x0 + 2 * lane, c1 = c0 + 1;
+    const int xw = c0 == 0 ? nx - 1 : c0 - 1, xe = c0 + 2 == nx ? 0 : c0 + 2;
+    // this lane's halo column in a staged row: the west one (x0 - 1), in
+    // lane 31 the east one (x0 + 64); at the periodic edges of the domain
+    // the wrapped box's column is moved into that place first
+    const int hb = lane == 31 ? FW_H + FW_W : FW_H - 1;
+    const uint32_t bytes = FW_BYTES + ((wedge || eedge) ? FW_SIDE_BYTES : 0u) + p.tx_pad;
+    // row r = ys - 1 + o is staged if the sweep reads it: every o < nit
+    // if periodic in y (r wrapped), else those of rows 0 .. nf - 1
+    const int kfirst = (!py && ys == 0) ? 1 : 0, klast = (!py && ye == nf) ? nit - 2 : nit - 1;
+    auto staged = [&](int o, int &rr) {
+        const int r = ys - 1 + o;
+        rr = r < 0 ? r + nf : (r >= nf ? r - nf : r);
+        return o >= kfirst && o <= klast;
+    };
+    // lane 0: stage row o into ring row s (its previous contents read)
+    auto issue = [&](int o, int s) {
+        int rr;
+        if (!staged(o, rr)) return;
+        w.busy |= 1 << s;
+        if (lane != 0) return;
+        float *dst = w.ring + s * FW_SLOT;
+        fence_proxy_async();  // the warp's earlier reads of this row come first
+        mbar_arrive_expect_tx(&w.bar[s], bytes);
+        tma_load_3d(dst, map_f, x0 - FW_H, rr, 0, &w.bar[s]);
+        tma_load_2d(dst + FW_OT, map_t, x0 - FW_H, ns + rr, &w.bar[s]);
+        if (wedge) {
+            tma_load_3d(dst + FW_OSF, map_fs, nx - FW_H, rr, 0, &w.bar[s]);
+            tma_load_2d(dst + FW_OST, map_ts, nx - FW_H, ns + rr, &w.bar[s]);
+        } else if (eedge) {
+            tma_load_3d(dst + FW_OSF, map_fs, 0, rr, 0, &w.bar[s]);
+            tma_load_2d(dst + FW_OST, map_ts, 0, ns + rr, &w.bar[s]);
+        }
+    };
+    __syncwarp();  // the previous unit's reads of the ring are done
+    issue(0, 0);
+    issue(1, 1);
+
+    float2 gp[9];  // populations of the row to collide next
+    // psi, west / east psi of the rows below it (m), of it (c), above it
+    // (n); the sum g (rho - rho0) of it and of the row just read
+    float2 Pm = f2(0.0f), Wm = f2(0.0f), Em = f2(0.0f), Pc = f2(0.0f), Wc = f2(0.0f), Ec = f2(0.0f);
+    float2 Dc = f2(0.0f);
+    int s = 0;  // ring row of ordinal k (k % 3)
+    for (int k = 0; k < nit; k++) {
+        const int r = ys - 1 + k;
+        const int sn = s == 0 ? FW_RS - 1 : s - 1;  // ring row of ordinals k - 1 and k + 2
+        int rr;
+        const bool ld = staged(k, rr);
+        if (ld) {
+            const bool ok = mbar_wait(&w.bar[s], (w.ph >> s) & 1u);
+            if (!__all_sync(FULL, ok)) {  // the row stays owed: drained below
+                w.failed = true;
+                break;
+            }
+            w.ph ^= 1u << s;
+            w.busy &= ~(1 << s);
+        }
+        __syncwarp();  // ring row sn (ordinal k - 1) is read
+        issue(k + 2, sn);
+        float *const sr = w.ring + s * FW_SLOT;
+        if (ld && (wedge || eedge)) {
+            // the wrapped halo column into its place in the main box (whose
+            // copy read zeros there): lane 0 west, lane 31 east
+            if (lane == (wedge ? 0 : 31)) {
+                const int to = wedge ? FW_H - 1 : FW_H + FW_W, from = wedge ? FW_H - 1 : 0;
+                #pragma unroll
+                for (int i = 0; i < 9; i++) sr[i * FW_SC + to] = sr[FW_OSF + i * FW_H + from];
+                sr[FW_OT + to] = sr[FW_OST + from];
+            }
+            __syncwarp();
+        }
+        float2 Pn, Wn, En, Dn = f2(0.0f);
+        if (ld) {
+            float2 gr[9];
+            #pragma unroll
+            for (int i = 0; i < 9; i++) gr[i] = *reinterpret_cast<const float2 *>(sr + i * FW_SC + po);
+            const float2 Tr = *reinterpret_cast<const float2 *>(sr + FW_OT + po);
+            Dn = add2(add2(add2(add2(gr[0], gr[1]), add2(gr[2], gr[3])), add2(add2(gr[4], gr[5]), add2(gr[6], gr[7]))),
+                      gr[8]);
+            float hg[9];
+            #pragma unroll
+            for (int i = 0; i < 9; i++) hg[i] = sr[hb + i * FW_SC];
+            const float hd = ((hg[0] + hg[1]) + (hg[2] + hg[3])) + ((hg[4] + hg[5]) + (hg[6] + hg[7])) + hg[8];
+            Pn = psi_pair(K, add2(Dn, K.rho0), add2(Tr, K.tsat), errbits);
+            const float hp = psi_fast(p, hd + p.rho_shift, sr[FW_OT + hb] + p.T_sat, errbits);
+            const float wn = __shfl_up_sync(FULL, Pn.y, 1), en = __shfl_down_sync(FULL, Pn.x, 1);
+            Wn = make_float2(lane == 0 ? hp : wn, Pn.x);
+            En = make_float2(Pn.y, lane == 31 ? hp : en);
+        } else if (r >= nf && outflow) {
+            Pn = Pc; Wn = Wc; En = Ec;  // open top: zero normal gradient
+        } else {
+            Pn = f2(0.0f); Wn = f2(0.0f); En = f2(0.0f);  // wall rows
+        }
+        if (k >= 2)
+            wave_collide(p, K, gp, Dc, Pc, Wc, Ec, Pm, Wm, Em, Pn, Wn, En, r - 1, py, outflow, c0, c1, xw, xe, cw,
+                         op, rho_o, ux_o, uy_o, mass, nvap, errbits);
+        if (ld && k >= 1 && k <= nit - 2) {
+            #pragma unroll
+            for (int i = 0; i < 9; i++) gp[i] = *reinterpret_cast<const float2 *>(sr + i * FW_SC + po);
+        }
+        Pm = Pc; Wm = Wc; Em = Ec;
+        Pc = Pn; Wc = Wn; Ec = En;
+        Dc = Dn;
+        s = s == FW_RS - 1 ? 0 : s + 1;
+    }
+}
+
 template <int WPB, int MINB>
 __global__ void __launch_bounds__(32 * WPB, MINB)
 k_flow_wave(const __grid_constant__ CUtensorMap map_f, const __grid_constant__ CUtensorMap map_t,
@@ -229,152 +385,28 @@ k_flow_wave(const __grid_constant__ CUtensorMap map_f, const __grid_constant__ C
     // shared-memory loads)
     float *const ring = reinterpret_cast<float *>(fw_raw) + ((128u - (smem_u32(fw_raw) & 127u)) & 127u) / 4u +
                         warp * (FW_RS * FW_SLOT);
-    uint64_t *const bar = fw_bar[warp];
-    const int nx = p.nx, nf = p.nf, ns = p.ns;
-    const size_t plane = (size_t)nf * nx;
+    const size_t plane = (size_t)p.nf * p.nx;
     float *op[9];
     #pragma unroll
     for (int i = 0; i < 9; i++) op[i] = fout + i * plane;
-    const bool py = (p.flags & FLAG_PERIODIC_Y) != 0;
-    const bool outflow = p.top_mode == TOP_OUTFLOW;
-    const int po = FW_H + 2 * lane;  // this lane's pair in a staged array
     unsigned errbits = 0;
     float mass = 0.0f, nvap = 0.0f;
-    if (lane == 0) {
-        #pragma unroll
-        for (int s = 0; s < FW_RS; s++) mbar_init(&bar[s], 1);
-        fence_proxy_async();  // the initialised barriers are visible to the copy engine
-    }
-    __syncwarp();
-    uint32_t ph = 0;      // bit s: parity of ring row s's next completion
-    bool failed = false;  // a row wait ran out
-    int busy = 0;         // bit s: ring row s has copies nobody waited for
-
+    WaveRing w;
+    wave_ring_init(w, ring, fw_bar[warp], lane);
     for (;;) {
         int u = 0;
         if (lane == 0) u = (int)atomicAdd(wq, 1u);
         u = __shfl_sync(FULL, u, 0);
         if (u >= nunits) break;
         const int strip = u % nstrips, sgi = u / nstrips;
-        const int x0 = strip * FW_W;
-        const bool wedge = x0 == 0, eedge = x0 + FW_W == nx;
-        const int ys = sgi * seg, ye = min(ys + seg, nf);
-        const int nit = ye - ys + 2;  // rows ys - 1 .. ye
-        const int c0 = x0 + 2 * lane, c1 = c0 + 1;
-        const int xw = c0 == 0 ? nx - 1 : c0 - 1, xe = c0 + 2 == nx ? 0 : c0 + 2;
-        // this lane's halo column in a staged row: the west one (x0 - 1), in
-        // lane 31 the east one (x0 + 64); at the periodic edges of the domain
-        // the wrapped box's column is moved into that place first
-        const int hb = lane == 31 ? FW_H + FW_W : FW_H - 1;
-        const uint32_t bytes = FW_BYTES + ((wedge || eedge) ? FW_SIDE_BYTES : 0u) + p.tx_pad;
-        // row r = ys - 1 + o is staged if the sweep reads it: every o < nit
-        // if periodic in y (r wrapped), else those of rows 0 .. nf - 1
-        const int kfirst = (!py && ys == 0) ? 1 : 0, klast = (!py && ye == nf) ? nit - 2 : nit - 1;
-        auto staged = [&](int o, int &rr) {
-            const int r = ys - 1 + o;
-            rr = r < 0 ? r + nf : (r >= nf ? r - nf : r);
-            return o >= kfirst && o <= klast;
-        };
-        // lane 0: stage row o into ring row s (its previous contents read)
-        auto issue = [&](int o, int s) {
-            int rr;
-            if (!staged(o, rr)) return;
-            busy |= 1 << s;
-            if (lane != 0) return;
-            float *dst = ring + s * FW_SLOT;
-            fence_proxy_async();  // the warp's earlier reads of this row come first
-            mbar_arrive_expect_tx(&bar[s], bytes);
-            tma_load_3d(dst, &map_f, x0 - FW_H, rr, 0, &bar[s]);
-            tma_load_2d(dst + FW_OT, &map_t, x0 - FW_H, ns + rr, &bar[s]);
-            if (wedge) {
-                tma_load_3d(dst + FW_OSF, &map_fs, nx - FW_H, rr, 0, &bar[s]);
-                tma_load_2d(dst + FW_OST, &map_ts, nx - FW_H, ns + rr, &bar[s]);
-            } else if (eedge) {
-                tma_load_3d(dst + FW_OSF, &map_fs, 0, rr, 0, &bar[s]);
-                tma_load_2d(dst + FW_OST, &map_ts, 0, ns + rr, &bar[s]);
-            }
-        };
-        __syncwarp();  // the previous unit's reads of the ring are done
-        issue(0, 0);
-        issue(1, 1);
-
-        float2 gp[9];  // populations of the row to collide next
-        // psi, west / east psi of the rows below it (m), of it (c), above it
-        // (n); the sum g (rho - rho0) of it and of the row just read
-        float2 Pm = f2(0.0f), Wm = f2(0.0f), Em = f2(0.0f), Pc = f2(0.0f), Wc = f2(0.0f), Ec = f2(0.0f);
-        float2 Dc = f2(0.0f);
-        int s = 0;  // ring row of ordinal k (k % 3)
-        for (int k = 0; k < nit; k++) {
-            const int r = ys - 1 + k;
-            const int sn = s == 0 ? FW_RS - 1 : s - 1;  // ring row of ordinals k - 1 and k + 2
-            int rr;
-            const bool ld = staged(k, rr);
-            if (ld) {
-                const bool ok = mbar_wait(&bar[s], (ph >> s) & 1u);
-                if (!__all_sync(FULL, ok)) {  // the row stays owed: drained below
-                    failed = true;
-                    break;
-                }
-                ph ^= 1u << s;
-                busy &= ~(1 << s);
-            }
-            __syncwarp();  // ring row sn (ordinal k - 1) is read
-            issue(k + 2, sn);
-            float *const sr = ring + s * FW_SLOT;
-            if (ld && (wedge || eedge)) {
-                // the wrapped halo column into its place in the main box (whose
-                // copy read zeros there): lane 0 west, lane 31 east
-                if (lane == (wedge ? 0 : 31)) {
-                    const int to = wedge ? FW_H - 1 : FW_H + FW_W, from = wedge ? FW_H - 1 : 0;
-                    #pragma unroll
-                    for (int i = 0; i < 9; i++) sr[i * FW_SC + to] = sr[FW_OSF + i * FW_H + from];
-                    sr[FW_OT + to] = sr[FW_OST + from];
-                }
-                __syncwarp();
-            }
-            float2 Pn, Wn, En, Dn = f2(0.0f);
-            if (ld) {
-                float2 gr[9];
-                #pragma unroll
-                for (int i = 0; i < 9; i++) gr[i] = *reinterpret_cast<const float2 *>(sr + i * FW_SC + po);
-                const float2 Tr = *reinterpret_cast<const float2 *>(sr + FW_OT + po);
-                Dn = add2(add2(add2(add2(gr[0], gr[1]), add2(gr[2], gr[3])), add2(add2(gr[4], gr[5]), add2(gr[6], gr[7]))),
-                          gr[8]);
-                float hg[9];
-                #pragma unroll
-                for (int i = 0; i < 9; i++) hg[i] = sr[hb + i * FW_SC];
-                const float hd = ((hg[0] + hg[1]) + (hg[2] + hg[3])) + ((hg[4] + hg[5]) + (hg[6] + hg[7])) + hg[8];
-                Pn = psi_pair(K, add2(Dn, K.rho0), add2(Tr, K.tsat), errbits);
-                const float hp = psi_fast(p, hd + p.rho_shift, sr[FW_OT + hb] + p.T_sat, errbits);
-                const float wn = __shfl_up_sync(FULL, Pn.y, 1), en = __shfl_down_sync(FULL, Pn.x, 1);
-                Wn = make_float2(lane == 0 ? hp : wn, Pn.x);
-                En = make_float2(Pn.y, lane == 31 ? hp : en);
-            } else if (r >= nf && outflow) {
-                Pn = Pc; Wn = Wc; En = Ec;  // open top: zero normal gradient
-            } else {
-                Pn = f2(0.0f); Wn = f2(0.0f); En = f2(0.0f);  // wall rows
-            }
-            if (k >= 2)
-                wave_collide(p, K, gp, Dc, Pc, Wc, Ec, Pm, Wm, Em, Pn, Wn, En, r - 1, py, outflow, c0, c1, xw, xe, cw,
-                             op, rho_o, ux_o, uy_o, mass, nvap, errbits);
-            if (ld && k >= 1 && k <= nit - 2) {
-                #pragma unroll
-                for (int i = 0; i < 9; i++) gp[i] = *reinterpret_cast<const float2 *>(sr + i * FW_SC + po);
-            }
-            Pm = Pc; Wm = Wc; Em = Ec;
-            Pc = Pn; Wc = Wn; Ec = En;
-            Dc = Dn;
-            s = s == FW_RS - 1 ? 0 : s + 1;
-        }
-        if (failed) break;
+        const int ys = sgi * seg;
+        wave_unit(p, K, &map_f, &map_t, &map_fs, &map_ts, strip * FW_W, ys, min(ys + seg, p.nf), op, rho_o, ux_o,
+                  uy_o, cw, w, lane, mass, nvap, errbits);
+        if (w.failed) break;
     }
-    if (failed) {
-        // let the copies still owed to this warp's ring land before its
-        // shared memory is released (each wait bounded)
+    if (w.failed) {
         errbits |= ERRW_TIMEOUT;
-        #pragma unroll
-        for (int s = 0; s < FW_RS; s++)
-            if (busy & (1 << s)) mbar_wait(&bar[s], (ph >> s) & 1u);
+        wave_ring_drain(w);
     }
     // per-warp mass and vapour count: FP32 inside the warp, FP64 across warps
     #pragma unroll

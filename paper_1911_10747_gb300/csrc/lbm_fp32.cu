@@ -36,17 +36,18 @@ cudaError_t diag(const DevParams &p, const StepBuffers &b, int nblk, cudaStream_
     {"heatwave_c" #CL "_w" #WPB "_b" #MB "_r" #RS, HeatWaveShape<P, CL, WPB, MB, RS>::launch, \
      HeatWaveShape<P, CL, WPB, MB, RS>::prepare}
 #define FLOWM(P) {"flowmulti_32x8x2", MultiKernels<P>::flow, MultiKernels<P>::flow_blocks, MultiKernels<P>::prepare}
+#define FLOWWM(P) {"flowwavemulti_w4_b3", MultiKernels<P>::wave, MultiKernels<P>::wave_blocks, MultiKernels<P>::prepare}
 #define HEATM(P) {"heatmulti_64x12x4", MultiKernels<P>::heat, MultiKernels<P>::prepare}
-#define MULTI(P) sizeof(MultiRun), fill_multi, multi_flow_tiles, multi_heat_tiles, MultiKernels<P>::launch
-#define NOMULTI 0, nullptr, nullptr, nullptr, nullptr
+#define MULTI(P) sizeof(MultiRun), fill_multi<P>, multi_flow_items<P>, multi_heat_tiles, multi_wave_ok<P>, MultiKernels<P>::launch
+#define NOMULTI 0, nullptr, nullptr, nullptr, nullptr, nullptr
 #define HEATV(P, TX, TY, BX, BY) \
     {"heat_" #TX "x" #TY "_t" #BX "x" #BY, HeatFastShape<P, TX, TY, BX, BY>::launch, HeatFastShape<P, TX, TY, BX, BY>::prepare}
 
 const FlowVariant flows32[] = {
     FLOWT(PolicyF32, 4, 2, 3), FLOWP(PolicyF32, 64, 4, 2, 2), FLOWP(PolicyF32, 32, 8, 2, 2),
     FLOWP(PolicyF32, 32, 8, 1, 3), FLOWV(PolicyF32, 32, 8, 2, 3), FLOWV(PolicyF32, 64, 4, 2, 3),
-    FLOWW(4, 3, 6), FLOWW(4, 4, 6), FLOWW(4, 3, 8), FLOWW(4, 4, 8),
-    FLOWM(PolicyF32),
+    FLOWW(4, 3, 8), FLOWW(4, 4, 8),
+    FLOWWM(PolicyF32), FLOWM(PolicyF32),
 };
 const HeatVariant heats32[] = {
     HEATS(PolicyF32, 64, 6, 5, 1), HEATS(PolicyF32, 64, 8, 4, 1), HEATS(PolicyF32, 64, 10, 3, 1),
@@ -66,9 +67,9 @@ const KernelSet ks32 = {"fp32", sizeof(float), sizeof(float), sizeof(float),
                         (int)(sizeof(flows32) / sizeof(flows32[0])), flows32,
                         (int)(sizeof(heats32) / sizeof(heats32[0])), heats32, diag<PolicyF32>,
                         launch_init<PolicyF32>, launch_import<PolicyF32>, launch_export<PolicyF32>, MULTI(PolicyF32)};
-// (the multi-run flow variant, listed last, needs a run descriptor this set does not keep)
+// (the two multi-run flow variants, listed last, need a run descriptor this set does not keep)
 const KernelSet ks32df = {"fp32dfsrc", sizeof(float), sizeof(float), sizeof(float),
-                          (int)(sizeof(flows32) / sizeof(flows32[0])) - 1, flows32,
+                          (int)(sizeof(flows32) / sizeof(flows32[0])) - 2, flows32,
                           (int)(sizeof(heats32df) / sizeof(heats32df[0])), heats32df, diag<PolicyF32>,
                           launch_init<PolicyF32>, launch_import<PolicyF32>, launch_export<PolicyF32>, NOMULTI};
 const KernelSet ks16 = {"fp16", sizeof(__half), sizeof(float), sizeof(float),

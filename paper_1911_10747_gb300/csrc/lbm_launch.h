@@ -103,17 +103,23 @@ struct KernelSet {
     cudaError_t (*export_fields)(const DevParams &, const StepBuffers &, double *rho, double *ux,
                                  double *uy, double *T, double *f, cudaStream_t);
     // Multi-run launches (one launch per kernel kind steps many runs over a
-    // work list of (run, tile)); multi_desc_bytes = 0 if the set has none.
+    // work list of (run, item)); multi_desc_bytes = 0 if the set has none.
     size_t multi_desc_bytes;
     // a run's descriptor (host memory `out`) for its buffers of parity 0 / 1,
-    // the parity of its state at phase 0, and its first tiles in the launch
-    void (*multi_fill)(const DevParams &, const StepBuffers &b0, const StepBuffers &b1, int parity, int flow_tile0,
-                       int heat_tile0, void *out);
-    int (*multi_flow_tiles)(const DevParams &);
+    // the parity of its state at phase 0 of the launches, its flow mode (0:
+    // 32 x 16-site tiles; 1: wavefront units, for runs multi_wave_ok accepts)
+    // and its first flow items and heat tiles in the launches
+    void (*multi_fill)(const DevParams &, const StepBuffers &b0, const StepBuffers &b1, int parity, int mode,
+                       int flow0, int heat_tile0, void *out);
+    int (*multi_flow_items)(const DevParams &, int mode);
     int (*multi_heat_tiles)(const DevParams &);
-    // kind 0 flow, 1 heat, 2 diagnostics over nruns descriptors (device), tiles of that kind in total
-    cudaError_t (*multi_launch)(int kind, const void *desc, int nruns, int tiles, int phase, unsigned *errw,
-                                cudaStream_t);
+    int (*multi_wave_ok)(const DevParams &);
+    // kind 0 flow (tiles), 1 heat, 2 diagnostics, 3 flow (wavefront units)
+    // over nruns descriptors (device), items of that kind in total; errw: the
+    // launches' error word; wq: two words, zero between launches, for the
+    // wavefront launches' work counter
+    cudaError_t (*multi_launch)(int kind, const void *desc, int nruns, int items, int phase, unsigned *errw,
+                                unsigned *wq, cudaStream_t);
 };
 
 // Message returned by lbm_last_error(NULL) (thread-local).

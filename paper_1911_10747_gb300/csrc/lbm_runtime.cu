@@ -425,7 +425,7 @@ int lbm_create(const lbm_domain_t *domain, const lbm_heater_t *heater, const lbm
         const size_t db = h->ks->multi_desc_bytes;
         std::vector<char> hd(2 * db);
         for (int par = 0; par < 2; par++)
-            h->ks->multi_fill(h->p, buffers(h, 0), buffers(h, 1), par, 0, 0, hd.data() + par * db);
+            h->ks->multi_fill(h->p, buffers(h, 0), buffers(h, 1), par, 0, 0, 0, hd.data() + par * db);
         if ((e = cudaMemcpyAsync(h->mdesc, hd.data(), 2 * db, cudaMemcpyHostToDevice, h->stream)) != cudaSuccess ||
             (e = cudaStreamSynchronize(h->stream)) != cudaSuccess) {
             cuda_fail(h, e, "run descriptors");
@@ -765,10 +765,13 @@ int lbm_kernels_per_step(lbm_handle h) { return h ? 3 : 0; }
 // ---- batches of runs ---------------------------------------------------------
 // Runs of one kernel set that has multi-run kernels are stepped together:
 // per step one flow, one heat and one diagnostics launch over all their
-// tiles.  The other runs of a batch are stepped by their own kernels, one
-// concurrent branch per run.
+// work items -- one group for the runs that take the wavefront flow kernel
+// and one for the others.  The other runs of a batch are stepped by their
+// own kernels, one concurrent branch per run.
 struct MultiGroup {
     const KernelSet *ks = nullptr;
+    int mode = 0;                   // flow work items: 0 tiles, 1 wavefront units
+    unsigned *wq = nullptr;         // 2 words: the wavefront launches' work counter
     std::vector<int> idx;           // positions in the batch's run list
     void *desc = nullptr;           // device descriptors, in idx order
     std::vector<char> host;         // their host image
@@ -804,6 +807,7 @@ static void batch_free(lbm_batch_s *b) {
     if (b->fork) cudaEventDestroy(b->fork);
     for (auto &g : b->groups) {
         if (g.desc) cudaFree(g.desc);
+        if (g.wq) cudaFree(g.wq);
         for (cudaEvent_t ev : {g.ev_heat, g.ev_diag, g.xev_heat, g.xev_diag})
             if (ev) cudaEventDestroy(ev);
         for (cudaStream_t st : {g.gs, g.gd})
@@ -827,8 +831,8 @@ static int batch_fill_groups(lbm_batch_s *b) {
         int f0 = 0, h0 = 0;
         for (size_t k = 0; k < g.idx.size(); k++) {
             lbm_run *h = b->runs[g.idx[k]];
-            g.ks->multi_fill(h->p, buffers(h, 0), buffers(h, 1), h->parity, f0, h0, g.host.data() + k * db);
-            f0 += g.ks->multi_flow_tiles(h->p);
+            g.ks->multi_fill(h->p, buffers(h, 0), buffers(h, 1), h->parity, g.mode, f0, h0, g.host.data() + k * db);
+            f0 += g.ks->multi_flow_items(h->p, g.mode);
             h0 += g.ks->multi_heat_tiles(h->p);
         }
         g.flow_tiles = f0;
@@ -860,12 +864,14 @@ static cudaError_t batch_groups_step(lbm_batch_s *b, int phase, bool first, bool
         } else if (fp16 && (e = cudaStreamWaitEvent(g.gs, ev_diag, 0)) != cudaSuccess) {
             return e;
         }
-        if ((e = g.ks->multi_launch(0, g.desc, n, g.flow_tiles, phase, b->errw, g.gs)) != cudaSuccess) return e;
+        if ((e = g.ks->multi_launch(g.mode == 1 ? 3 : 0, g.desc, n, g.flow_tiles, phase, b->errw, g.wq, g.gs)) !=
+            cudaSuccess)
+            return e;
         if (!first && !fp16 && (e = cudaStreamWaitEvent(g.gs, ev_diag, 0)) != cudaSuccess) return e;
-        if ((e = g.ks->multi_launch(1, g.desc, n, g.heat_tiles, phase, b->errw, g.gs)) != cudaSuccess) return e;
+        if ((e = g.ks->multi_launch(1, g.desc, n, g.heat_tiles, phase, b->errw, g.wq, g.gs)) != cudaSuccess) return e;
         if ((e = cudaEventRecord(ev_heat, g.gs)) != cudaSuccess) return e;
         if ((e = cudaStreamWaitEvent(g.gd, ev_heat, 0)) != cudaSuccess) return e;
-        if ((e = g.ks->multi_launch(2, g.desc, n, 0, phase, b->errw, g.gd)) != cudaSuccess) return e;
+        if ((e = g.ks->multi_launch(2, g.desc, n, 0, phase, b->errw, g.wq, g.gd)) != cudaSuccess) return e;
         if ((e = cudaEventRecord(ev_diag, g.gd)) != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -945,17 +951,19 @@ int lbm_batch_create(const lbm_handle *runs, int32_t n, lbm_batch *out) {
         b->in_group.push_back(false);
     }
     // runs whose kernel set has multi-run kernels are stepped per kernel set
-    // in one launch per kernel kind
+    // and flow mode in one launch per kernel kind
     for (int i = 0; i < n; i++) {
         const KernelSet *ks = b->runs[i]->ks;
         if (ks->multi_desc_bytes == 0) continue;
+        const int mode = ks->multi_wave_ok(b->runs[i]->p) ? 1 : 0;
         MultiGroup *g = nullptr;
         for (auto &q : b->groups)
-            if (q.ks == ks) g = &q;
+            if (q.ks == ks && q.mode == mode) g = &q;
         if (!g) {
             b->groups.emplace_back();
             g = &b->groups.back();
             g->ks = ks;
+            g->mode = mode;
         }
         g->idx.push_back(i);
         b->in_group[i] = true;
@@ -971,6 +979,9 @@ int lbm_batch_create(const lbm_handle *runs, int32_t n, lbm_batch *out) {
     for (auto &g : b->groups) {
         g.host.resize(g.idx.size() * g.ks->multi_desc_bytes);
         if (e == cudaSuccess) e = cudaMalloc(&g.desc, g.host.size());
+        if (e == cudaSuccess) e = cudaMalloc(&g.wq, 2 * sizeof(unsigned));
+        if (e == cudaSuccess) e = cudaMemsetAsync(g.wq, 0, 2 * sizeof(unsigned), b->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&g.gs, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&g.gd, cudaStreamNonBlocking);
         for (cudaEvent_t *ev : {&g.ev_heat, &g.ev_diag, &g.xev_heat, &g.xev_diag})

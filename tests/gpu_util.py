@@ -36,3 +36,18 @@ def field_errors(g, o):
         "T": rel_err(fg["T"], o.T),
         "f": rel_err(fg["f"], fo, fscale),
     }
+
+
+def select_multi(run):
+    """Select the multi-run kernels as the run's own launch shapes: the
+    kernels a batch steps it with (FP32 and FP16 storage; the wavefront flow
+    variant takes runs whose width is a multiple of 64, at least 128, and
+    runs the tiles otherwise, as a batch does).  Other precisions keep
+    theirs."""
+    v = run.variants()
+    for name in ("flowwavemulti_w4_b3", "flowmulti_32x8x2"):
+        if name in v["flow"]:
+            run.select_variants(v["flow"].index(name), v["heat"].index("heatmulti_64x12x4"))
+            break
+    return run
+

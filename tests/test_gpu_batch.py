@@ -2,8 +2,10 @@
 batch (different sizes, precisions and bottom modes), bitwise; the FP64
 members, a sweep-drawn one among them, match the oracle.  A batch steps its
 FP32 and FP16 runs with the multi-run kernels (one launch per kernel kind
-over a work list of (run, tile)); a run stepped alone with those kernels
-(the "multi" launch-shape variants) gives bit for bit the same."""
+over a work list of (run, tile), the FP32 runs whose width is a multiple of
+64 with the wavefront flow over (run, unit)); a run stepped alone with
+those kernels (the "multi" launch-shape variants) gives bit for bit the
+same."""
 import numpy as np
 import pytest
 
@@ -35,12 +37,8 @@ def mixed_configs():
 
 
 def multi(run):
-    """Select the multi-run kernels as the run's own launch shapes (FP32 and
-    FP16 storage; other precisions keep theirs)."""
-    v = run.variants()
-    if "flowmulti_32x8x2" in v["flow"]:
-        run.select_variants(v["flow"].index("flowmulti_32x8x2"), v["heat"].index("heatmulti_64x12x4"))
-    return run
+    from gpu_util import select_multi
+    return select_multi(run)
 
 
 def test_results_alone_and_in_a_batch_are_identical():
@@ -103,7 +101,8 @@ def test_multi_run_variants_agree_with_the_single_run_kernels_and_the_oracle():
     """The multi-run kernels do the single-run kernels' per-site arithmetic:
     against the oracle within the FP32 bounds, on a ragged domain, model A
     with the sine bottom, an open top with the noisy bottom and a doubly
-    periodic box with heat."""
+    periodic box with heat, with the tiles and (widths of 128 and more in
+    strips of 64) with the wavefront units."""
     from gpu_util import field_errors
     cases = [W.small_parity(precision="fp32").replace(nx=70, nf=45, ns=5, liquid_rows=15, spot_x=(3, 40, 69),
                                                        spot_half_width=2, rho_mean=2.3),
@@ -112,7 +111,14 @@ def test_multi_run_variants_agree_with_the_single_run_kernels_and_the_oracle():
                                                        rho_mean=2.3),
              W.small_parity(precision="fp32").replace(nx=40, nf=33, ns=4, liquid_rows=11, top_mode="outflow",
                                                        bc_mode="noise", spot_x=(), c_w_spot=(), rho_mean=2.3),
-             W.periodic_box(64, 40, liquid_rows=13, init_noise=1e-3, isothermal=False, precision="fp32")]
+             W.periodic_box(64, 40, liquid_rows=13, init_noise=1e-3, isothermal=False, precision="fp32"),
+             # wavefront units: several strips, spots on a strip edge, the
+             # segment ends of a 45-row domain; an open top; a periodic box
+             W.small_parity(precision="fp32").replace(nx=192, nf=45, ns=5, liquid_rows=15, spot_x=(3, 64, 191),
+                                                       spot_half_width=2, rho_mean=2.3),
+             W.small_parity(precision="fp32").replace(nx=128, nf=37, ns=4, liquid_rows=12, top_mode="outflow",
+                                                       bc_mode="noise", spot_x=(), c_w_spot=(), rho_mean=2.3),
+             W.periodic_box(128, 30, liquid_rows=10, init_noise=1e-3, isothermal=False, precision="fp32")]
     for cfg in cases:
         o = O.OracleRun(cfg)
         o.step(60)

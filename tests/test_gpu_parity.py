@@ -189,7 +189,7 @@ def test_fp64_parity_sessile_drop_from_set_state():
     assert all(v <= TOL64 for v in errs.values()), errs
 
 
-@pytest.mark.parametrize("variant", ["flowtma_64x4x2_b3", "flowwave_w4_b4_u6"])
+@pytest.mark.parametrize("variant", ["flowtma_64x4x2_b3", "flowwave_w4_b4_u8"])
 def test_staged_copy_wait_that_runs_out_is_reported_and_the_context_survives(monkeypatch, variant):
     """The flow kernels that stage rows or tiles by tensor copies bound their
     waits on the copy barriers.  The test hook makes each stage expect 16

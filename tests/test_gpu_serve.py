@@ -39,10 +39,8 @@ def alone(cfg, steps):
     """The request stepped by itself.  The request loop steps its runs in
     batches, and a batch steps FP32 and FP16 runs with the multi-run kernels,
     so the run alone uses those kernels too (its "multi" launch shapes)."""
-    r = lbm.Run(cfg)
-    v = r.variants()
-    if "flowmulti_32x8x2" in v["flow"]:
-        r.select_variants(v["flow"].index("flowmulti_32x8x2"), v["heat"].index("heatmulti_64x12x4"))
+    from gpu_util import select_multi
+    r = select_multi(lbm.Run(cfg))
     r.step(steps)
     f = r.fields(("rho", "T"))
     return r.series(steps - 1, 1)[0], f["rho"], f["T"]
