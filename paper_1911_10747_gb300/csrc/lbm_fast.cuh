@@ -957,6 +957,12 @@ __device__ __forceinline__ void cp_async4(float *dst, const float *src, bool pre
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sa), "l"(src), "r"(pred ? 4 : 0) : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+// 16-byte global -> shared copy (zero-filled and not read when !pred; src
+// must still be a valid, 16-byte aligned address)
+__device__ __forceinline__ void cp_async16z(float *dst, const float *src, bool pred) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(src), "r"(pred ? 16 : 0) : "memory");
+}
 
 // DF: the phase-change source of Eq. 24 in double-float arithmetic (the
 // rho-only EOS factors, 1 / (rho c), div u and C1, C2 once per step; C1 T +
@@ -1291,7 +1297,11 @@ int HeatRowsShape<P, BW, BY, R, MINB, DF>::grid_blocks = 152;
 // (below end) of a run: a persistent block of a single-run launch, or a
 // block's contiguous share of a run in a multi-run launch; p may live in the
 // constant bank or in shared memory.
-template <class P, int BY, int R, bool WIDE>
+// RAW: the next tile's T, rho, u_x, u_y arrive as whole rows in 16-byte
+// cp.async chunks (four per row and array per thread pair of passes)
+// instead of one 4-byte copy per cell and array; needs nx a multiple of 4
+// and at least 64.
+template <class P, int BY, int R, bool WIDE, bool RAW = false>
 __device__ __forceinline__ void
 heat_pair_body(const FParams &p, int tiles_x, int end, int first, int step, const typename P::tst *__restrict__ Tin,
                typename P::tst *__restrict__ Tout, const float *__restrict__ rho_i, const float *__restrict__ ux_i,
@@ -1301,7 +1311,7 @@ heat_pair_body(const FParams &p, int tiles_x, int end, int first, int step, cons
     // 1/lambda, u_x, u_y of the tile for the coefficient pass; afterwards the
     // same arrays (and gV) stage the next tile's raw T, rho, u_x, u_y, each
     // slot written and read by its owning thread only
-    __shared__ float2 sL[SH][NSL], sU[SH][NSL], sV[SH][NSL], gV[SH][NSL];
+    __shared__ __align__(16) float2 sL[SH][NSL], sU[SH][NSL], sV[SH][NSL], gV[SH][NSL];
     const int tx = threadIdx.x, ty = threadIdx.y, y0 = R * ty;
     const int so = tx, sl = (tx + HW - 1) & (HW - 1), sr = (tx + 1) & (HW - 1);  // own, west, east slots
     const bool wrap_w = tx == 0, wrap_e = tx == HW - 1;  // lanes whose west / east pair is the wrapped one
@@ -1328,6 +1338,36 @@ heat_pair_body(const FParams &p, int tiles_x, int end, int first, int step, cons
         pxa = xa;
         pxb = xb;
         pk = 0;
+        if constexpr (RAW) {
+            static_assert(R % 2 == 0 && WIDE, "whole-row staging: even strips, one column wrap");
+            // this thread's chunks: column chunk q of rows tid / 16 + 2 BY h
+            const int tid = ty * 32 + tx, q = tid & 15;
+            int col = x0 - H + 4 * q;
+            col = col < 0 ? col + nx : (col >= nx ? col - nx : col);
+            #pragma unroll
+            for (int h = 0; h < R / 2; h++) {
+                const int hr = (tid >> 4) + 2 * BY * h;  // tile row
+                int row = r0 + hr - H, k;
+                if (I) k = HK_FLUID;
+                else if (py) { row = row < 0 ? row + nt : (row >= nt ? row - nt : row); k = HK_FLUID; }
+                else if (row < 0 || row > nt) k = HK_OUT;
+                else if (row == 0) k = HK_BOTTOM;
+                else if (row == nt) k = HK_GHOST;
+                else k = (row < ns) ? HK_SOLID : HK_FLUID;
+                const bool inT = k == HK_SOLID || k == HK_FLUID, fl = k == HK_FLUID, gh = k == HK_GHOST;
+                const bool wa = k == HK_BOTTOM && model_a;
+                const int kt = inT ? row * nx + col : 0;
+                const int kf = fl ? kt - ns * nx : (gh ? (nt - ns - 1) * nx + col : (wa ? col : 0));
+                float *dT = reinterpret_cast<float *>(&sL[0][0]) + hr * BW + 4 * q;
+                float *dR = reinterpret_cast<float *>(&sU[0][0]) + hr * BW + 4 * q;
+                float *dX = reinterpret_cast<float *>(&sV[0][0]) + hr * BW + 4 * q;
+                float *dY = reinterpret_cast<float *>(&gV[0][0]) + hr * BW + 4 * q;
+                cp_async16z(dT, Tin + kt, inT);
+                cp_async16z(dR, rho_i + kf, fl || gh || wa);
+                cp_async16z(dX, ux_i + kf, fl);
+                cp_async16z(dY, uy_i + kf, fl);
+            }
+        }
         #pragma unroll
         for (int c = 0; c < R; c++) {
             int row = r0 + y0 + c - H, k;
@@ -1338,6 +1378,7 @@ heat_pair_body(const FParams &p, int tiles_x, int end, int first, int step, cons
             else if (row == nt) k = HK_GHOST;
             else k = (row < ns) ? HK_SOLID : HK_FLUID;
             pk |= k << (3 * c);
+            if constexpr (RAW) continue;  // (the rows were staged above)
             const bool inT = k == HK_SOLID || k == HK_FLUID, fl = k == HK_FLUID, gh = k == HK_GHOST;
             const bool wa = k == HK_BOTTOM && model_a;  // Model A wall row: rho of the first fluid row
             const int kta = inT ? row * nx + xa : 0, ktb = inT ? row * nx + xb : 0;
@@ -1390,12 +1431,31 @@ heat_pair_body(const FParams &p, int tiles_x, int end, int first, int step, cons
         auto prepare = [&](auto itag) {
         constexpr bool I = decltype(itag)::value;
         int kd[R];
-        float2 irc[R], rho[R], ux[R], uy[R], lam[R];
+        float2 irc[R], rho[R], ux[R], uy[R], lam[R], Tw[R];
         cp_async_wait_all();
+        if constexpr (RAW) {
+            __syncthreads();  // every thread's chunks have landed
+            const float *rT = reinterpret_cast<const float *>(&sL[0][0]), *rR = reinterpret_cast<const float *>(&sU[0][0]);
+            const float *rX = reinterpret_cast<const float *>(&sV[0][0]), *rY = reinterpret_cast<const float *>(&gV[0][0]);
+            #pragma unroll
+            for (int c = 0; c < R; c++) {
+                const int o = (y0 + c) * BW + tx;
+                Tw[c] = make_float2(rT[o], rT[o + HW]);
+                rho[c] = make_float2(rR[o], rR[o + HW]);
+                ux[c] = make_float2(rX[o], rX[o + HW]);
+                uy[c] = make_float2(rY[o], rY[o + HW]);
+            }
+            __syncthreads();  // read before the arrays take the coefficients
+        } else {
+            #pragma unroll
+            for (int c = 0; c < R; c++) {
+                Tw[c] = sL[y0 + c][so];
+                rho[c] = sU[y0 + c][so]; ux[c] = sV[y0 + c][so]; uy[c] = gV[y0 + c][so];
+            }
+        }
         #pragma unroll
         for (int c = 0; c < R; c++) {
-            const float2 Tr = sL[y0 + c][so];
-            rho[c] = sU[y0 + c][so]; ux[c] = sV[y0 + c][so]; uy[c] = gV[y0 + c][so];
+            const float2 Tr = Tw[c];
             const int k = I ? (int)HK_FLUID : (pk >> (3 * c)) & 7;
             kd[c] = k;
             float2 T = Tr, l = f2(0.0f), rc = f2(1.0f);
@@ -1427,18 +1487,23 @@ heat_pair_body(const FParams &p, int tiles_x, int end, int first, int step, cons
             west(sL, Ll);
             east(sL, Lr);
             const float2 Lb = sL[yb][so], Lt = sL[yt][so];
+            // the vertical link between rows c and c + 1 of the strip is the
+            // north link of one and the south link of the other: one reciprocal
+            float2 hN[R];
+            #pragma unroll
+            for (int c = 0; c < R; c++) hN[c] = rcp2(add2(lam[c], c + 1 < R ? lam[c + 1] : Lt));
+            const float2 hS0 = rcp2(add2(lam[0], Lb));
             #pragma unroll
             for (int c = 0; c < R; c++) {
                 const float2 l0 = lam[c];
-                const float2 lN = c + 1 < R ? lam[c + 1] : Lt, lS = c > 0 ? lam[c - 1] : Lb;
                 const int k = kd[c];
                 const bool moves = (k == HK_SOLID || k == HK_FLUID) && !iso;
                 const float2 f12 = moves ? mul2(f2(12.0f), irc[c]) : f2(0.0f);
                 const float2 cax = mul2(f2(w1), f12), cdg = mul2(f2(w2), f12);
                 kk[c][0] = mul2(cax, rcp2(add2(l0, Lr[c + 1])));
-                kk[c][1] = mul2(cax, rcp2(add2(l0, lN)));
+                kk[c][1] = mul2(cax, hN[c]);
                 kk[c][2] = mul2(cax, rcp2(add2(l0, Ll[c + 1])));
-                kk[c][3] = mul2(cax, rcp2(add2(l0, lS)));
+                kk[c][3] = mul2(cax, c > 0 ? hN[c - 1] : hS0);
                 kk[c][4] = mul2(cdg, rcp2(add2(l0, Lr[c + 2])));
                 kk[c][5] = mul2(cdg, rcp2(add2(l0, Ll[c + 2])));
                 kk[c][6] = mul2(cdg, rcp2(add2(l0, Ll[c])));
@@ -1579,23 +1644,24 @@ heat_pair_body(const FParams &p, int tiles_x, int end, int first, int step, cons
 }
 
 
-template <class P, int BY, int R, int MINB, bool WIDE>
+template <class P, int BY, int R, int MINB, bool WIDE, bool RAW = false>
 __global__ void __launch_bounds__(32 * BY, MINB)
 k_heat_pair(const __grid_constant__ FParams p, int tiles_x, int ntiles, const typename P::tst *__restrict__ Tin,
             typename P::tst *__restrict__ Tout, const float *__restrict__ rho_i, const float *__restrict__ ux_i,
             const float *__restrict__ uy_i, const long long *__restrict__ stepp, unsigned *__restrict__ err) {
-    heat_pair_body<P, BY, R, WIDE>(p, tiles_x, ntiles, (int)blockIdx.x, (int)gridDim.x, Tin, Tout, rho_i, ux_i, uy_i,
-                                   stepp, err);
+    heat_pair_body<P, BY, R, WIDE, RAW>(p, tiles_x, ntiles, (int)blockIdx.x, (int)gridDim.x, Tin, Tout, rho_i, ux_i,
+                                        uy_i, stepp, err);
 }
 
-template <class P, int BY, int R, int MINB>
+template <class P, int BY, int R, int MINB, bool RAW = false>
 struct HeatPairShape {
     static int grid_blocks;
     static cudaError_t prepare() {
         int dev = 0, sms = 0, per = 0;
         cudaError_t e = cudaGetDevice(&dev);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_heat_pair<P, BY, R, MINB, true>, 32 * BY, 0);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_heat_pair<P, BY, R, MINB, true, RAW>, 32 * BY, 0);
         if (e != cudaSuccess) return e;
         grid_blocks = sms * (per > 0 ? per : 1);
         return cudaSuccess;
@@ -1606,15 +1672,18 @@ struct HeatPairShape {
         const int ntiles = tx * ty;
         const int g = ntiles < grid_blocks ? ntiles : grid_blocks;
         const bool wide = p.nx >= 64 && (!(p.flags & FLAG_PERIODIC_Y) || p.nt >= R * BY);
-        auto k = wide ? k_heat_pair<P, BY, R, MINB, true> : k_heat_pair<P, BY, R, MINB, false>;
+        // whole-row staging: whole 16-byte chunks (nx a multiple of 4), one column wrap
+        auto k = (RAW && wide && p.nx % 4 == 0) ? k_heat_pair<P, BY, R, MINB, true, RAW>
+                 : wide                       ? k_heat_pair<P, BY, R, MINB, true>
+                                              : k_heat_pair<P, BY, R, MINB, false>;
         k<<<g, dim3(32, BY), 0, s>>>(
             make_fparams(p), tx, ntiles, (const typename P::tst *)b.T_in, (typename P::tst *)b.T_out,
             (const float *)b.rho, (const float *)b.ux, (const float *)b.uy, b.step, b.err);
         return cudaGetLastError();
     }
 };
-template <class P, int BY, int R, int MINB>
-int HeatPairShape<P, BY, R, MINB>::grid_blocks = 152;
+template <class P, int BY, int R, int MINB, bool RAW>
+int HeatPairShape<P, BY, R, MINB, RAW>::grid_blocks = 152;
 
 }  // namespace lbmgb
 

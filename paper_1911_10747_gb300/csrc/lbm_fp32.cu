@@ -32,6 +32,9 @@ cudaError_t diag(const DevParams &p, const StepBuffers &b, int nblk, cudaStream_
      HeatRowsShape<P, BW, BY, R, MB, true>::prepare}
 #define HEATP(P, BY, R, MB) \
     {"heatpair_64x" #BY "x" #R, HeatPairShape<P, BY, R, MB>::launch, HeatPairShape<P, BY, R, MB>::prepare}
+#define HEATP16(P, BY, R, MB)                                                                     \
+    {"heatpair16_64x" #BY "x" #R, HeatPairShape<P, BY, R, MB, true>::launch,                           \
+     HeatPairShape<P, BY, R, MB, true>::prepare}
 #define HEATW(P, CL, WPB, MB, RS) \
     {"heatwave_c" #CL "_w" #WPB "_b" #MB "_r" #RS, HeatWaveShape<P, CL, WPB, MB, RS>::launch, \
      HeatWaveShape<P, CL, WPB, MB, RS>::prepare}
@@ -53,7 +56,7 @@ const HeatVariant heats32[] = {
     HEATS(PolicyF32, 64, 6, 5, 1), HEATS(PolicyF32, 64, 8, 4, 1), HEATS(PolicyF32, 64, 10, 3, 1),
     HEATS(PolicyF32, 64, 6, 6, 1),
     HEATS(PolicyF32, 32, 8, 4, 2),
-    HEATP(PolicyF32, 12, 4, 1), HEATP(PolicyF32, 8, 4, 1),
+    HEATP(PolicyF32, 12, 4, 1), HEATP(PolicyF32, 8, 4, 1), HEATP16(PolicyF32, 12, 4, 1),
     HEATW(PolicyF32, 2, 2, 4, 8), HEATM(PolicyF32),
     HEATV(PolicyF32, 32, 16, 32, 8), HEATV(PolicyF32, 64, 32, 32, 16),
 };

@@ -213,17 +213,20 @@ def test_fp32_bulk_copy_flow_in_a_periodic_box():
     dict(nx=150, nf=45, ns=5, liquid_rows=15, spot_x=(3, 80, 149), spot_half_width=2),
     dict(nx=40, nf=33, ns=4, liquid_rows=11, top_mode="outflow", bc_mode="noise", spot_x=(), c_w_spot=()),
     dict(nx=96, nf=40, ns=0, liquid_rows=13, bc_mode="sine", spot_x=(), c_w_spot=()),
+    dict(nx=192, nf=45, ns=5, liquid_rows=15, spot_x=(3, 100, 191), spot_half_width=2),
+    dict(nx=128, nf=37, ns=4, liquid_rows=12, top_mode="outflow", bc_mode="noise", spot_x=(), c_w_spot=()),
 ])
 def test_fp32_paired_column_and_wavefront_heat_variants_against_the_oracle(kw):
-    """The heat kernels that hold two columns per thread as packed pairs and
-    the row-wavefront kernels (one warp per column strip): several tiles or
-    strips across with a ragged last one, a domain narrower than one tile or
-    strip (columns wrap inside it), model A, each bottom mode."""
+    """The heat kernels that hold two columns per thread as packed pairs (with
+    4-byte or whole-row 16-byte staging) and the row-wavefront kernels (one
+    warp per column strip): several tiles or strips across with a ragged
+    last one, a domain narrower than one tile or strip (columns wrap inside
+    it), model A, heater rows, an open top, each bottom mode."""
     cfg = W.small_parity(precision="fp32").replace(rho_mean=2.3, **kw)
     if cfg.bc_mode == "sine":
         cfg = cfg.replace(sine_t0=5, sine_t1=50, sine_wavelength=48.0)
     names = lbm.Run(cfg).variants()["heat"]
-    pair = [i for i, n in enumerate(names) if n.startswith(("heatpair_", "heatwave_"))]
+    pair = [i for i, n in enumerate(names) if n.startswith(("heatpair_", "heatpair16_", "heatwave_"))]
     assert pair
     o = O.OracleRun(cfg)
     o.step(60)
