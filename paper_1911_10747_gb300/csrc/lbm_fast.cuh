@@ -31,6 +31,7 @@ struct FParams {
     float s[9], hs[9];
     float c_w_top, vap_threshold;
     float lambda_s, cv_chi, c_v, rho_c_s;
+    float inv_c_v, inv_cv_chi;                     // 1 / c_v, 1 / (C_V chi)
     float a_kappa, kappa_over_Tc, B_coef;          // (dp/dT)_rho pieces: a kappa, kappa / Tc, (1 + kappa) / sqrt(Tc)
     float dTb, Tb_noise, sine_amp, sine_wl;        // bottom: T_b - T_sat, T_b A, amp Tc, wavelength
     unsigned tx_pad;                               // test hook of the staged-copy waits (0)
@@ -55,6 +56,7 @@ inline FParams make_fparams(const DevParams &p) {
     for (int k = 0; k < 9; k++) { q.s[k] = (float)p.s[k]; q.hs[k] = (float)p.hs[k]; }
     q.c_w_top = (float)p.c_w_top; q.vap_threshold = (float)p.vap_threshold;
     q.lambda_s = (float)p.lambda_s; q.cv_chi = (float)p.cv_chi; q.c_v = (float)p.c_v; q.rho_c_s = (float)p.rho_c_s;
+    q.inv_c_v = (float)(1.0 / p.c_v); q.inv_cv_chi = (float)(1.0 / p.cv_chi);
     q.a_kappa = (float)(p.a * p.kappa); q.kappa_over_Tc = (float)(p.kappa / p.Tc);
     q.B_coef = (float)((1.0 + p.kappa) / sqrt(p.Tc));
     q.dTb = (float)(p.T_b - p.T_sat); q.Tb_noise = (float)(p.T_b * p.bc_noise);
@@ -1458,9 +1460,16 @@ heat_pair_body(const FParams &p, int tiles_x, int end, int first, int step, cons
             const float2 Tr = Tw[c];
             const int k = I ? (int)HK_FLUID : (pk >> (3 * c)) & 7;
             kd[c] = k;
+            Tn[c] = Tr; Tc[c] = Tr;
+            if (k == HK_FLUID) {
+                // 1 / (rho c_v) and 1 / lambda = 1 / (C_V chi rho) from one reciprocal of rho
+                const float2 ir = rcp2(rho[c]);
+                irc[c] = mul2(ir, f2(p.inv_c_v));
+                lam[c] = mul2(ir, f2(p.inv_cv_chi));
+                continue;
+            }
             float2 T = Tr, l = f2(0.0f), rc = f2(1.0f);
             if (k == HK_SOLID) { l = f2(p.lambda_s); rc = f2(p.rho_c_s); }
-            else if (k == HK_FLUID) { l = mul2(f2(p.cv_chi), rho[c]); rc = mul2(rho[c], f2(p.c_v)); }
             else if (k == HK_BOTTOM) {
                 const long long n = *stepp;
                 T = make_float2(bottom_theta(p, pxa, n), bottom_theta(p, pxb, n));
