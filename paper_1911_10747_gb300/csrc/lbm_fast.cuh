@@ -1113,7 +1113,7 @@ k_heat_rows(const FParams p, int tiles_x, int ntiles, const typename P::tst *__r
             // advection (-u . grad T = sum_a adv_a T_a, adv_a = -3 w_a (e_a . u))
             // and the (dp/dT)_rho div u source of Eq. 24, with the Eq. 27 gradient
             float dd[R];
-            dfloat Dd[R];  // DF: the same divergence sum in double-float
+            [[maybe_unused]] dfloat Dd[R];  // DF: the same divergence sum in double-float
             const dfloat dw1 = {p.df_w1[0], p.df_w1[1]}, dw2 = {p.df_w2[0], p.df_w2[1]};
             auto ddiff = [](float a, float b) { return df_two_sum(a, -b); };  // a - b exactly
             {
@@ -1161,9 +1161,9 @@ k_heat_rows(const FParams p, int tiles_x, int ntiles, const typename P::tst *__r
                 const float iod = fast_rcp(omb * den);
                 const float pa = p.a_kappa * r * r * (omb * iod);
                 const float A = r * p.R * (den * iod) - pa * p.kappa_over_Tc;
-                const float B = pa * p.B_coef;
+                [[maybe_unused]] const float B = pa * p.B_coef;
                 const float g0 = -divu * irc[c];
-                const float C1 = g0 * A;
+                [[maybe_unused]] const float C1 = g0 * A;
                 if constexpr (DF) {
                     // (dp/dT)_rho = A + B / sqrt(T), C1 = -(3 D / (rho C_V)) A, C2 = -(3 D / (rho C_V)) B
                     const dfloat one = df_from(1.0f);

@@ -41,7 +41,7 @@ cudaError_t diag(const DevParams &p, const StepBuffers &b, int nblk, cudaStream_
 #define FLOWM(P) {"flowmulti_32x8x2", MultiKernels<P>::flow, MultiKernels<P>::flow_blocks, MultiKernels<P>::prepare}
 #define FLOWWM(P) {"flowwavemulti_w4_b3", MultiKernels<P>::wave, MultiKernels<P>::wave_blocks, MultiKernels<P>::prepare}
 #define HEATM(P) {"heatmulti_64x12x4", MultiKernels<P>::heat, MultiKernels<P>::prepare}
-#define MULTI(P) sizeof(MultiRun), fill_multi<P>, multi_flow_items<P>, multi_heat_tiles, multi_wave_ok<P>, MultiKernels<P>::launch
+#define MULTI(P) sizeof(MultiRun), fill_multi<P>, multi_flow_items<P>, multi_heat_tiles, multi_mode<P>, MultiKernels<P>::launch
 #define NOMULTI 0, nullptr, nullptr, nullptr, nullptr, nullptr
 #define HEATV(P, TX, TY, BX, BY) \
     {"heat_" #TX "x" #TY "_t" #BX "x" #BY, HeatFastShape<P, TX, TY, BX, BY>::launch, HeatFastShape<P, TX, TY, BX, BY>::prepare}

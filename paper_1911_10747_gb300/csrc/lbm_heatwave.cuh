@@ -104,7 +104,6 @@ k_heat_wave(const FParams p, const WaveConsts wk, int nstrips, int seg, int nuni
     const bool py = (p.flags & FLAG_PERIODIC_Y) != 0;
     const bool model_a = (p.flags & FLAG_MODEL_A) != 0;
     const bool iso = (p.flags & FLAG_ISOTHERMAL) != 0;
-    const float tsat = p.T_sat;
     const float irc_s = fast_rcp(p.rho_c_s);  // used on heater rows only
     // this lane's columns; the H columns at each side of the strip are halo
     int xc[CL];

@@ -106,16 +106,18 @@ struct KernelSet {
     // work list of (run, item)); multi_desc_bytes = 0 if the set has none.
     size_t multi_desc_bytes;
     // a run's descriptor (host memory `out`) for its buffers of parity 0 / 1,
-    // the parity of its state at phase 0 of the launches, its flow mode (0:
-    // 32 x 16-site tiles; 1: wavefront units, for runs multi_wave_ok accepts)
-    // and its first flow items and heat tiles in the launches
+    // the parity of its state at phase 0 of the launches, its launch mode (bit
+    // 0: wavefront flow units instead of 32 x 16-site tiles; bit 1: heat tiles
+    // staged as whole rows; multi_mode gives the bits a run can take) and its
+    // first flow items and heat tiles in the launches
     void (*multi_fill)(const DevParams &, const StepBuffers &b0, const StepBuffers &b1, int parity, int mode,
                        int flow0, int heat_tile0, void *out);
     int (*multi_flow_items)(const DevParams &, int mode);
     int (*multi_heat_tiles)(const DevParams &);
-    int (*multi_wave_ok)(const DevParams &);
-    // kind 0 flow (tiles), 1 heat, 2 diagnostics, 3 flow (wavefront units)
-    // over nruns descriptors (device), items of that kind in total; errw: the
+    int (*multi_mode)(const DevParams &);
+    // kind 0 flow (tiles), 1 heat, 2 diagnostics, 3 flow (wavefront units),
+    // 4 heat (whole-row staging; every run of the launch must take it) over
+    // nruns descriptors (device), items of that kind in total; errw: the
     // launches' error word; wq: two words, zero between launches, for the
     // wavefront launches' work counter
     cudaError_t (*multi_launch)(int kind, const void *desc, int nruns, int items, int phase, unsigned *errw,

@@ -136,18 +136,24 @@ k_flow_multi(const MultiRun *__restrict__ runs, int nruns, int total, int phase,
 }
 
 // ---- heat: one RK4 step over the paired-column tiles -------------------------
-template <class P>
+// ROWS: every run stages whole rows of the next tile (nx a multiple of 4 and
+// at least 64; if periodic in y, at least one tile of rows): a single
+// column wrap.  Otherwise the general column wrap serves runs of any width
+// (computed once per tile).  Both give the same results.
+template <class P, bool ROWS>
 __global__ void __launch_bounds__(32 * MR_HBY, 1)
 k_heat_multi(const MultiRun *__restrict__ runs, int nruns, int total, int phase, unsigned *__restrict__ errw) {
     __shared__ FParams sp;
     __shared__ int s_run[3];
     for_each_run_segment<1>(runs, nruns, total, errw, sp, s_run, [&](const MultiRun *run, const FParams &p, int lb, int le) {
         const StepBuffers &B = run->b[(run->parity + phase) & 1];
-        // the general column wrap serves runs of any width (computed once per tile)
-        heat_pair_body<P, MR_HBY, MR_HR, false>(p, run->heat_tiles_x, le, lb, 1, (const typename P::tst *)B.T_in,
-                                                (typename P::tst *)B.T_out, (const float *)B.rho, (const float *)B.ux,
-                                                (const float *)B.uy, B.step, B.err);
+        heat_pair_body<P, MR_HBY, MR_HR, ROWS, ROWS>(p, run->heat_tiles_x, le, lb, 1, (const typename P::tst *)B.T_in,
+                                                     (typename P::tst *)B.T_out, (const float *)B.rho,
+                                                     (const float *)B.ux, (const float *)B.uy, B.step, B.err);
     });
+}
+inline bool multi_heat_rows(const DevParams &p) {
+    return p.nx % 4 == 0 && p.nx >= 64 && (!(p.flags & FLAG_PERIODIC_Y) || p.nt >= MR_HR * MR_HBY);
 }
 
 // ---- diagnostics: one block per run ----------------------------------------
@@ -271,10 +277,15 @@ inline int multi_wave_ok(const DevParams &p) {
            tensor_map_encoder() != nullptr;
 }
 inline int multi_wave_units(const DevParams &p) { return (p.nx / FW_W) * ((p.nf + MR_WSEG - 1) / MR_WSEG); }
-// flow work items of a run: tiles (mode 0) or wavefront units (mode 1)
+// flow work items of a run: tiles, or wavefront units (mode bit 0)
 template <class P>
 inline int multi_flow_items(const DevParams &p, int mode) {
-    return mode == 1 && multi_wave_ok<P>(p) ? multi_wave_units(p) : multi_flow_tiles(p);
+    return (mode & 1) && multi_wave_ok<P>(p) ? multi_wave_units(p) : multi_flow_tiles(p);
+}
+// the run's launch mode: bit 0 wavefront flow, bit 1 whole-row heat staging
+template <class P>
+inline int multi_mode(const DevParams &p) {
+    return (multi_wave_ok<P>(p) ? 1 : 0) | (multi_heat_rows(p) ? 2 : 0);
 }
 
 // the tensor maps of the wavefront flow (see FlowWaveShape::launch)
@@ -325,7 +336,7 @@ inline void fill_multi(const DevParams &p, const StepBuffers &b0, const StepBuff
         // input of a run whose state is in parity 0
         if (!wave_maps(p, b0, m->wave_map[0]) || !wave_maps(p, b1, m->wave_map[1])) m->wave_ok = 0;
     }
-    const bool wave = mode == 1 && m->wave_ok;
+    const bool wave = (mode & 1) && m->wave_ok;
     m->flow_tile0 = wave ? 0 : flow0;
     m->wave_unit0 = wave ? flow0 : 0;
     m->nblk = wave ? m->wave_nunits : m->flow_ntiles;
@@ -344,7 +355,7 @@ struct MultiKernels {
         cudaError_t e = cudaGetDevice(&dev);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pf, k_flow_multi<P>, MR_FBX * MR_FBY, 0);
-        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ph, k_heat_multi<P>, 32 * MR_HBY, 0);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ph, k_heat_multi<P, false>, 32 * MR_HBY, 0);
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(k_flow_wave_multi<MR_WWPB, MR_WMINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)wave_smem);
@@ -357,7 +368,8 @@ struct MultiKernels {
         wave_grid = sms * (pw > 0 ? pw : 1);
         return cudaSuccess;
     }
-    // kind 0 flow (tiles), 1 heat, 2 diagnostics, 3 flow (wavefront units);
+    // kind 0 flow (tiles), 1 heat, 2 diagnostics, 3 flow (wavefront units),
+    // 4 heat (whole-row staging);
     // items = all runs' work items of that kind; errw: the launch's error
     // word (ERRW_DESC); wq: the wavefront launches' work counter
     static cudaError_t launch(int kind, const void *desc, int nruns, int tiles, int phase, unsigned *errw,
@@ -370,9 +382,10 @@ struct MultiKernels {
         } else if (kind == 0) {
             const int g = tiles < flow_grid ? tiles : flow_grid;
             k_flow_multi<P><<<g, dim3(MR_FBX, MR_FBY), 0, s>>>(d, nruns, tiles, phase, errw);
-        } else if (kind == 1) {
+        } else if (kind == 1 || kind == 4) {
             const int g = tiles < heat_grid ? tiles : heat_grid;
-            k_heat_multi<P><<<g, dim3(32, MR_HBY), 0, s>>>(d, nruns, tiles, phase, errw);
+            auto k = kind == 4 ? k_heat_multi<P, true> : k_heat_multi<P, false>;
+            k<<<g, dim3(32, MR_HBY), 0, s>>>(d, nruns, tiles, phase, errw);
         } else {
             k_diag_multi<P><<<nruns, 1024, 0, s>>>(d, phase, errw);
         }
@@ -385,7 +398,7 @@ struct MultiKernels {
         return launch(0, b.mdesc, 1, multi_flow_tiles(p), 0, b.err, b.wq, s);
     }
     static cudaError_t heat(const DevParams &p, const StepBuffers &b, cudaStream_t s) {
-        return launch(1, b.mdesc, 1, multi_heat_tiles(p), 0, b.err, b.wq, s);
+        return launch(multi_heat_rows(p) ? 4 : 1, b.mdesc, 1, multi_heat_tiles(p), 0, b.err, b.wq, s);
     }
     // the wavefront flow, for runs that can take it (else the tiles)
     static int wave_blocks(const DevParams &p) { return multi_flow_items<P>(p, 1); }

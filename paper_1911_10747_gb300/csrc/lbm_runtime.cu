@@ -765,12 +765,12 @@ int lbm_kernels_per_step(lbm_handle h) { return h ? 3 : 0; }
 // ---- batches of runs ---------------------------------------------------------
 // Runs of one kernel set that has multi-run kernels are stepped together:
 // per step one flow, one heat and one diagnostics launch over all their
-// work items -- one group for the runs that take the wavefront flow kernel
-// and one for the others.  The other runs of a batch are stepped by their
+// work items -- one group per launch mode (wavefront flow or tiles, heat
+// tiles staged as whole rows or cell by cell).  The other runs of a batch are stepped by their
 // own kernels, one concurrent branch per run.
 struct MultiGroup {
     const KernelSet *ks = nullptr;
-    int mode = 0;                   // flow work items: 0 tiles, 1 wavefront units
+    int mode = 0;                   // launch mode: bit 0 wavefront flow units, bit 1 whole-row heat staging
     unsigned *wq = nullptr;         // 2 words: the wavefront launches' work counter
     std::vector<int> idx;           // positions in the batch's run list
     void *desc = nullptr;           // device descriptors, in idx order
@@ -864,11 +864,13 @@ static cudaError_t batch_groups_step(lbm_batch_s *b, int phase, bool first, bool
         } else if (fp16 && (e = cudaStreamWaitEvent(g.gs, ev_diag, 0)) != cudaSuccess) {
             return e;
         }
-        if ((e = g.ks->multi_launch(g.mode == 1 ? 3 : 0, g.desc, n, g.flow_tiles, phase, b->errw, g.wq, g.gs)) !=
+        if ((e = g.ks->multi_launch((g.mode & 1) ? 3 : 0, g.desc, n, g.flow_tiles, phase, b->errw, g.wq, g.gs)) !=
             cudaSuccess)
             return e;
         if (!first && !fp16 && (e = cudaStreamWaitEvent(g.gs, ev_diag, 0)) != cudaSuccess) return e;
-        if ((e = g.ks->multi_launch(1, g.desc, n, g.heat_tiles, phase, b->errw, g.wq, g.gs)) != cudaSuccess) return e;
+        if ((e = g.ks->multi_launch((g.mode & 2) ? 4 : 1, g.desc, n, g.heat_tiles, phase, b->errw, g.wq, g.gs)) !=
+            cudaSuccess)
+            return e;
         if ((e = cudaEventRecord(ev_heat, g.gs)) != cudaSuccess) return e;
         if ((e = cudaStreamWaitEvent(g.gd, ev_heat, 0)) != cudaSuccess) return e;
         if ((e = g.ks->multi_launch(2, g.desc, n, 0, phase, b->errw, g.wq, g.gd)) != cudaSuccess) return e;
@@ -955,7 +957,7 @@ int lbm_batch_create(const lbm_handle *runs, int32_t n, lbm_batch *out) {
     for (int i = 0; i < n; i++) {
         const KernelSet *ks = b->runs[i]->ks;
         if (ks->multi_desc_bytes == 0) continue;
-        const int mode = ks->multi_wave_ok(b->runs[i]->p) ? 1 : 0;
+        const int mode = ks->multi_mode(b->runs[i]->p);
         MultiGroup *g = nullptr;
         for (auto &q : b->groups)
             if (q.ks == ks && q.mode == mode) g = &q;
