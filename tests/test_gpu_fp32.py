@@ -285,13 +285,15 @@ def test_fp32_heat_variants_in_a_periodic_box_with_heat(ny):
     dict(nx=128, nf=37, ns=4, liquid_rows=12, top_mode="outflow", bc_mode="noise", spot_x=(), c_w_spot=()),
     dict(nx=128, nf=40, ns=0, liquid_rows=13, bc_mode="sine", spot_x=(), c_w_spot=()),
     dict(nx=64, nf=200, ns=3, liquid_rows=60, spot_x=(0, 31, 63), spot_half_width=1),
+    dict(nx=256, nf=45, ns=5, liquid_rows=15, spot_x=(0, 127, 200), spot_half_width=2),
+    dict(nx=256, nf=37, ns=4, liquid_rows=12, top_mode="outflow", bc_mode="noise", spot_x=(), c_w_spot=()),
 ])
 def test_fp32_wavefront_flow_variants_against_the_oracle(kw):
     """The flow kernels in which each warp sweeps a 64-column strip up a
     segment of rows (nx a multiple of 64): several strips across with the
     periodic x edges, nucleate spots on a strip edge, an open top, model A
     with the sine bottom, and a tall single-strip domain cut into many
-    segments, against the oracle; and both wavefront shapes agree."""
+    segments, against the oracle; and the wavefront shapes agree."""
     cfg = W.small_parity(precision="fp32").replace(rho_mean=2.3, **kw)
     if cfg.bc_mode == "sine":
         cfg = cfg.replace(sine_t0=5, sine_t1=50, sine_wavelength=48.0)
@@ -310,15 +312,16 @@ def test_fp32_wavefront_flow_variants_against_the_oracle(kw):
         assert errs["rho"] < 1e-4 and errs["T"] < 1e-5, (names[fv], errs)
         assert g.mass() == pytest.approx(o.diagnostics()["mass"], rel=1e-6), names[fv]
         got.append(g.fields(("rho", "f")))
-    for k in got[0]:   # same per-site arithmetic whatever the launch shape
-        assert np.max(np.abs(got[0][k] - got[1][k])) <= 1e-5 * np.abs(got[0][k]).max(), k
+    for other in got[1:]:   # same per-site arithmetic whatever the launch shape
+        for k in got[0]:
+            assert np.max(np.abs(got[0][k] - other[k])) <= 1e-5 * np.abs(got[0][k]).max(), k
 
 
-@pytest.mark.parametrize("ny", [6, 70])
-def test_fp32_wavefront_flow_in_a_periodic_box(ny):
+@pytest.mark.parametrize("nx,ny", [(128, 6), (128, 70), (256, 40)])
+def test_fp32_wavefront_flow_in_a_periodic_box(nx, ny):
     """Periodic in y: the sweep's first and last rows wrap (6 rows: fewer
-    than one segment), against the oracle."""
-    cfg = W.periodic_box(128, ny, liquid_rows=max(1, ny // 3), init_noise=1e-3, precision="fp32")
+    than one segment), against the oracle, on one and on several strips."""
+    cfg = W.periodic_box(nx, ny, liquid_rows=max(1, ny // 3), init_noise=1e-3, precision="fp32")
     names = lbm.Run(cfg).variants()["flow"]
     o = O.OracleRun(cfg)
     o.step(40)
