@@ -49,7 +49,7 @@
 extern "C" {
 #endif
 
-#define LBM_ABI_VERSION 2
+#define LBM_ABI_VERSION 3
 
 enum lbm_status {
     LBM_OK = 0,
@@ -208,6 +208,14 @@ int lbm_fields(lbm_handle h, unsigned mask, double *const *dst, int dst_is_devic
  * describe the state before the import). */
 int lbm_set_state(lbm_handle h, const double *f, const double *T, int64_t step,
                   int src_is_device);
+
+/* lbm_set_state with float32 arrays (same layout, same semantics): half the
+ * bytes to move when the state comes from host memory.  The values are
+ * widened to float64 before the conversion to the run's storage, so a
+ * float32 array and the same values given as float64 to lbm_set_state give
+ * the same state bit for bit. */
+int lbm_set_state_f32(lbm_handle h, const float *f, const float *T, int64_t step,
+                      int src_is_device);
 
 /* Checkpoint: the state lbm_set_state takes back -- post-stream populations
  * f (9*NF*NX) and temperature T (NT*NX) as float64, and the step counter.

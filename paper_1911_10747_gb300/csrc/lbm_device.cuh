@@ -713,20 +713,26 @@ __global__ void k_init_state(const DevParams p, const typename P::real *__restri
     if (k < ntl) st_as(T + k, (typename P::real)(P::shifted ? 0.0 : p.T_sat));
 }
 
-// ---- state import / field export (float64 at the ABI) -----------------------
-template <class P>
-__global__ void k_import(const DevParams p, const double *__restrict__ f64, const double *__restrict__ T64,
+// ---- state import / field export (float64 at the ABI; float32 import too) --
+// In: the ABI arrays' type (double, or float for lbm_set_state_f32); the
+// shift to storage is taken in float64 either way, so a float32 array and
+// the same values widened to float64 import to the same storage.
+template <class P, class In = double>
+__global__ void k_import(const DevParams p, const In *__restrict__ f64, const In *__restrict__ T64,
                          typename P::fst *__restrict__ f, typename P::tst *__restrict__ T) {
     const size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     const size_t nfl = (size_t)p.nx * p.nf, ntl = (size_t)p.nx * p.nt;
     if (f64 && k < nfl) {
         #pragma unroll
         for (int i = 0; i < 9; i++) {
-            const double v = f64[i * nfl + k];
+            const double v = (double)f64[i * nfl + k];
             st_as(f + i * nfl + k, (typename P::real)(P::shifted ? v - wl<double>(i) * p.rho_shift : v));
         }
     }
-    if (T64 && k < ntl) st_as(T + k, (typename P::real)(P::shifted ? T64[k] - p.T_sat : T64[k]));
+    if (T64 && k < ntl) {
+        const double v = (double)T64[k];
+        st_as(T + k, (typename P::real)(P::shifted ? v - p.T_sat : v));
+    }
 }
 
 template <class P>
@@ -820,6 +826,13 @@ template <class P>
 cudaError_t launch_import(const DevParams &p, const double *f, const double *T, const StepBuffers &b, cudaStream_t s) {
     const size_t n = (size_t)p.nx * p.nt;
     k_import<P><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p, f, T, (typename P::fst *)b.f_out, (typename P::tst *)b.T_out);
+    return cudaGetLastError();
+}
+template <class P>
+cudaError_t launch_import32(const DevParams &p, const float *f, const float *T, const StepBuffers &b, cudaStream_t s) {
+    const size_t n = (size_t)p.nx * p.nt;
+    k_import<P, float><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p, f, T, (typename P::fst *)b.f_out,
+                                                                    (typename P::tst *)b.T_out);
     return cudaGetLastError();
 }
 

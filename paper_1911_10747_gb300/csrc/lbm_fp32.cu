@@ -41,8 +41,9 @@ cudaError_t diag(const DevParams &p, const StepBuffers &b, int nblk, cudaStream_
 #define FLOWM(P) {"flowmulti_32x8x2", MultiKernels<P>::flow, MultiKernels<P>::flow_blocks, MultiKernels<P>::prepare}
 #define FLOWWM(P) {"flowwavemulti_w4_b3", MultiKernels<P>::wave, MultiKernels<P>::wave_blocks, MultiKernels<P>::prepare}
 #define HEATM(P) {"heatmulti_64x12x4", MultiKernels<P>::heat, MultiKernels<P>::prepare}
-#define MULTI(P) sizeof(MultiRun), fill_multi<P>, multi_flow_items<P>, multi_heat_tiles, multi_mode<P>, MultiKernels<P>::launch
-#define NOMULTI 0, nullptr, nullptr, nullptr, nullptr, nullptr
+#define MULTI(P) sizeof(MultiRun), fill_multi<P>, multi_flow_items<P>, multi_heat_tiles, multi_mode<P>, MultiKernels<P>::launch, \
+    launch_import32<P>
+#define NOMULTI(P) 0, nullptr, nullptr, nullptr, nullptr, nullptr, launch_import32<P>
 #define HEATV(P, TX, TY, BX, BY) \
     {"heat_" #TX "x" #TY "_t" #BX "x" #BY, HeatFastShape<P, TX, TY, BX, BY>::launch, HeatFastShape<P, TX, TY, BX, BY>::prepare}
 
@@ -74,7 +75,7 @@ const KernelSet ks32 = {"fp32", sizeof(float), sizeof(float), sizeof(float),
 const KernelSet ks32df = {"fp32dfsrc", sizeof(float), sizeof(float), sizeof(float),
                           (int)(sizeof(flows32) / sizeof(flows32[0])) - 2, flows32,
                           (int)(sizeof(heats32df) / sizeof(heats32df[0])), heats32df, diag<PolicyF32>,
-                          launch_init<PolicyF32>, launch_import<PolicyF32>, launch_export<PolicyF32>, NOMULTI};
+                          launch_init<PolicyF32>, launch_import<PolicyF32>, launch_export<PolicyF32>, NOMULTI(PolicyF32)};
 const KernelSet ks16 = {"fp16", sizeof(__half), sizeof(float), sizeof(float),
                         (int)(sizeof(flows16) / sizeof(flows16[0])), flows16,
                         (int)(sizeof(heats16) / sizeof(heats16[0])), heats16, diag<PolicyF16>,

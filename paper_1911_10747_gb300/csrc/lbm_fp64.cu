@@ -15,7 +15,8 @@ cudaError_t no_prepare() { return cudaSuccess; }
 const FlowVariant flows[] = {{"flow64_32x8x2", Flow::launch, Flow::blocks, no_prepare}};
 const HeatVariant heats[] = {{"heat64_32x16_t256", Heat::launch, Heat::prepare}};
 const KernelSet ks = {"fp64", sizeof(double), sizeof(double), sizeof(double), 1, flows, 1, heats, diag,
-                      launch_init<P>, launch_import<P>, launch_export<P>, 0, nullptr, nullptr, nullptr, nullptr, nullptr};
+                      launch_init<P>, launch_import<P>, launch_export<P>, 0, nullptr, nullptr, nullptr, nullptr, nullptr,
+                      launch_import32<P>};
 }  // namespace
 const KernelSet *kernels_fp64() { return &ks; }
 }  // namespace lbmgb

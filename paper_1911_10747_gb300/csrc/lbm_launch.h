@@ -122,6 +122,9 @@ struct KernelSet {
     // wavefront launches' work counter
     cudaError_t (*multi_launch)(int kind, const void *desc, int nruns, int items, int phase, unsigned *errw,
                                 unsigned *wq, cudaStream_t);
+    // float32 post-stream f / T (device) -> storage, as import_state
+    cudaError_t (*import_state32)(const DevParams &, const float *f, const float *T, const StepBuffers &,
+                                  cudaStream_t);
 };
 
 // Message returned by lbm_last_error(NULL) (thread-local).

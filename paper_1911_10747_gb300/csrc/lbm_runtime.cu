@@ -245,14 +245,15 @@ static int fill_params(const lbm_domain_t *d, const lbm_heater_t *ht, const lbm_
 
 // Device address of page-locked host memory mapped for the current device,
 // or nullptr (pageable memory, or not a host pointer).
-static const double *host_alias(const double *p) {
+template <class V>
+static const V *host_alias(const V *p) {
     if (!p) return nullptr;
     cudaPointerAttributes a{};
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
         return nullptr;
     }
-    return (a.type == cudaMemoryTypeHost && a.devicePointer) ? static_cast<const double *>(a.devicePointer) : nullptr;
+    return (a.type == cudaMemoryTypeHost && a.devicePointer) ? static_cast<const V *>(a.devicePointer) : nullptr;
 }
 
 static int ensure_stage(lbm_run *h, size_t elems) {
@@ -626,35 +627,40 @@ int lbm_fields(lbm_handle h, unsigned mask, double *const *dst, int dst_is_devic
     return check_err_word(h);
 }
 
-int lbm_set_state(lbm_handle h, const double *f, const double *T, int64_t step, int src_is_device) {
+// lbm_set_state / lbm_set_state_f32: V is the arrays' type.
+extern "C++" {
+template <class V>
+static int set_state(lbm_handle h, const V *f, const V *T, int64_t step, int src_is_device) {
     if (!h) return LBM_E_INVAL;
     if (step < 0) return fail(h, LBM_E_INVAL, "negative step");
     CK(h, cudaSetDevice(h->device));
     const size_t nfl = (size_t)h->p.nx * h->p.nf, ntl = (size_t)h->p.nx * h->p.nt;
-    const double *df = f, *dT = T;
+    const V *df = f, *dT = T;
     int rc;
     if (!src_is_device && (f || T)) {
         // Page-locked host memory the device can address is read by the
         // import kernel itself (over NVLink-C2C on Grace: copy and conversion
-        // in one pass); other host memory is staged with an async copy.
-        const double *af = host_alias(f), *aT = host_alias(T);
+        // in one pass); other host memory is staged with an async copy (the
+        // stage holds 9 NF NX + NT NX doubles, room for either type).
+        const V *af = host_alias(f), *aT = host_alias(T);
         if ((f && !af) || (T && !aT)) {
             if ((rc = ensure_stage(h, 9 * nfl + ntl)) != LBM_OK) return rc;
         }
+        V *stage = reinterpret_cast<V *>(h->stage);
         if (f) {
             if (af) {
                 df = af;
             } else {
-                CK(h, cudaMemcpyAsync(h->stage, f, 9 * nfl * sizeof(double), cudaMemcpyHostToDevice, h->stream));
-                df = h->stage;
+                CK(h, cudaMemcpyAsync(stage, f, 9 * nfl * sizeof(V), cudaMemcpyHostToDevice, h->stream));
+                df = stage;
             }
         }
         if (T) {
             if (aT) {
                 dT = aT;
             } else {
-                CK(h, cudaMemcpyAsync(h->stage + 9 * nfl, T, ntl * sizeof(double), cudaMemcpyHostToDevice, h->stream));
-                dT = h->stage + 9 * nfl;
+                CK(h, cudaMemcpyAsync(stage + 9 * nfl, T, ntl * sizeof(V), cudaMemcpyHostToDevice, h->stream));
+                dT = stage + 9 * nfl;
             }
         }
     }
@@ -663,7 +669,9 @@ int lbm_set_state(lbm_handle h, const double *f, const double *T, int64_t step, 
     b.f_out = h->f[h->parity];
     b.T_out = h->T[h->parity];
     if (df || dT) {
-        cudaError_t e = h->ks->import_state(h->p, df, dT, b, h->stream);
+        cudaError_t e;
+        if constexpr (sizeof(V) == sizeof(double)) e = h->ks->import_state(h->p, (const double *)df, (const double *)dT, b, h->stream);
+        else e = h->ks->import_state32(h->p, (const float *)df, (const float *)dT, b, h->stream);
         if (e != cudaSuccess) return cuda_fail(h, e, "import kernel");
     }
     long long s = step;
@@ -676,6 +684,15 @@ int lbm_set_state(lbm_handle h, const double *f, const double *T, int64_t step, 
     h->series_from = step;
     h->diag_stale = true;
     return LBM_OK;
+}
+}  // extern "C++"
+
+int lbm_set_state(lbm_handle h, const double *f, const double *T, int64_t step, int src_is_device) {
+    return set_state(h, f, T, step, src_is_device);
+}
+
+int lbm_set_state_f32(lbm_handle h, const float *f, const float *T, int64_t step, int src_is_device) {
+    return set_state(h, f, T, step, src_is_device);
 }
 
 static const char *kStaleDiag = "no step has run since lbm_set_state: the diagnostics describe the previous state";

@@ -27,7 +27,7 @@ LBM_FIELD_RHO, LBM_FIELD_UX, LBM_FIELD_UY, LBM_FIELD_T, LBM_FIELD_F = 1, 2, 4, 8
 
 #: every entry point declared in include/lbm.h
 EXPORTS = ("lbm_create", "lbm_destroy", "lbm_step", "lbm_sync", "lbm_step_count", "lbm_fields",
-           "lbm_set_state", "lbm_get_state", "lbm_wall_heat_flux", "lbm_vapour_fraction", "lbm_mass", "lbm_series",
+           "lbm_set_state", "lbm_set_state_f32", "lbm_get_state", "lbm_wall_heat_flux", "lbm_vapour_fraction", "lbm_mass", "lbm_series",
            "lbm_set_timing", "lbm_kernel_times", "lbm_kernels_per_step", "lbm_variants",
            "lbm_variant_name", "lbm_select_variants", "lbm_autotune", "lbm_diagnostics_static",
            "lbm_batch_create", "lbm_batch_step", "lbm_batch_sync", "lbm_batch_destroy",
@@ -130,6 +130,7 @@ def load(path: str = LIB_PATH):
     L.lbm_step_count.restype = C.c_int64
     L.lbm_fields.argtypes = [C.c_void_p, C.c_uint, C.POINTER(C.c_void_p), C.c_int]
     L.lbm_set_state.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int]
+    L.lbm_set_state_f32.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int]
     L.lbm_get_state.argtypes = [C.c_void_p, _D, _D, C.POINTER(C.c_int64), C.c_int]
     L.lbm_wall_heat_flux.argtypes = [C.c_void_p, _D, _D]
     L.lbm_vapour_fraction.argtypes = [C.c_void_p, _D]
@@ -324,6 +325,26 @@ class Run:
             keep = (fa, ta)
         _check(load().lbm_set_state(self._h, fp, tp, int(step), 1 if src_is_device else 0), self._h,
                "lbm_set_state")
+        del keep
+
+    def set_state_f32(self, f=None, T=None, step: int = 0, src_is_device: bool = False):
+        """lbm_set_state_f32: as set_state with float32 arrays (or raw pointers
+        to float32 data)."""
+        if src_is_device or isinstance(f, int) or isinstance(T, int):
+            fp, tp = f, T
+            keep = None
+        else:
+            fa = None if f is None else np.ascontiguousarray(f, dtype=np.float32)
+            ta = None if T is None else np.ascontiguousarray(T, dtype=np.float32)
+            if fa is not None and fa.size != 9 * self.nf * self.nx:
+                raise ValueError("f must have 9 * nf * nx values")
+            if ta is not None and ta.size != self.nt * self.nx:
+                raise ValueError("T must have t_rows * nx values")
+            fp = None if fa is None else fa.ctypes.data
+            tp = None if ta is None else ta.ctypes.data
+            keep = (fa, ta)
+        _check(load().lbm_set_state_f32(self._h, fp, tp, int(step), 1 if src_is_device else 0), self._h,
+               "lbm_set_state_f32")
         del keep
 
     def get_state(self):

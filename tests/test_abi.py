@@ -25,14 +25,14 @@ def lib():
 def declared_functions():
     text = open(HEADER).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(lbm_[a-z_]+)\s*\(", text)))
+    return sorted(set(re.findall(r"\b(lbm_[a-z0-9_]+)\s*\(", text)))
 
 
 def test_every_declared_symbol_is_exported(lib):
     names = declared_functions()
     assert len(names) >= 10
     out = subprocess.check_output(["nm", "-D", "--defined-only", B.LIB]).decode()
-    exported = set(re.findall(r" T (lbm_[a-z_]+)", out))
+    exported = set(re.findall(r" T (lbm_[a-z0-9_]+)", out))
     assert set(names) <= exported, set(names) - exported
     assert set(names) == set(lbm.EXPORTS)
     for n in names:

@@ -126,6 +126,34 @@ def test_set_state_round_trip_and_restart_is_exact():
         assert np.array_equal(fa[k], fb[k]), k
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp16"])
+@pytest.mark.parametrize("pinned", [False, True])
+def test_float32_state_import_equals_the_same_values_as_float64(precision, pinned):
+    """lbm_set_state_f32 widens its float32 arrays before converting them to
+    the run's storage: the same values given as float64 to lbm_set_state give
+    the same state and the same next steps, bit for bit, from pageable and
+    from page-locked host memory."""
+    torch = pytest.importorskip("torch")
+    cfg = W.small_parity(precision=precision).replace(bc_mode="noise", spot_x=(), c_w_spot=(), rho_mean=2.42)
+    a = lbm.Run(cfg).step(7)
+    st = a.fields(("f", "T"))
+    f32, T32 = st["f"].astype(np.float32), st["T"].astype(np.float32)
+    b, c = lbm.Run(cfg), lbm.Run(cfg)
+    b.set_state(f32.astype(np.float64), T32.astype(np.float64), step=7)
+    if pinned:
+        hf = torch.from_numpy(f32.reshape(-1)).pin_memory()
+        hT = torch.from_numpy(T32.reshape(-1)).pin_memory()
+        c.set_state_f32(hf.data_ptr(), hT.data_ptr(), step=7)
+    else:
+        c.set_state_f32(f32, T32, step=7)
+    for r in (b, c):
+        r.step(5)
+    fb, fc = b.fields(("rho", "T", "f")), c.fields(("rho", "T", "f"))
+    for k in fb:
+        assert np.array_equal(fb[k], fc[k]), k
+    assert np.array_equal(b.series(7, 5), c.series(7, 5))
+
+
 def test_get_state_checkpoint_restarts_bit_for_bit():
     """lbm_get_state returns what lbm_set_state takes back: a run restarted
     from the checkpoint (populations, temperature, step counter that keys
