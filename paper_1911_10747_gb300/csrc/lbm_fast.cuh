@@ -1502,6 +1502,30 @@ heat_pair_body(const FParams &p, int tiles_x, int end, int first, int step, cons
             #pragma unroll
             for (int c = 0; c < R; c++) hN[c] = rcp2(add2(lam[c], c + 1 < R ? lam[c + 1] : Lt));
             const float2 hS0 = rcp2(add2(lam[0], Lb));
+            // likewise the east link of a cell is the west link of its east
+            // neighbour, and the north-east (north-west) link the south-west
+            // (south-east) link of the cell above it to the east (west): those
+            // come from the neighbouring lane (the column pairs are x, x + 32,
+            // so lane 0's second column meets lane 31's first).  Lane 0's first
+            // and lane 31's second column are the tile's outermost halo
+            // cells, whose coefficients no kept value depends on.
+            float2 hE[R], hNE[R], hNW[R];
+            #pragma unroll
+            for (int c = 0; c < R; c++) {
+                hE[c] = rcp2(add2(lam[c], Lr[c + 1]));
+                hNE[c] = rcp2(add2(lam[c], Lr[c + 2]));
+                hNW[c] = rcp2(add2(lam[c], Ll[c + 2]));
+            }
+            auto from_west = [&](float2 v) {  // v of the west neighbour's column pair
+                const float a = __shfl_up_sync(0xffffffffu, v.x, 1), b = __shfl_up_sync(0xffffffffu, v.y, 1);
+                const float w = __shfl_sync(0xffffffffu, v.x, HW - 1);
+                return make_float2(a, wrap_w ? w : b);
+            };
+            auto from_east = [&](float2 v) {  // v of the east neighbour's column pair
+                const float a = __shfl_down_sync(0xffffffffu, v.x, 1), b = __shfl_down_sync(0xffffffffu, v.y, 1);
+                const float e = __shfl_sync(0xffffffffu, v.y, 0);
+                return make_float2(wrap_e ? e : a, b);
+            };
             #pragma unroll
             for (int c = 0; c < R; c++) {
                 const float2 l0 = lam[c];
@@ -1509,14 +1533,14 @@ heat_pair_body(const FParams &p, int tiles_x, int end, int first, int step, cons
                 const bool moves = (k == HK_SOLID || k == HK_FLUID) && !iso;
                 const float2 f12 = moves ? mul2(f2(12.0f), irc[c]) : f2(0.0f);
                 const float2 cax = mul2(f2(w1), f12), cdg = mul2(f2(w2), f12);
-                kk[c][0] = mul2(cax, rcp2(add2(l0, Lr[c + 1])));
+                kk[c][0] = mul2(cax, hE[c]);
                 kk[c][1] = mul2(cax, hN[c]);
-                kk[c][2] = mul2(cax, rcp2(add2(l0, Ll[c + 1])));
+                kk[c][2] = mul2(cax, from_west(hE[c]));
                 kk[c][3] = mul2(cax, c > 0 ? hN[c - 1] : hS0);
-                kk[c][4] = mul2(cdg, rcp2(add2(l0, Lr[c + 2])));
-                kk[c][5] = mul2(cdg, rcp2(add2(l0, Ll[c + 2])));
-                kk[c][6] = mul2(cdg, rcp2(add2(l0, Ll[c])));
-                kk[c][7] = mul2(cdg, rcp2(add2(l0, Lr[c])));
+                kk[c][4] = mul2(cdg, hNE[c]);
+                kk[c][5] = mul2(cdg, hNW[c]);
+                kk[c][6] = mul2(cdg, c > 0 ? from_west(hNE[c - 1]) : rcp2(add2(l0, Ll[c])));
+                kk[c][7] = mul2(cdg, c > 0 ? from_east(hNW[c - 1]) : rcp2(add2(l0, Lr[c])));
                 const float2 ks = add2(add2(add2(kk[c][0], kk[c][1]), add2(kk[c][2], kk[c][3])),
                                        add2(add2(kk[c][4], kk[c][5]), add2(kk[c][6], kk[c][7])));
                 nks[c] = mul2(ks, f2(-1.0f));
