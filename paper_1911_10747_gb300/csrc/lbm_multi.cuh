@@ -177,11 +177,14 @@ k_diag_multi(const MultiRun *__restrict__ runs, int phase, unsigned *__restrict_
 // constants to the warp's shared memory when the run changes, and sweep the
 // unit with the single-run wavefront kernel's body; the unit's mass and
 // vapour count go to its own partial slot.
-__device__ __forceinline__ int find_run_wave(const MultiRun *__restrict__ runs, int nruns, int u) {
+// the runs' first units, in shared memory for launches of at most this many runs
+constexpr int MR_WTAB = 256;
+__device__ __forceinline__ int find_run_wave(const MultiRun *__restrict__ runs, const int *s_u0, int nruns, int u) {
     int lo = 0, hi = nruns - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
-        if (runs[mid].wave_unit0 <= u) lo = mid;
+        const int u0 = nruns <= MR_WTAB ? s_u0[mid] : runs[mid].wave_unit0;
+        if (u0 <= u) lo = mid;
         else hi = mid - 1;
     }
     return lo;
@@ -194,8 +197,12 @@ k_flow_wave_multi(const MultiRun *__restrict__ runs, int nruns, int total, int p
     __shared__ __align__(8) uint64_t fw_bar[WPB][FW_RS];
     __shared__ FParams s_p[WPB];
     __shared__ FlowWaveConsts s_k[WPB];
+    __shared__ int s_u0[MR_WTAB];
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (nruns <= MR_WTAB)
+        for (int r = threadIdx.x; r < nruns; r += blockDim.x) s_u0[r] = runs[r].wave_unit0;
+    __syncthreads();
     float *const ring = reinterpret_cast<float *>(fw_raw) + ((128u - (smem_u32(fw_raw) & 127u)) & 127u) / 4u +
                         warp * (FW_RS * FW_SLOT);
     FParams &p = s_p[warp];
@@ -208,7 +215,7 @@ k_flow_wave_multi(const MultiRun *__restrict__ runs, int nruns, int total, int p
         if (lane == 0) u = (int)atomicAdd(wq, 1u);
         u = __shfl_sync(FULL, u, 0);
         if (u >= total) break;
-        const int r = find_run_wave(runs, nruns, u);
+        const int r = find_run_wave(runs, s_u0, nruns, u);
         const MultiRun *q = runs + r;
         const int lu = u - q->wave_unit0;
         if (!(r >= 0 && r < nruns && q->magic == MULTI_MAGIC && q->wave_ok && lu >= 0 && lu < q->wave_nunits)) {
