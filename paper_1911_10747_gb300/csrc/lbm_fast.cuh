@@ -1307,7 +1307,8 @@ template <class P, int BY, int R, bool WIDE, bool RAW = false>
 __device__ __forceinline__ void
 heat_pair_body(const FParams &p, int tiles_x, int end, int first, int step, const typename P::tst *__restrict__ Tin,
                typename P::tst *__restrict__ Tout, const float *__restrict__ rho_i, const float *__restrict__ ux_i,
-               const float *__restrict__ uy_i, const long long *__restrict__ stepp, unsigned *__restrict__ err) {
+               const float *__restrict__ uy_i, const long long *__restrict__ stepp, unsigned *__restrict__ err,
+               int ymirror = -1) {
     constexpr int HW = 32, BW = 2 * HW, NSL = HW, H = 4, SH = R * BY, TXO = BW - 2 * H, TYO = SH - 2 * H;
     __shared__ float2 sT[2][SH][NSL];
     // 1/lambda, u_x, u_y of the tile for the coefficient pass; afterwards the
@@ -1397,7 +1398,11 @@ heat_pair_body(const FParams &p, int tiles_x, int end, int first, int step, cons
             cp_async4(dW + 1, uy_i + kfb, fl);
         }
     };
+    // tile rows in sequence order -> tile rows in the domain (ymirror >= 0:
+    // the last tile row first, so that the sweep runs down the rows)
+    auto ymap = [&](int tyt) { return ymirror >= 0 ? ymirror - tyt : tyt; };
     auto fetch = [&](int txt, int tyt) {
+        tyt = ymap(tyt);
         if (interior(tyt)) fetch_tile(txt, tyt, std::true_type{});
         else fetch_tile(txt, tyt, std::false_type{});
     };
@@ -1604,7 +1609,7 @@ heat_pair_body(const FParams &p, int tiles_x, int end, int first, int step, cons
             }
         }
         };
-        if (interior(cyt)) prepare(std::true_type{});
+        if (interior(ymap(cyt))) prepare(std::true_type{});
         else prepare(std::false_type{});
         // ---- four RK stages; stage s reads sT[s & 1], writes sT[(s + 1) & 1] ----
         if (!iso) {
@@ -1652,7 +1657,7 @@ heat_pair_body(const FParams &p, int tiles_x, int end, int first, int step, cons
             fetch(nxt, nyt);
         }
         // ---- write the tile (fixed cells have acc = 0) ----
-        const int x0 = cxt * TXO, r0 = cyt * TYO;
+        const int x0 = cxt * TXO, r0 = ymap(cyt) * TYO;
         const int xa = x0 + tx - H, xb = x0 + tx + HW - H;
         #pragma unroll
         for (int c = 0; c < R; c++) {
@@ -1681,12 +1686,16 @@ template <class P, int BY, int R, int MINB, bool WIDE, bool RAW = false>
 __global__ void __launch_bounds__(32 * BY, MINB)
 k_heat_pair(const __grid_constant__ FParams p, int tiles_x, int ntiles, const typename P::tst *__restrict__ Tin,
             typename P::tst *__restrict__ Tout, const float *__restrict__ rho_i, const float *__restrict__ ux_i,
-            const float *__restrict__ uy_i, const long long *__restrict__ stepp, unsigned *__restrict__ err) {
+            const float *__restrict__ uy_i, const long long *__restrict__ stepp, unsigned *__restrict__ err,
+            int ymirror) {
     heat_pair_body<P, BY, R, WIDE, RAW>(p, tiles_x, ntiles, (int)blockIdx.x, (int)gridDim.x, Tin, Tout, rho_i, ux_i,
-                                        uy_i, stepp, err);
+                                        uy_i, stepp, err, ymirror);
 }
 
-template <class P, int BY, int R, int MINB, bool RAW = false>
+// DOWN: the tiles are taken from the top tile row down, so that the rows the
+// flow kernel (sweeping up) wrote last are read first, while they are still
+// in L2, and the next flow kernel finds the bottom rows of T there.
+template <class P, int BY, int R, int MINB, bool RAW = false, bool DOWN = false>
 struct HeatPairShape {
     static int grid_blocks;
     static cudaError_t prepare() {
@@ -1711,12 +1720,13 @@ struct HeatPairShape {
                                               : k_heat_pair<P, BY, R, MINB, false>;
         k<<<g, dim3(32, BY), 0, s>>>(
             make_fparams(p), tx, ntiles, (const typename P::tst *)b.T_in, (typename P::tst *)b.T_out,
-            (const float *)b.rho, (const float *)b.ux, (const float *)b.uy, b.step, b.err);
+            (const float *)b.rho, (const float *)b.ux, (const float *)b.uy, b.step, b.err,
+            DOWN ? ty - 1 : -1);
         return cudaGetLastError();
     }
 };
-template <class P, int BY, int R, int MINB, bool RAW>
-int HeatPairShape<P, BY, R, MINB, RAW>::grid_blocks = 152;
+template <class P, int BY, int R, int MINB, bool RAW, bool DOWN>
+int HeatPairShape<P, BY, R, MINB, RAW, DOWN>::grid_blocks = 152;
 
 }  // namespace lbmgb
 

@@ -369,12 +369,33 @@ __device__ __forceinline__ void wave_unit(const FParams &p, const FlowWaveConsts
     }
 }
 
+// Work units of the wavefront flow kernel: strips of 64 columns times row
+// segments, taken in counter order one band of rows (all strips) at a time.
+// Rows [0, y2) come in segments of seg rows, rows [y2, nf) in shorter
+// segments of seg2 rows, so that the units taken last, while the other
+// warps run out of work, are short.
+struct WaveUnits {
+    int nstrips, seg, nmain, y2, seg2, nunits;
+    __device__ __forceinline__ void unit(int u, int nf, int &strip, int &ys, int &ye) const {
+        if (u < nmain) {
+            strip = u % nstrips;
+            ys = (u / nstrips) * seg;
+            ye = min(ys + seg, y2);
+        } else {
+            const int v = u - nmain;
+            strip = v % nstrips;
+            ys = y2 + (v / nstrips) * seg2;
+            ye = min(ys + seg2, nf);
+        }
+    }
+};
+
 template <int WPB, int MINB>
 __global__ void __launch_bounds__(32 * WPB, MINB)
 k_flow_wave(const __grid_constant__ CUtensorMap map_f, const __grid_constant__ CUtensorMap map_t,
             const __grid_constant__ CUtensorMap map_fs, const __grid_constant__ CUtensorMap map_ts,
-            const __grid_constant__ FParams p, const __grid_constant__ FlowWaveConsts K, int nstrips, int seg,
-            int nunits, float *__restrict__ fout, float *__restrict__ rho_o, float *__restrict__ ux_o,
+            const __grid_constant__ FParams p, const __grid_constant__ FlowWaveConsts K, WaveUnits wu,
+            float *__restrict__ fout, float *__restrict__ rho_o, float *__restrict__ ux_o,
             float *__restrict__ uy_o, const double *__restrict__ cw, double *__restrict__ part,
             unsigned *__restrict__ err, unsigned *__restrict__ wq) {
     extern __shared__ float4 fw_raw[];  // the warps' rings (+128 bytes of slack)
@@ -397,11 +418,11 @@ k_flow_wave(const __grid_constant__ CUtensorMap map_f, const __grid_constant__ C
         int u = 0;
         if (lane == 0) u = (int)atomicAdd(wq, 1u);
         u = __shfl_sync(FULL, u, 0);
-        if (u >= nunits) break;
-        const int strip = u % nstrips, sgi = u / nstrips;
-        const int ys = sgi * seg;
-        wave_unit(p, K, &map_f, &map_t, &map_fs, &map_ts, strip * FW_W, ys, min(ys + seg, p.nf), op, rho_o, ux_o,
-                  uy_o, cw, w, lane, mass, nvap, errbits);
+        if (u >= wu.nunits) break;
+        int ys, ye, strip;
+        wu.unit(u, p.nf, strip, ys, ye);
+        wave_unit(p, K, &map_f, &map_t, &map_fs, &map_ts, strip * FW_W, ys, ye, op, rho_o, ux_o, uy_o, cw, w, lane,
+                  mass, nvap, errbits);
         if (w.failed) break;
     }
     if (w.failed) {
@@ -430,8 +451,10 @@ k_flow_wave(const __grid_constant__ CUtensorMap map_f, const __grid_constant__ C
 }
 
 // Launch shape of k_flow_wave (U2: work units per resident warp, times
-// two); domains it cannot take run k_flow_pers (32 x 16-site tiles) instead.
-template <int WPB, int MINB, int U2>
+// two; SEGM > 0: segments of SEGM rows, and a last band of SEGT-row segments
+// with about TU2 / 2 units per resident warp); domains it cannot take run
+// k_flow_pers (32 x 16-site tiles) instead.
+template <int WPB, int MINB, int U2, int SEGM = 0, int SEGT = 0, int TU2 = 2>
 struct FlowWaveShape {
     using Fallback = FlowPersShape<PolicyF32, 32, 8, 2, 2>;
     static constexpr size_t smem_bytes = (size_t)WPB * FW_RS * FW_SLOT * sizeof(float) + 128;
@@ -453,28 +476,37 @@ struct FlowWaveShape {
         grid_blocks = sms * (per > 0 ? per : 1);
         return cudaSuccess;
     }
-    // strips of 64 columns x segments of at least 8 rows, about U2 / 2 units
-    // per resident warp (taken from the counter, so a warp that starts late
-    // takes fewer; longer segments re-read fewer rows at their ends)
-    static void shape(const DevParams &p, int &nstrips, int &seg, int &nunits) {
-        nstrips = p.nx / FW_W;
-        const long long want = (long long)U2 * grid_blocks * WPB / 2;
-        int nseg = (int)std::max<long long>(1, want / nstrips);
-        seg = std::max(8, (p.nf + nseg - 1) / nseg);
-        nseg = (p.nf + seg - 1) / seg;
-        nunits = nstrips * nseg;
+    // without SEGM: segments of at least 8 rows, about U2 / 2 units per
+    // resident warp (taken from the counter, so a warp that starts late takes
+    // fewer; longer segments re-read fewer rows at their ends)
+    static WaveUnits shape(const DevParams &p) {
+        WaveUnits wu;
+        wu.nstrips = p.nx / FW_W;
+        if (SEGM > 0) {
+            const long long warps = (long long)grid_blocks * WPB * TU2 / 2;
+            const int tail_bands = (int)((warps + wu.nstrips - 1) / wu.nstrips);
+            int tail_rows = std::min(p.nf, SEGT * tail_bands);
+            if (p.nf - tail_rows < SEGM) tail_rows = p.nf;  // too small for a main band
+            wu.seg = SEGM;
+            wu.y2 = p.nf - tail_rows;
+            wu.seg2 = SEGT;
+        } else {
+            const long long want = (long long)U2 * grid_blocks * WPB / 2;
+            const int nseg = (int)std::max<long long>(1, want / wu.nstrips);
+            wu.seg = std::max(8, (p.nf + nseg - 1) / nseg);
+            wu.y2 = p.nf;
+            wu.seg2 = wu.seg;
+        }
+        wu.nmain = wu.nstrips * ((wu.y2 + wu.seg - 1) / wu.seg);
+        wu.nunits = wu.nmain + wu.nstrips * ((p.nf - wu.y2 + wu.seg2 - 1) / wu.seg2);
+        return wu;
     }
-    static int grid(const DevParams &p) {
-        int nstrips, seg, nunits;
-        shape(p, nstrips, seg, nunits);
-        return std::min(grid_blocks, (nunits + WPB - 1) / WPB);
-    }
+    static int grid(const DevParams &p) { return std::min(grid_blocks, (shape(p).nunits + WPB - 1) / WPB); }
     // one pair of partial sums per warp
     static int blocks(const DevParams &p) { return eligible(p) ? grid(p) * WPB : Fallback::blocks(p); }
     static cudaError_t launch(const DevParams &p, const StepBuffers &b, cudaStream_t s) {
         if (!eligible(p)) return Fallback::launch(p, b, s);
-        int nstrips, seg, nunits;
-        shape(p, nstrips, seg, nunits);
+        const WaveUnits wu = shape(p);
         // boxes: 72 columns x 1 row x 9 planes of the populations and 72 x 1
         // of T (all T rows, heater included: fluid row y sits at ns + y);
         // the wrapped halo boxes 4 columns wide
@@ -498,12 +530,12 @@ struct FlowWaveShape {
         if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
         const FParams q = make_fparams(p);
         k_flow_wave<WPB, MINB><<<grid(p), 32 * WPB, smem_bytes, s>>>(
-            mf, mt, mfs, mts, q, make_flowwave_consts(q), nstrips, seg, nunits, (float *)b.f_out, (float *)b.rho,
+            mf, mt, mfs, mts, q, make_flowwave_consts(q), wu, (float *)b.f_out, (float *)b.rho,
             (float *)b.ux, (float *)b.uy, b.cw, b.part, b.err, b.wq);
         return cudaGetLastError();
     }
 };
-template <int WPB, int MINB, int U2>
-int FlowWaveShape<WPB, MINB, U2>::grid_blocks = 152;
+template <int WPB, int MINB, int U2, int SEGM, int SEGT, int TU2>
+int FlowWaveShape<WPB, MINB, U2, SEGM, SEGT, TU2>::grid_blocks = 152;
 
 }  // namespace lbmgb

@@ -25,6 +25,12 @@ cudaError_t diag(const DevParams &p, const StepBuffers &b, int nblk, cudaStream_
 #define FLOWW(WPB, MB, U2)                                                                        \
     {"flowwave_w" #WPB "_b" #MB "_u" #U2, FlowWaveShape<WPB, MB, U2>::launch,                          \
      FlowWaveShape<WPB, MB, U2>::blocks, FlowWaveShape<WPB, MB, U2>::prepare}
+#define FLOWWT(WPB, MB, SM, ST, TU)                                                               \
+    {"flowwave_w" #WPB "_b" #MB "_s" #SM "t" #ST "x" #TU, FlowWaveShape<WPB, MB, 0, SM, ST, TU>::launch, \
+     FlowWaveShape<WPB, MB, 0, SM, ST, TU>::blocks, FlowWaveShape<WPB, MB, 0, SM, ST, TU>::prepare}
+#define HEATP16D(P, BY, R, MB)                                                                    \
+    {"heatpair16_64x" #BY "x" #R "_down", HeatPairShape<P, BY, R, MB, true, true>::launch,              \
+     HeatPairShape<P, BY, R, MB, true, true>::prepare}
 #define HEATS(P, BW, BY, R, MB) \
     {"heatrows_" #BW "x" #BY "x" #R, HeatRowsShape<P, BW, BY, R, MB>::launch, HeatRowsShape<P, BW, BY, R, MB>::prepare}
 #define HEATSD(P, BW, BY, R, MB)                                                                 \
@@ -51,13 +57,14 @@ const FlowVariant flows32[] = {
     FLOWT(PolicyF32, 4, 2, 3), FLOWP(PolicyF32, 64, 4, 2, 2), FLOWP(PolicyF32, 32, 8, 2, 2),
     FLOWP(PolicyF32, 32, 8, 1, 3), FLOWV(PolicyF32, 32, 8, 2, 3), FLOWV(PolicyF32, 64, 4, 2, 3),
     FLOWW(4, 3, 8), FLOWW(4, 4, 8),
+    FLOWWT(4, 3, 16, 4, 4),
     FLOWWM(PolicyF32), FLOWM(PolicyF32),
 };
 const HeatVariant heats32[] = {
     HEATS(PolicyF32, 64, 6, 5, 1), HEATS(PolicyF32, 64, 8, 4, 1), HEATS(PolicyF32, 64, 10, 3, 1),
     HEATS(PolicyF32, 64, 6, 6, 1),
     HEATS(PolicyF32, 32, 8, 4, 2),
-    HEATP(PolicyF32, 12, 4, 1), HEATP(PolicyF32, 8, 4, 1), HEATP16(PolicyF32, 12, 4, 1),
+    HEATP(PolicyF32, 12, 4, 1), HEATP(PolicyF32, 8, 4, 1), HEATP16(PolicyF32, 12, 4, 1), HEATP16D(PolicyF32, 12, 4, 1),
     HEATW(PolicyF32, 2, 2, 4, 8), HEATM(PolicyF32),
     HEATV(PolicyF32, 32, 16, 32, 8), HEATV(PolicyF32, 64, 32, 32, 16),
 };
