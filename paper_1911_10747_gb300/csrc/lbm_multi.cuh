@@ -22,9 +22,10 @@ namespace lbmgb {
 
 // Runs whose columns come in strips of 64 (FP32 storage, at least 128
 // columns) take the row-wavefront flow kernel instead of the tiles: their
-// work items are strips of 64 columns x MR_WSEG rows (units), each swept by
-// one warp, with the unit's mass and vapour count as its partials.
-constexpr int MR_WSEG = 12, MR_WWPB = 4, MR_WMINB = 3;
+// work items are strips of 64 columns x MR_WSEG rows (units), the top
+// MR_WTAIL rows in segments of MR_WSEG2 rows, each unit swept by one warp,
+// with the unit's mass and vapour count as its partials.
+constexpr int MR_WSEG = 16, MR_WSEG2 = 4, MR_WTAIL = 48, MR_WWPB = 4, MR_WMINB = 3;
 // flow tiles: 32 x 16 sites, 256 threads of 2 sites
 constexpr int MR_FBX = 32, MR_FBY = 8, MR_FRY = 2, MR_FTX = MR_FBX, MR_FTY = MR_FBY * MR_FRY;
 // heat tiles: the paired-column tiles, 64 x 48 cells with a 4-cell halo (56 x 40 outputs), 384 threads
@@ -39,10 +40,12 @@ struct MultiRun {
     int nblk;              // partials its diagnostics sum (flow tiles, or units in wavefront mode)
     unsigned magic;        // MULTI_MAGIC: set by fill_multi, checked by every block
     double inv_nx, inv_nfl;
-    // wavefront mode (wave_ok): 64-column strips x MR_WSEG-row units, the
-    // first of them wave_unit0 in the launch; packed constants; tensor maps
-    // of f, T and the wrapped halo boxes for each state parity
-    int wave_ok, wave_nstrips, wave_nunits, wave_unit0;
+    // wavefront mode (wave_ok): 64-column strips x MR_WSEG-row units below
+    // row wave_y2 (wave_nmain of them) and MR_WSEG2-row units above, the
+    // first of them wave_unit0 in a launch that takes each run's units in
+    // turn; packed constants; tensor maps of f, T and the wrapped halo boxes
+    // for each state parity
+    int wave_ok, wave_nstrips, wave_nunits, wave_unit0, wave_nmain, wave_y2;
     FlowWaveConsts K;
     CUtensorMap wave_map[2][4];
 };
@@ -171,19 +174,24 @@ k_diag_multi(const MultiRun *__restrict__ runs, int phase, unsigned *__restrict_
                             B.series_cap, B.last, B.step, run->inv_nx, run->inv_nfl);
 }
 
-// ---- flow, wavefront mode: one warp per unit (strip x MR_WSEG rows) ----------
-// Warps take units from the launch's counter (wq, zero between launches),
-// find the run by binary search over the runs' first units, copy its
-// constants to the warp's shared memory when the run changes, and sweep the
-// unit with the single-run wavefront kernel's body; the unit's mass and
-// vapour count go to its own partial slot.
-// the runs' first units, in shared memory for launches of at most this many runs
+// ---- flow, wavefront mode: one warp per unit (strip x segment of rows) ------
+// Warps take units from the launch's counter (wq, zero between launches):
+// first every run's MR_WSEG-row units, run by run, then every run's
+// MR_WSEG2-row units of its top rows, so that the units taken last, while
+// the other warps run out of work, are short.  A warp finds the run by
+// binary search over the runs' first units in either phase, copies its
+// constants to the warp's shared memory when the run changes, and sweeps
+// the unit with the single-run wavefront kernel's body; the unit's mass and
+// vapour count go to its own partial slot (the run's unit numbering, the
+// same in every launch).  Launches of more than MR_WTAB runs take each
+// run's units in turn (wave_unit0).
 constexpr int MR_WTAB = 256;
+// index of the last run whose first unit (u0) is at most u
 __device__ __forceinline__ int find_run_wave(const MultiRun *__restrict__ runs, const int *s_u0, int nruns, int u) {
     int lo = 0, hi = nruns - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
-        const int u0 = nruns <= MR_WTAB ? s_u0[mid] : runs[mid].wave_unit0;
+        const int u0 = s_u0 ? s_u0[mid] : runs[mid].wave_unit0;
         if (u0 <= u) lo = mid;
         else hi = mid - 1;
     }
@@ -197,11 +205,34 @@ k_flow_wave_multi(const MultiRun *__restrict__ runs, int nruns, int total, int p
     __shared__ __align__(8) uint64_t fw_bar[WPB][FW_RS];
     __shared__ FParams s_p[WPB];
     __shared__ FlowWaveConsts s_k[WPB];
-    __shared__ int s_u0[MR_WTAB];
+    __shared__ int s_u0[MR_WTAB], s_u1[MR_WTAB], s_ta;  // first units of the runs in either phase
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (nruns <= MR_WTAB)
-        for (int r = threadIdx.x; r < nruns; r += blockDim.x) s_u0[r] = runs[r].wave_unit0;
+    const bool phased = nruns <= MR_WTAB;
+    if (phased && warp == 0) {
+        // exclusive prefix sums of the runs' long and short unit counts
+        int ca = 0, cb = 0;
+        for (int base = 0; base < nruns; base += 32) {
+            const int r = base + lane;
+            const int a = r < nruns ? runs[r].wave_nmain : 0, c = r < nruns ? runs[r].wave_nunits - a : 0;
+            int ia = a, ic = c;
+            #pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int ta = __shfl_up_sync(FULL, ia, o), tc = __shfl_up_sync(FULL, ic, o);
+                if (lane >= o) {
+                    ia += ta;
+                    ic += tc;
+                }
+            }
+            if (r < nruns) {
+                s_u0[r] = ca + ia - a;
+                s_u1[r] = cb + ic - c;
+            }
+            ca += __shfl_sync(FULL, ia, 31);
+            cb += __shfl_sync(FULL, ic, 31);
+        }
+        if (lane == 0) s_ta = ca;
+    }
     __syncthreads();
     float *const ring = reinterpret_cast<float *>(fw_raw) + ((128u - (smem_u32(fw_raw) & 127u)) & 127u) / 4u +
                         warp * (FW_RS * FW_SLOT);
@@ -215,9 +246,18 @@ k_flow_wave_multi(const MultiRun *__restrict__ runs, int nruns, int total, int p
         if (lane == 0) u = (int)atomicAdd(wq, 1u);
         u = __shfl_sync(FULL, u, 0);
         if (u >= total) break;
-        const int r = find_run_wave(runs, s_u0, nruns, u);
+        int r, lu;
+        if (!phased) {
+            r = find_run_wave(runs, nullptr, nruns, u);
+            lu = u - runs[r].wave_unit0;
+        } else if (u < s_ta) {
+            r = find_run_wave(runs, s_u0, nruns, u);
+            lu = u - s_u0[r];
+        } else {
+            r = find_run_wave(runs, s_u1, nruns, u - s_ta);
+            lu = runs[r].wave_nmain + (u - s_ta - s_u1[r]);
+        }
         const MultiRun *q = runs + r;
-        const int lu = u - q->wave_unit0;
         if (!(r >= 0 && r < nruns && q->magic == MULTI_MAGIC && q->wave_ok && lu >= 0 && lu < q->wave_nunits)) {
             if (lane == 0) atomicOr(errw, (unsigned)ERRW_DESC);
             continue;
@@ -239,13 +279,20 @@ k_flow_wave_multi(const MultiRun *__restrict__ runs, int nruns, int total, int p
         float *op[9];
         #pragma unroll
         for (int i = 0; i < 9; i++) op[i] = (float *)B.f_out + i * plane;
-        const int strip = lu % q->wave_nstrips, sgi = lu / q->wave_nstrips;
-        const int ys = sgi * MR_WSEG;
+        WaveUnits wu;
+        wu.nstrips = q->wave_nstrips;
+        wu.seg = MR_WSEG;
+        wu.nmain = q->wave_nmain;
+        wu.y2 = q->wave_y2;
+        wu.seg2 = MR_WSEG2;
+        wu.nunits = q->wave_nunits;
+        int strip, ys, ye;
+        wu.unit(lu, p.nf, strip, ys, ye);
         float mass = 0.0f, nvap = 0.0f;
         unsigned errbits = 0;
         wave_unit(p, K, &q->wave_map[par][0], &q->wave_map[par][1], &q->wave_map[par][2], &q->wave_map[par][3],
-                  strip * FW_W, ys, min(ys + MR_WSEG, p.nf), op, (float *)B.rho, (float *)B.ux, (float *)B.uy, B.cw,
-                  w, lane, mass, nvap, errbits);
+                  strip * FW_W, ys, ye, op, (float *)B.rho, (float *)B.ux, (float *)B.uy, B.cw, w, lane, mass, nvap,
+                  errbits);
         #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             mass += __shfl_down_sync(FULL, mass, o);
@@ -283,7 +330,11 @@ inline int multi_wave_ok(const DevParams &p) {
     return sizeof(typename P::fst) == 4 && p.nx % FW_W == 0 && p.nx >= 2 * FW_W && !(p.flags & FLAG_FROZEN_FLOW) &&
            tensor_map_encoder() != nullptr;
 }
-inline int multi_wave_units(const DevParams &p) { return (p.nx / FW_W) * ((p.nf + MR_WSEG - 1) / MR_WSEG); }
+inline int multi_wave_y2(const DevParams &p) { return p.nf > MR_WTAIL ? p.nf - MR_WTAIL : 0; }
+inline int multi_wave_nmain(const DevParams &p) { return (p.nx / FW_W) * ((multi_wave_y2(p) + MR_WSEG - 1) / MR_WSEG); }
+inline int multi_wave_units(const DevParams &p) {
+    return multi_wave_nmain(p) + (p.nx / FW_W) * ((p.nf - multi_wave_y2(p) + MR_WSEG2 - 1) / MR_WSEG2);
+}
 // flow work items of a run: tiles, or wavefront units (mode bit 0)
 template <class P>
 inline int multi_flow_items(const DevParams &p, int mode) {
@@ -338,6 +389,8 @@ inline void fill_multi(const DevParams &p, const StepBuffers &b0, const StepBuff
     if (m->wave_ok) {
         m->wave_nstrips = p.nx / FW_W;
         m->wave_nunits = multi_wave_units(p);
+        m->wave_nmain = multi_wave_nmain(p);
+        m->wave_y2 = multi_wave_y2(p);
         m->K = make_flowwave_consts(m->p);
         // the copies read the state parity's input buffers: f_in of b0 is the
         // input of a run whose state is in parity 0
