@@ -103,7 +103,7 @@ def ncu_instructions(kind: str, variant: str):
 
 
 # the heat variant whose FP32 operations were counted when the timed one was not
-HEAT_COUNTED_VARIANT = "heatpair16_64x12x4"
+HEAT_COUNTED_VARIANT = "heatpair16_64x12x4_down"
 
 
 def heat_flops(variant: str):
