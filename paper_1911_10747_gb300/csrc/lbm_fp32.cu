@@ -45,7 +45,7 @@ cudaError_t diag(const DevParams &p, const StepBuffers &b, int nblk, cudaStream_
     {"heatwave_c" #CL "_w" #WPB "_b" #MB "_r" #RS, HeatWaveShape<P, CL, WPB, MB, RS>::launch, \
      HeatWaveShape<P, CL, WPB, MB, RS>::prepare}
 #define FLOWM(P) {"flowmulti_32x8x2", MultiKernels<P>::flow, MultiKernels<P>::flow_blocks, MultiKernels<P>::prepare}
-#define FLOWWM(P) {"flowwavemulti_w4_b3", MultiKernels<P>::wave, MultiKernels<P>::wave_blocks, MultiKernels<P>::prepare}
+#define FLOWWM(P) {"flowwavemulti_w4_b4", MultiKernels<P>::wave, MultiKernels<P>::wave_blocks, MultiKernels<P>::prepare}
 #define HEATM(P) {"heatmulti_64x12x4", MultiKernels<P>::heat, MultiKernels<P>::prepare}
 #define MULTI(P) sizeof(MultiRun), fill_multi<P>, multi_flow_items<P>, multi_heat_tiles, multi_mode<P>, MultiKernels<P>::launch, \
     launch_import32<P>

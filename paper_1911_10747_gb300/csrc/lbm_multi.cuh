@@ -25,7 +25,7 @@ namespace lbmgb {
 // work items are strips of 64 columns x MR_WSEG rows (units), the top
 // MR_WTAIL rows in segments of MR_WSEG2 rows, each unit swept by one warp,
 // with the unit's mass and vapour count as its partials.
-constexpr int MR_WSEG = 16, MR_WSEG2 = 4, MR_WTAIL = 48, MR_WWPB = 4, MR_WMINB = 3;
+constexpr int MR_WSEG = 16, MR_WSEG2 = 4, MR_WTAIL = 48, MR_WWPB = 4, MR_WMINB = 4;
 // flow tiles: 32 x 16 sites, 256 threads of 2 sites
 constexpr int MR_FBX = 32, MR_FBY = 8, MR_FRY = 2, MR_FTX = MR_FBX, MR_FTY = MR_FBY * MR_FRY;
 // heat tiles: the paired-column tiles, 64 x 48 cells with a 4-cell halo (56 x 40 outputs), 384 threads

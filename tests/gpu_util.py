@@ -45,7 +45,7 @@ def select_multi(run):
     runs the tiles otherwise, as a batch does).  Other precisions keep
     theirs."""
     v = run.variants()
-    for name in ("flowwavemulti_w4_b3", "flowmulti_32x8x2"):
+    for name in ("flowwavemulti_w4_b4", "flowmulti_32x8x2"):
         if name in v["flow"]:
             run.select_variants(v["flow"].index(name), v["heat"].index("heatmulti_64x12x4"))
             break
