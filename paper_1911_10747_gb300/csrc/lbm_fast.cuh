@@ -1211,8 +1211,7 @@ k_heat_rows(const FParams p, int tiles_x, int ntiles, const typename P::tst *__r
                     // T_0 + T_sat > 0 in every cell whose value is used
                     float v;
                     if constexpr (DF) {
-                        const dfloat ta = df_add(df_from(t0), dfloat{p.df_tsat[0], p.df_tsat[1]});
-                        v = df_to_float(df_add(df_mul(C1d[c], ta), df_mul(C2d[c], df_sqrt(ta))));
+                        v = df_source(C1d[c], C2d[c], t0, dfloat{p.df_tsat[0], p.df_tsat[1]});
                     } else {
                         v = c0[c] + c2[c] * fast_sqrt(t0 + tsat);
                     }
