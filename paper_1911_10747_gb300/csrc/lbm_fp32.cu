@@ -72,6 +72,7 @@ const HeatVariant heats32[] = {
 const HeatVariant heats32df[] = {HEATSD(PolicyF32, 64, 8, 4, 1), HEATSD(PolicyF32, 64, 6, 5, 1)};
 const FlowVariant flows16[] = {FLOWP(PolicyF16, 32, 8, 2, 2), FLOWV(PolicyF16, 32, 8, 2, 3), FLOWM(PolicyF16)};
 const HeatVariant heats16[] = {HEATS(PolicyF16, 64, 10, 3, 1), HEATS(PolicyF16, 64, 8, 4, 1), HEATP(PolicyF16, 12, 4, 1),
+                               HEATP16(PolicyF16, 12, 4, 1), HEATP16D(PolicyF16, 12, 4, 1),
                                HEATV(PolicyF16, 32, 32, 32, 16), HEATM(PolicyF16)};
 
 const KernelSet ks32 = {"fp32", sizeof(float), sizeof(float), sizeof(float),

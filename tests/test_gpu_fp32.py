@@ -239,14 +239,16 @@ def test_fp32_paired_column_and_wavefront_heat_variants_against_the_oracle(kw):
         assert errs["rho"] < 1e-4 and errs["T"] < 1e-5, (names[hv], errs)
 
 
-def test_fp16_storage_heat_variants_agree():
+@pytest.mark.parametrize("nx", [70, 128])
+def test_fp16_storage_heat_variants_agree(nx):
     """The heat kernels read float T, rho and u whatever the population
     storage: with FP16 storage every heat variant follows the same run (the
     flow kernel's stochastic rounding is keyed by site and step, so it draws
     the same dither in every run; values that land next to a rounding step
-    can still differ by one half ulp)."""
-    cfg = W.small_parity(precision="fp16").replace(nx=70, nf=45, ns=5, liquid_rows=15, rho_mean=2.3,
-                                                   spot_x=(3, 40, 69), spot_half_width=2)
+    can still differ by one half ulp).  128 columns: the row-staged kernels
+    stage whole rows (nx a multiple of 4)."""
+    cfg = W.small_parity(precision="fp16").replace(nx=nx, nf=45, ns=5, liquid_rows=15, rho_mean=2.3,
+                                                   spot_x=(3, 40, nx - 1), spot_half_width=2)
     names = lbm.Run(cfg).variants()["heat"]
 
     def run(hv):
