@@ -319,6 +319,26 @@ def test_fp32_wavefront_flow_variants_against_the_oracle(kw):
             assert np.max(np.abs(got[0][k] - other[k])) <= 1e-5 * np.abs(got[0][k]).max(), k
 
 
+def test_fp32_wavefront_flow_long_and_short_units():
+    """A domain wide enough (2048 columns, 32 strips) that the wavefront
+    shapes cut it into long units below a band of short ones, with 700 rows
+    so that the last long segment is ragged (shapes with 16-row units: 92
+    rows below the short band); three steps against the oracle for every
+    wavefront shape, and the shapes agree."""
+    cfg = W.large(precision="fp32").replace(nf=700, ns=16, liquid_rows=233, rho_mean=2.41)
+    names = lbm.Run(cfg).variants()["flow"]
+    o = O.OracleRun(cfg)
+    o.step(3)
+    for fv in [i for i, n in enumerate(names) if n.startswith("flowwave_")]:
+        g = lbm.Run(cfg)
+        g.select_variants(fv, 0)
+        g.step(3)
+        g.sync()
+        errs = field_errors(g, o)
+        g.close()
+        assert errs["rho"] < 1e-5 and errs["T"] < 1e-6 and errs["f"] < 1e-5, (names[fv], errs)
+
+
 @pytest.mark.parametrize("nx,ny", [(128, 6), (128, 70), (256, 40)])
 def test_fp32_wavefront_flow_in_a_periodic_box(nx, ny):
     """Periodic in y: the sweep's first and last rows wrap (6 rows: fewer
