@@ -148,3 +148,27 @@ def test_fresh_batches_take_odd_steps_at_once():
         q.step(r.step_count)
         a, c = r.fields(("rho", "T")), q.fields(("rho", "T"))
         assert np.array_equal(a["rho"], c["rho"]) and np.array_equal(a["T"], c["T"])
+
+
+def test_batch_of_more_runs_than_the_wavefront_lookup_table():
+    """More than 256 wavefront-capable runs in one batch: the multi-run
+    wavefront flow then takes each run's units in turn (no shared-memory
+    prefix tables); the per-run unit numbering is the same, so members agree
+    bitwise with the same runs stepped alone with the multi-run kernels."""
+    base = W.small_parity(precision="fp32").replace(nx=128, ns=4, spot_x=(3, 64, 127), rho_mean=2.3)
+    cfgs = [base.replace(nf=20 + (i % 13), liquid_rows=7 + (i % 5), seed=100 + i) for i in range(260)]
+    runs = [multi(lbm.Run(c)) for c in cfgs]
+    batch = lbm.Batch(runs)
+    batch.step(6)
+    batch.sync()
+    for i in (0, 1, 137, 255, 256, 259):
+        r = multi(lbm.Run(cfgs[i]))
+        r.step(6)
+        want = r.fields(("rho", "T", "f"))
+        got = runs[i].fields(("rho", "T", "f"))
+        for k in want:
+            assert np.array_equal(got[k], want[k]), (i, k)
+        r.close()
+    batch.close()
+    for r in runs:
+        r.close()
