@@ -131,6 +131,20 @@ def issue_roofline(inst_per_site, sites, ms):
             "instructions_per_site": inst_per_site}
 
 
+def ncu_fp64_instructions(kind: str):
+    """FP64 pipe instructions per site (DADD + DMUL + DFMA executed, from ncu)
+    of the FP64 flow or heat kernel in the committed summary, or None."""
+    try:
+        text = open(PROFILES["fp64"]).read()
+    except OSError:
+        return None
+    m = re.search(r"fp64_source_sha256_16:\s*([0-9a-f]+)", text)
+    t = re.search(r"fp64_instructions_per_site\[" + re.escape(kind) + r"\]:\s*([0-9.eE+]+)", text)
+    if not m or not t or m.group(1) != kernel_source_hash(FP64_SOURCES):
+        return None
+    return float(t.group(1))
+
+
 def ncu_fp64_flops(kind: str):
     """FP64 flops per site (DADD + DMUL + 2 DFMA executed, from ncu) of the
     FP64 flow or heat kernel in the committed summary, or None when absent
@@ -810,6 +824,19 @@ def run_ours(args):
                 "heat": {"bound": "fp64_alu", "achieved": ach[1], "peak": fma64, "unit": "TFLOP/s",
                          "frac": ach[1] / fma64, "flops_per_site": fh},
                 "peak_source": "lbm_peak_fma(64): FMA chains on every SM, measured in this run"}
+            # the same kernels against the FP64 pipe's instruction rate: a
+            # DADD or DMUL takes the pipe like a DFMA, so with -fmad=false the
+            # flop fraction understates how busy the pipe is
+            il, ih = ncu_fp64_instructions("flow"), ncu_fp64_instructions("heat")
+            if il is not None and ih is not None:
+                ipk = fma64 / 2.0  # T FP64 instructions/s
+                ia = (il * sites / (k64ms[0] / 1e3) / 1e12, ih * cfg.temperature_sites / (k64ms[1] / 1e3) / 1e12)
+                fp64["pipe_roofline"] = {
+                    "flow": {"achieved": ia[0], "peak": ipk, "unit": "T FP64 instructions/s", "frac": ia[0] / ipk,
+                             "instructions_per_site": il},
+                    "heat": {"achieved": ia[1], "peak": ipk, "unit": "T FP64 instructions/s", "frac": ia[1] / ipk,
+                             "instructions_per_site": ih},
+                    "peak_source": "half the measured FP64 FMA flop rate (one DFMA = 2 flops per instruction)"}
     else:
         run.close()
 

@@ -61,3 +61,18 @@ def test_issue_roofline_arithmetic(monkeypatch):
     assert r["achieved"] == pytest.approx(0.01)
     assert r["frac"] == pytest.approx(0.01 / r["peak"])
     assert bench.issue_roofline(None, 1, 1.0) is None
+
+
+def test_fp64_counts_are_used_only_for_the_current_fp64_sources(tmp_path, monkeypatch):
+    path = tmp_path / "fp64.md"
+    monkeypatch.setitem(bench.PROFILES, "fp64", str(path))
+    h = bench.kernel_source_hash(bench.FP64_SOURCES)
+    path.write_text("fp64_instructions_per_site[flow]: 370.4\n"
+                    "fp64_flops_per_site[flow]: 464.1\n"
+                    f"fp64_source_sha256_16: {h}\n")
+    assert bench.ncu_fp64_instructions("flow") == 370.4
+    assert bench.ncu_fp64_flops("flow") == 464.1
+    assert bench.ncu_fp64_instructions("heat") is None      # not counted
+    path.write_text("fp64_instructions_per_site[flow]: 370.4\n"
+                    "fp64_source_sha256_16: 0000000000000000\n")
+    assert bench.ncu_fp64_instructions("flow") is None      # taken on other code
