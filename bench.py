@@ -640,7 +640,7 @@ def measure_dfsrc(lbm, W, torch, stream, steps, err_steps=20):
             "kernel_ms": {"flow": kms[0], "heat": kms[1], "diag": kms[2]},
             "variants": {"flow": v["flow"][v["selected"][0]], "heat": v["heat"][v["selected"][1]]},
             "max_rel_error_vs_fp64": errs, "error_steps": err_steps,
-            "note": "source term of Eq. 24 in double-float (FP32 pairs, ~48-bit significand); errors after "
+            "note": "source term of Eq. 24 in double-float (FP32 pairs, ~45-48-bit significand); errors after "
                     f"{err_steps} steps against the FP64 GPU path, both FP32 runs on the same heat shape "
                     "(heatrows_64x8x4) and flow variant"}
 
